@@ -1,0 +1,313 @@
+"""Python face of the CPU oracle (test infrastructure only).
+
+Loads the plain C library built from stab_oracle.c and exposes each step of the
+stabiliser's hot path on numpy arrays, plus `run_clip`, the whole per-frame
+schedule of Sec. 3-5 of arXiv 1701.03572 chained in the order the paper gives.
+
+Only the tests, the smoke check and the benchmark's CPU-baseline leg import
+this module.  It never imports the CUDA package, and the CUDA package never
+imports it.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import subprocess
+from dataclasses import dataclass
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "stab_oracle.c")
+_LIB = os.path.join(_HERE, "_build", "libstab_oracle.so")
+_lib = None
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle with gcc (no contraction of a*b+c: decisions taken in
+    FP32 must reproduce the stated operation order)."""
+    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+        os.makedirs(os.path.dirname(_LIB), exist_ok=True)
+        tmp = _LIB + f".{os.getpid()}.tmp"
+        subprocess.check_call(["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fPIC", "-shared",
+                               "-o", tmp, _SRC, "-lm"])
+        os.replace(tmp, _LIB)
+    return _LIB
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        _lib = C.CDLL(build())
+        _declare(_lib)
+    return _lib
+
+
+_u8p = C.POINTER(C.c_uint8)
+_f32p = C.POINTER(C.c_float)
+_f64p = C.POINTER(C.c_double)
+_i32p = C.POINTER(C.c_int32)
+
+
+def _declare(L):
+    L.or_luma.argtypes = [_u8p, C.c_int, C.c_int, C.c_int, _u8p, C.c_int]
+    L.or_pyr_down.argtypes = [_u8p, C.c_int, C.c_int, C.c_int, _u8p, C.c_int]
+    L.or_structure.argtypes = [_u8p, C.c_int, C.c_int, C.c_int, _i32p]
+    L.or_lambda32.argtypes = [C.c_int32] * 3
+    L.or_lambda32.restype = C.c_float
+    L.or_lambda64.argtypes = [C.c_int32] * 3
+    L.or_lambda64.restype = C.c_double
+    L.or_response.argtypes = [_u8p, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, _f32p, _f64p]
+    L.or_detect.argtypes = [_u8p, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, C.c_float,
+                            C.c_int, _f32p, _f32p, _i32p]
+    L.or_detect.restype = C.c_int
+    L.or_track.argtypes = [C.POINTER(_u8p), C.POINTER(_u8p), _i32p, _i32p, _i32p, C.c_int, _f32p, C.c_int,
+                           C.c_int, C.c_int, C.c_double, C.c_double, C.c_double, _f64p, _f64p, _f64p, _u8p, _u8p,
+                           _i32p]
+    L.or_track.restype = C.c_int
+    L.or_splitmix64.argtypes = [C.c_uint64]
+    L.or_splitmix64.restype = C.c_uint64
+    L.or_sample_pair.argtypes = [C.c_uint64, C.c_int, C.c_int, C.c_int, _i32p, _i32p]
+    L.or_fit.argtypes = [_f32p, _f32p, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, C.c_uint64, C.c_int,
+                         C.c_float, C.c_int, _f64p, _i32p, _f64p, _u8p, _i32p]
+    L.or_fit.restype = C.c_int
+    L.or_ls_similarity.argtypes = [_f64p, _f64p, C.c_int, C.c_int, _f64p]
+    L.or_smooth.argtypes = [_f64p, C.c_int, C.c_int, _f64p, _f64p, _f64p]
+    L.or_warp_inverse.argtypes = [_f64p, C.c_int, C.c_int, _f32p]
+    L.or_warp.argtypes = [_u8p, C.c_int, C.c_int, C.c_int, C.c_int, _f32p, _u8p, C.c_int]
+    L.or_charb.argtypes = [_f32p, _f32p, C.c_int, C.c_int, C.c_int, _f64p, C.c_double, _f64p, _f64p, _f64p,
+                           _f64p, _f64p]
+    L.or_charb.restype = C.c_double
+
+
+def _p(a, t):
+    return a.ctypes.data_as(t) if a is not None else None
+
+
+def _c(a, dt):
+    return np.ascontiguousarray(a, dtype=dt)
+
+
+# ---------------------------------------------------------------- pyramid --
+def luma(rgb: np.ndarray) -> np.ndarray:
+    rgb = _c(rgb, np.uint8)
+    h, w, _ = rgb.shape
+    out = np.empty((h, w), np.uint8)
+    lib().or_luma(_p(rgb, _u8p), w, h, w * 3, _p(out, _u8p), w)
+    return out
+
+
+def pyr_down(img: np.ndarray) -> np.ndarray:
+    img = _c(img, np.uint8)
+    h, w = img.shape
+    out = np.empty(((h + 1) // 2, (w + 1) // 2), np.uint8)
+    lib().or_pyr_down(_p(img, _u8p), w, h, w, _p(out, _u8p), out.shape[1])
+    return out
+
+
+def pyramid(img: np.ndarray, levels: int) -> list:
+    pyr = [_c(img, np.uint8)]
+    for _ in range(1, levels):
+        pyr.append(pyr_down(pyr[-1]))
+    return pyr
+
+
+# ---------------------------------------------------------------- corners --
+def structure(img, x, y):
+    img = _c(img, np.uint8)
+    out = np.zeros(3, np.int32)
+    lib().or_structure(_p(img, _u8p), img.shape[1], x, y, _p(out, _i32p))
+    return out
+
+
+def lambda32(a, b, c) -> float:
+    return float(lib().or_lambda32(int(a), int(b), int(c)))
+
+
+def lambda64(a, b, c) -> float:
+    return float(lib().or_lambda64(int(a), int(b), int(c)))
+
+
+def response(img, x0, y0, x1, y1):
+    img = _c(img, np.uint8)
+    l32 = np.zeros((y1 - y0, x1 - x0), np.float32)
+    l64 = np.zeros((y1 - y0, x1 - x0), np.float64)
+    lib().or_response(_p(img, _u8p), img.shape[1], x0, y0, x1, y1, _p(l32, _f32p), _p(l64, _f64p))
+    return l32, l64
+
+
+def roi_of(w: int, h: int, win_r: int = 10):
+    """Reduced region of interest (Sec. 3.1; size not stated): a margin of
+    max(size // 10, win_r + 2) pixels on each side."""
+    mx, my = max(w // 10, win_r + 2), max(h // 10, win_r + 2)
+    return mx, my, w - mx, h - my
+
+
+def detect(img, roi, K: int, q: float = 0.01):
+    img = _c(img, np.uint8)
+    h, w = img.shape
+    pts = np.zeros((max(K, 1), 2), np.float32)
+    lam = np.zeros(max(K, 1), np.float32)
+    nc = np.zeros(1, np.int32)
+    m = lib().or_detect(_p(img, _u8p), w, h, w, roi[0], roi[1], roi[2], roi[3], q, K, _p(pts, _f32p),
+                        _p(lam, _f32p), _p(nc, _i32p))
+    if m < 0:
+        raise ValueError("bad ROI")
+    return pts[:m].copy(), lam[:m].copy(), int(nc[0])
+
+
+# --------------------------------------------------------------- tracking --
+def track(pyrI: list, pyrJ: list, pts: np.ndarray, win_r=10, max_iters=30, eps=0.01, min_eig=1e-2,
+          fb_thresh=1.0) -> dict:
+    L = len(pyrI)
+    pyrI = [_c(a, np.uint8) for a in pyrI]
+    pyrJ = [_c(a, np.uint8) for a in pyrJ]
+    PI = (_u8p * L)(*[_p(a, _u8p) for a in pyrI])
+    PJ = (_u8p * L)(*[_p(a, _u8p) for a in pyrJ])
+    lw = np.array([a.shape[1] for a in pyrI], np.int32)
+    lh = np.array([a.shape[0] for a in pyrI], np.int32)
+    pts = _c(pts, np.float32).reshape(-1, 2)
+    n = pts.shape[0]
+    fwd = np.zeros((n, 2)); back = np.zeros((n, 2)); fb = np.zeros(n)
+    st = np.zeros(n, np.uint8); stf = np.zeros(n, np.uint8); it = np.zeros(1, np.int32)
+    lib().or_track(PI, PJ, _p(lw, _i32p), _p(lh, _i32p), _p(lw, _i32p), L, _p(pts, _f32p), n, win_r, max_iters,
+                   eps, min_eig, fb_thresh, _p(fwd, _f64p), _p(back, _f64p), _p(fb, _f64p), _p(st, _u8p),
+                   _p(stf, _u8p), _p(it, _i32p))
+    return dict(fwd=fwd, back=back, fb_err=fb, status=st, status_fwd=stf, iters=int(it[0]))
+
+
+# -------------------------------------------------------------------- fit --
+def splitmix64(x: int) -> int:
+    return int(lib().or_splitmix64(C.c_uint64(x & 0xFFFFFFFFFFFFFFFF)))
+
+
+def sample_pair(seed: int, t: int, h: int, n: int):
+    i = np.zeros(1, np.int32); j = np.zeros(1, np.int32)
+    lib().or_sample_pair(C.c_uint64(seed), t, h, n, _p(i, _i32p), _p(j, _i32p))
+    return int(i[0]), int(j[0])
+
+
+def fit(src, dst, w, h, rigid: bool, H: int, seed: int, t: int, tau: float = 1.0, min_pts: int = 10) -> dict:
+    src = _c(src, np.float32).reshape(-1, 2)
+    dst = _c(dst, np.float32).reshape(-1, 2)
+    n = src.shape[0]
+    out = np.zeros(4); bh = np.zeros(1, np.int32); rms = np.zeros(1); fl = np.zeros(1, np.int32)
+    mask = np.zeros(max(n, 1), np.uint8)
+    ni = lib().or_fit(_p(src, _f32p), _p(dst, _f32p), n, w, h, int(rigid), H, C.c_uint64(seed), t, tau,
+                      min_pts, _p(out, _f64p), _p(bh, _i32p), _p(rms, _f64p), _p(mask, _u8p), _p(fl, _i32p))
+    return dict(m=out, inliers=int(ni), best_h=int(bh[0]), rms=float(rms[0]), mask=mask[:n].astype(bool),
+                flags=int(fl[0]))
+
+
+def ls_similarity(src, dst, rigid: bool):
+    src = _c(src, np.float64).reshape(-1, 2)
+    dst = _c(dst, np.float64).reshape(-1, 2)
+    out = np.zeros(4)
+    lib().or_ls_similarity(_p(src, _f64p), _p(dst, _f64p), src.shape[0], int(rigid), _p(out, _f64p))
+    return out
+
+
+# ------------------------------------------------------- smoothing, warp --
+def smooth(m, W: int):
+    m = _c(m, np.float64).reshape(-1, 4)
+    T = m.shape[0]
+    Cc = np.zeros_like(m); S = np.zeros_like(m); mp = np.zeros_like(m)
+    lib().or_smooth(_p(m, _f64p), T, W, _p(Cc, _f64p), _p(S, _f64p), _p(mp, _f64p))
+    return Cc, S, mp
+
+
+def warp_inverse(m, w, h) -> np.ndarray:
+    m = _c(m, np.float64)
+    out = np.zeros(6, np.float32)
+    lib().or_warp_inverse(_p(m, _f64p), w, h, _p(out, _f32p))
+    return out
+
+
+def warp(src: np.ndarray, Minv) -> np.ndarray:
+    src = _c(src, np.uint8)
+    h, w = src.shape[:2]
+    ch = 1 if src.ndim == 2 else src.shape[2]
+    M = _c(Minv, np.float32)
+    out = np.empty_like(src)
+    lib().or_warp(_p(src, _u8p), w, h, ch, w * ch, _p(M, _f32p), _p(out, _u8p), w * ch)
+    return out
+
+
+# ------------------------------------------------------- photometric GN --
+def charb(It, Ip, theta, margin=48, eps=1e-3, want_dI=False, want_gn=False) -> dict:
+    It = _c(It, np.float32); Ip = _c(Ip, np.float32)
+    h, w = It.shape
+    th = _c(theta, np.float64)
+    dth = np.zeros(4)
+    dIt = np.zeros((h, w)) if want_dI else None
+    dIp = np.zeros((h, w)) if want_dI else None
+    Hm = np.zeros((4, 4)) if want_gn else None
+    g = np.zeros(4) if want_gn else None
+    L = lib().or_charb(_p(It, _f32p), _p(Ip, _f32p), w, h, margin, _p(th, _f64p), eps, _p(dth, _f64p),
+                       _p(dIt, _f64p), _p(dIp, _f64p), _p(Hm, _f64p), _p(g, _f64p))
+    return dict(loss=L, dtheta=dth, dIt=dIt, dIp=dIp, H=Hm, g=g)
+
+
+def gauss_newton(It, Ip, theta0, steps=10, margin=48, eps=1e-3):
+    """IRLS Gauss-Newton on the Charbonnier objective: theta <- theta - H^-1 g."""
+    th = np.array(theta0, np.float64)
+    for _ in range(steps):
+        r = charb(It, Ip, th, margin, eps, want_gn=True)
+        th = th - np.linalg.solve(r["H"], r["g"])
+    return th
+
+
+# ---------------------------------------------------------- whole clip --
+@dataclass
+class Params:
+    """Per-clip settings (paper constants where it gives them)."""
+    max_corners: int = 200
+    levels: int = 3
+    win_r: int = 10              # 21 x 21 window
+    max_iters: int = 30
+    eps: float = 0.01
+    min_eig: float = 1e-2
+    quality: float = 0.01
+    redetect_period: int = 5     # Sec. 3.2: detect on one frame, track through the next five
+    min_tracks: int = 10
+    fb_thresh: float = 1.0
+    inlier_thresh: float = 1.0
+    hypotheses: int = 100
+    seed: int = 0
+    min_fit: int = 10
+    smooth_window: int = 15
+    rigid: bool = False
+
+
+def run_clip(frames: np.ndarray, p: Params) -> dict:
+    """Motion estimation, compensation and composition over a whole clip
+    (Sec. 3-5, offline form).  frames: (T, h, w) or (T, h, w, 3) uint8."""
+    frames = np.asarray(frames)
+    T = frames.shape[0]
+    h, w = frames.shape[1:3]
+    gray = [luma(f) if frames.ndim == 4 else _c(f, np.uint8) for f in frames]
+    pyrs = [pyramid(g, p.levels) for g in gray]
+    roi = roi_of(w, h, p.win_r)
+    incs = np.zeros((T, 4)); flags = np.zeros(T, np.int32)
+    n_tracked = np.zeros(T, np.int32); n_inl = np.zeros(T, np.int32); detected = np.zeros(T, bool)
+    feats = None
+    for t in range(1, T):
+        if feats is None or (t - 1) % p.redetect_period == 0 or len(feats) < p.min_tracks:
+            feats, _, _ = detect(gray[t - 1], roi, p.max_corners, p.quality)
+            detected[t - 1] = True
+        tr = track(pyrs[t - 1], pyrs[t], feats, p.win_r, p.max_iters, p.eps, p.min_eig, p.fb_thresh)
+        keep = tr["status"] == 1
+        src = feats[keep]
+        dst = tr["fwd"][keep].astype(np.float32)
+        n_tracked[t] = int(keep.sum())
+        f = fit(src, dst, w, h, p.rigid, p.hypotheses, p.seed, t, p.inlier_thresh, p.min_fit)
+        incs[t] = f["m"]; flags[t] = f["flags"]; n_inl[t] = f["inliers"]
+        feats = dst
+    Cc, S, mp = smooth(incs, p.smooth_window)
+    Minv = np.zeros((T, 6), np.float32)
+    out = np.zeros_like(frames)
+    for t in range(1, T):
+        Minv[t] = warp_inverse(mp[t], w, h)
+        out[t - 1] = warp(frames[t - 1], Minv[t])
+    return dict(incs=incs, flags=flags, n_tracked=n_tracked, n_inliers=n_inl, detected=detected, C=Cc, S=S,
+                mp=mp, Minv=Minv, out=out)
