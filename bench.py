@@ -1,0 +1,476 @@
+"""Benchmark: 1080p stabilised frames/s on one GB300 (batched vs plain) and
+per-step latency percentiles.
+
+Workload (one step): every stream of a batch of 16 independent 1920x1080 RGB
+videos advances by one frame through the whole path -- luma + 5-level
+pyramid with FP16 I/Ix/Iy planes, corner detection when due (every 5th
+frame), pyramidal LK forward + backward on 1000 corners, robust similarity
+fit (100 hypotheses), streaming 30-frame smoothing, RGB compensating warp --
+as one CUDA-graph launch.  `value` = stabilised frames/s of the batch with
+the frames already in HBM (an input ring larger than L2); `plain` = the same
+path for one stream through the single-stream calls with FP32 planes;
+`e2e` = the batch through stab_batch_step_host with pinned host frames in and
+stabilised frames out.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+Under torchrun each rank runs its own batch on its own GPU (independent
+videos: no exchange), and rank 0 prints one JSON line.
+"""
+from __future__ import annotations
+
+import argparse
+import ctypes as C
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "1080p stabilized frames/s on 1 GB300 (batched vs plain); p99 frame latency ms"
+W, H, CH = 1920, 1080, 3
+STREAMS = 16
+PARAMS = dict(max_corners=1000, levels=5, hypotheses=100, smooth_window=30, model=1)
+FP32_PEAK_NOTE = "152 SMs x 128 FP32 lanes x 2 flop x 2.07 GHz max SM clock"
+FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
+# LK algorithmic work per window sample: template pass = bilinear I, Ix, Iy
+# (3 x 7 flop) + G accumulation (3 FMA = 6 flop) = 27; iteration = bilinear J
+# (7) + residual (1) + b accumulation (2 FMA = 4) = 12.
+LK_FLOP_TEMPLATE, LK_FLOP_ITER = 27, 12
+# DRAM traffic per launch of the dominant kernel from an ncu capture
+# (profiles/); used only while the kernel source is unchanged.
+TRAFFIC = {}
+
+
+def config_dict(streams):
+    return {"workload": f"{streams} streams x 1920x1080 RGB, config-2 shape (K=1000 corners, 5 levels, "
+                        "similarity, 100 hypotheses, 30-frame window), batched CUDA-graph step, FP16 plane storage",
+            "streams": streams, "resolution": "1920x1080", "channels": 3, "corners": 1000, "levels": 5,
+            "hypotheses": 100, "smooth_window": 30,
+            "l2": "inputs larger than L2: each step reads new frames from a device ring of "
+                  f"{streams} x 18 RGB 1080p frames (1.8 GB)"}
+
+
+# ------------------------------------------------------------ distributed --
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def partition_streams(total: int, world: int, rank: int) -> list:
+    """Stream indices of `rank` (round-robin): independent videos, no exchange."""
+    return list(range(rank, total, world))
+
+
+def max_over_ranks(x: float, device=None) -> float:
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()):
+        return x
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def barrier(device=None):
+    import torch.distributed as dist
+    if dist.is_available() and dist.is_initialized():
+        dist.barrier()
+
+
+# ------------------------------------------------------------------ clocks --
+class ClockSampler:
+    FIELDS = "clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown," \
+             "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown," \
+             "clocks_event_reasons.sw_power_cap"
+
+    def __init__(self, gpu: int):
+        self.gpu, self.proc, self.path = gpu, None, None
+
+    def start(self):
+        try:
+            import tempfile
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        rows = []
+        for line in open(self.path):
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 8:
+                continue
+            try:
+                rows.append((float(f[0]), float(f[1]), f[4:8]))
+            except ValueError:
+                continue
+        os.unlink(self.path)
+        if not rows:
+            return None
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for _, _, r in rows for i, v in enumerate(r) if v.lower() == "active"})
+        return {"sm_mhz": statistics.median(r[0] for r in rows), "sm_max_mhz": max(r[1] for r in rows),
+                "reasons": reasons, "samples": len(rows)}
+
+
+# ------------------------------------------------------------------ frames --
+def make_frames(n_clips: int, ring: int, device: str):
+    """n_clips seeded 1080p RGB clips of `ring` frames that retrace their path
+    (frame ring == frame 0), so cycling the ring is a continuous video."""
+    import dataclasses
+
+    import torch
+    from paper_1701_03572_gb300.synth import CONFIG_SPECS, make_clip
+    spec = dataclasses.replace(CONFIG_SPECS[2], frames=ring, pingpong=True)
+    return [make_clip(spec, 2000 + c, device=device, dtype=torch.float32)["frames"] for c in range(n_clips)]
+
+
+# ----------------------------------------------------------- our arm (GPU) --
+def run_ours(args):
+    import torch
+    ws, rank, local = dist_env()
+    if ws > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", init_method="env://")
+    dev = f"cuda:{local}" if ws > 1 else "cuda:0"
+    torch.cuda.set_device(dev)
+    from paper_1701_03572_gb300 import build as build_lib
+    build_lib()
+    from paper_1701_03572_gb300 import stab as S
+
+    B = args.streams
+    A = PARAMS["smooth_window"] // 2
+    ring = 2 * (A + 2)                      # >= A + 2 and even for the retracing clip
+    clips = make_frames(min(4, B), ring, dev)
+    p16 = S.default_params(**PARAMS, precision=S.STAB_FP16_STORAGE)
+    batch = S.Batch([(W, H, CH, p16) for _ in range(B)], ring=ring)
+    offs = [(i // len(clips)) * 3 % ring for i in range(B)]
+    for i in range(B):
+        for s in range(ring):
+            batch.input_slot(i, s).copy_(clips[i % len(clips)][(s + offs[i]) % ring])
+    stream = torch.cuda.current_stream()
+    # prime the smoother's lookahead (no composed frame before step A + 1), then warm up
+    for _ in range(A + 2 + args.warmup):
+        batch.step(True)
+    torch.cuda.synchronize()
+    n_k = 11 + (PARAMS["levels"] - 1)       # kernels per step
+    # ---- timed region: K graph steps
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps + 1)]
+    clocks = ClockSampler(local)
+    clocks.start()
+    barrier()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    ev[0].record(stream)
+    for k in range(args.steps):
+        batch.step(True)
+        ev[k + 1].record(stream)
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - t0
+    barrier()
+    clk = clocks.stop()
+    assert batch.sync() == 0
+    step_ms = [ev[k].elapsed_time(ev[k + 1]) for k in range(args.steps)]
+    total_ms = ev[0].elapsed_time(ev[-1])
+    total_ms = max_over_ranks(total_ms, dev)
+    value = ws * B * args.steps / (total_ms / 1e3)
+    lat = sorted(step_ms)
+    p50 = lat[len(lat) // 2]
+    p99 = lat[min(len(lat) - 1, int(math.ceil(0.99 * len(lat))) - 1)]
+
+    # ---- per-kernel times (event-bracketed steps without a graph)
+    kt, lkw = {}, []
+    for _ in range(args.prof_steps):
+        for name, ms in batch.step_profiled().items():
+            kt.setdefault(name, []).append(ms)
+        lkw.append(batch.lk_work())
+    kavg = {k: sum(v) / len(v) for k, v in kt.items()}
+    roof = roofline(kavg, lkw, B)
+
+    # ---- plain single-stream path, FP32 planes
+    plain = run_plain(S, clips[0], ring, args.plain_steps, dev)
+
+    # ---- end to end through host buffers
+    e2e = run_e2e(S, batch, clips, offs, ring, args.e2e_steps, B)
+
+    out = {"metric": METRIC, "value": round(value, 1), "unit": "frames/s", "n_gpus": ws, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": round(total_ms / args.steps, 4), "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f32", "storage": "u8 frames, f16 I/Ix/Iy planes",
+           "data": "synthetic", "config": config_dict(B),
+           "latency_ms": {"p50": round(p50, 4), "p99": round(p99, 4), "per": "batch step (16 frames)"},
+           "plain": plain, "e2e": e2e, "roofline": roof,
+           "kernels_ms": {k: round(v, 4) for k, v in kavg.items()},
+           "gpu_launches": n_k * args.steps, "clocks": clk, "wall_s": round(wall, 3)}
+    if ws == 1 and rank == 0 and not args.no_cpu_baseline:
+        out["cpu_baseline"] = cpu_baseline(clips[0].cpu().numpy(), args.cpu_frames)
+    if rank == 0:
+        print(json.dumps(out))
+    if ws > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+def kernel_source_sha(name: str) -> str:
+    path = os.path.join(ROOT, "paper_1701_03572_gb300", "csrc", name)
+    return hashlib.sha256(open(path, "rb").read()).hexdigest()[:16]
+
+
+def roofline(kavg: dict, lkw: list, B: int) -> dict:
+    import json as _json
+    peaks = {}
+    pk = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(pk):
+        peaks = _json.load(open(pk))
+    hbm = peaks.get("hbm_gbs")
+    hbm_src = "of measured" if hbm else "of fallback"
+    hbm = hbm or 6800.0
+    dom = max(kavg, key=kavg.get)
+    # algorithmic bytes per launch of the HBM-bound kernels (16 streams)
+    L = PARAMS["levels"]
+    sizes = [(W, H)]
+    for _ in range(1, L):
+        sizes.append(((sizes[-1][0] + 1) // 2, (sizes[-1][1] + 1) // 2))
+    alg_bytes = {
+        # RGB in (3 B/px), luma level 0 out (1 B/px), I + (Ix, Iy) FP16 out (6 B/px)
+        "level0": B * W * H * (3 + 1 + 6),
+        # warp: RGB frame in, RGB frame out
+        "warp": B * W * H * CH * 2,
+    }
+    for l in range(1, L):
+        pw, ph = sizes[l - 1]
+        w_, h_ = sizes[l]
+        alg_bytes[f"pyr_down_{l}"] = B * (pw * ph + w_ * h_ * (1 + 6))
+    kernels = {}
+    for k, ms in kavg.items():
+        if k in alg_bytes and ms > 0:
+            gbs = alg_bytes[k] / (ms / 1e3) / 1e9
+            kernels[k] = {"bound": "hbm", "achieved": round(gbs, 1), "unit": "GB/s", "frac": round(gbs / hbm, 3),
+                          "ms": round(ms, 4)}
+    it = sum(x[0] for x in lkw) / max(len(lkw), 1)
+    tp = sum(x[1] for x in lkw) / max(len(lkw), 1)
+    n_win = (2 * 10 + 1) ** 2
+    lk_flop = tp * n_win * LK_FLOP_TEMPLATE + it * n_win * LK_FLOP_ITER
+    if kavg.get("lk", 0) > 0:
+        tf = lk_flop / (kavg["lk"] / 1e3) / 1e12
+        kernels["lk"] = {"bound": "alu", "achieved": round(tf, 3), "unit": "TFLOP/s",
+                         "frac": round(tf / FP32_PEAK_TFLOPS, 4), "ms": round(kavg["lk"], 4),
+                         "iterations": int(it), "template_passes": int(tp)}
+    if dom in kernels:
+        d = kernels[dom]
+        traffic = None
+        tr = TRAFFIC.get(dom)
+        if tr and tr.get("sha") == kernel_source_sha(tr["file"]):
+            traffic = tr["bytes_per_launch"]
+        peak = FP32_PEAK_TFLOPS if d["bound"] == "alu" else hbm
+        res = {"kernel": dom, "bound": d["bound"], "achieved": d["achieved"], "peak": round(peak, 1),
+               "unit": d["unit"], "frac": d["frac"], "traffic": traffic,
+               "peak_source": FP32_PEAK_NOTE if d["bound"] == "alu" else f"MEASURED_PEAKS.json hbm_gbs ({hbm_src})",
+               "per_kernel": kernels}
+        if d["bound"] == "alu":
+            res["algorithmic_flop_per_launch"] = round(lk_flop)
+        else:
+            res["algorithmic_bytes_per_launch"] = alg_bytes[dom]
+        return res
+    return {"kernel": dom, "bound": None, "achieved": None, "peak": None, "unit": None, "frac": None,
+            "traffic": None, "per_kernel": kernels}
+
+
+def run_plain(S, clip, ring, steps, dev):
+    """One 1080p stream through stab_track / stab_fit / stab_smooth_push /
+    stab_warp with FP32 planes, buffers allocated once."""
+    import torch
+    p = S.default_params(**PARAMS, precision=S.STAB_FP32)
+    ctx = S.Context(W, H, p)
+    L = S.lib()
+    K = p.max_corners
+    src = torch.zeros((K, 2), device=dev)
+    dst = torch.zeros((K, 2), device=dev)
+    status = torch.zeros(K, dtype=torch.uint8, device=dev)
+    n = torch.zeros(1, dtype=torch.int32, device=dev)
+    mot = torch.zeros(8, device=dev)
+    Minv = torch.zeros(6, device=dev)
+    ready = torch.zeros(1, dtype=torch.int32, device=dev)
+    out = torch.zeros((H, W, CH), dtype=torch.uint8, device=dev)
+    fr = clip.contiguous()
+    A = p.smooth_window // 2
+    s = S._s()
+    pitch = W * CH
+    vp = C.c_void_p
+
+    def frame_step(t):
+        prev, nxt = fr[(t - 1) % ring], fr[t % ring]
+        L.stab_track(ctx._h, vp(prev.data_ptr()), vp(nxt.data_ptr()), pitch, CH, 1 if t > 1 else 0,
+                     vp(src.data_ptr()), vp(dst.data_ptr()), vp(status.data_ptr()), vp(n.data_ptr()), s)
+        L.stab_fit(ctx._h, vp(src.data_ptr()), vp(dst.data_ptr()), vp(n.data_ptr()), p.model, t,
+                   vp(mot.data_ptr()), s)
+        L.stab_smooth_push(ctx._h, vp(mot.data_ptr()), vp(Minv.data_ptr()), vp(ready.data_ptr()), s)
+        u = t - 1 - A
+        if u >= 0:
+            L.stab_warp(ctx._h, vp(fr[u % ring].data_ptr()), pitch, vp(out.data_ptr()), pitch, CH,
+                        vp(Minv.data_ptr()), s)
+
+    t = 1
+    for _ in range(A + 4):
+        frame_step(t)
+        t += 1
+    torch.cuda.synchronize()
+    stream = torch.cuda.current_stream()
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(steps + 1)]
+    ev[0].record(stream)
+    for k in range(steps):
+        frame_step(t)
+        t += 1
+        ev[k + 1].record(stream)
+    torch.cuda.synchronize()
+    assert ctx.sync() == 0
+    ms = [ev[k].elapsed_time(ev[k + 1]) for k in range(steps)]
+    tot = ev[0].elapsed_time(ev[-1])
+    lat = sorted(ms)
+    return {"value": round(steps / (tot / 1e3), 1), "unit": "frames/s", "p50_ms": round(lat[len(lat) // 2], 4),
+            "p99_ms": round(lat[min(len(lat) - 1, int(math.ceil(0.99 * len(lat))) - 1)], 4),
+            "config": "1 stream 1920x1080 RGB, FP32 planes, single-stream calls (no graph)", "frames": steps}
+
+
+def run_e2e(S, batch, clips, offs, ring, steps, B):
+    import torch
+    host = [c.cpu().pin_memory() for c in clips]
+    outs = [torch.empty((H, W, CH), dtype=torch.uint8).pin_memory() for _ in range(B)]
+    stream = torch.cuda.current_stream()
+    t0 = batch.frame
+
+    def one(t):
+        frames = [host[i % len(host)][(t + offs[i]) % ring] for i in range(B)]
+        batch.step_host(frames, outs)
+
+    for k in range(3):
+        one(t0 + k)
+    torch.cuda.synchronize()
+    t0 = batch.frame
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for k in range(steps):
+        one(t0 + k)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    assert batch.sync() == 0
+    ms = e0.elapsed_time(e1)
+    return {"value": round(B * steps / (ms / 1e3), 1), "unit": "frames/s",
+            "h2d_bytes_per_step": B * W * H * CH, "d2h_bytes_per_step": B * W * H * CH,
+            "api": "stab_batch_step_host (pinned host frames in, stabilised frames out)", "steps": steps}
+
+
+# ---------------------------------------------------- oracle (CPU) timing --
+def oracle_stream(frames, n_frames, warm=0):
+    """Time the oracle frame by frame on one 1080p RGB stream (the same per-
+    frame path, FP64 C, one thread).  Returns (frames timed, seconds)."""
+    from oracle import oracle as O
+    p = O.Params(max_corners=PARAMS["max_corners"], levels=PARAMS["levels"], hypotheses=PARAMS["hypotheses"],
+                 smooth_window=PARAMS["smooth_window"], rigid=False)
+    ring = frames.shape[0]
+    roi = O.roi_of(W, H)
+    A = p.smooth_window // 2
+    incs = [[0.0, 0.0, 0.0, 0.0]]
+    gray_prev = O.luma(frames[0])
+    pyr_prev = O.pyramid(gray_prev, p.levels)
+    feats = None
+    t_start, counted = None, 0
+    for t in range(1, warm + n_frames + 1):
+        if t == warm + 1:
+            t_start = time.perf_counter()
+        rgb = frames[t % ring]
+        gray = O.luma(rgb)
+        pyr = O.pyramid(gray, p.levels)
+        if feats is None or (t - 1) % p.redetect_period == 0 or len(feats) < p.min_tracks:
+            feats, _, _ = O.detect(gray_prev, roi, p.max_corners, p.quality)
+        tr = O.track(pyr_prev, pyr, feats, p.win_r, p.max_iters, p.eps, p.min_eig, p.fb_thresh)
+        keep = tr["status"] == 1
+        dst = tr["fwd"][keep].astype("float32")
+        f = O.fit(feats[keep], dst, W, H, p.rigid, p.hypotheses, p.seed, t, p.inlier_thresh, p.min_fit)
+        incs.append(list(f["m"]))
+        feats = dst
+        u = t - 1 - A
+        if u >= 0:
+            import numpy as np
+            _, _, mp = O.smooth(np.array(incs), p.smooth_window)
+            O.warp(frames[u % ring], O.warp_inverse(mp[u + 1], W, H))
+        gray_prev, pyr_prev = gray, pyr
+        if t > warm:
+            counted += 1
+    return counted, time.perf_counter() - t_start
+
+
+def cpu_baseline(frames, n):
+    cnt, sec = oracle_stream(frames, n)
+    return {"value": round(cnt / sec, 4), "unit": "frames/s", "cores": 1, "kind": "oracle",
+            "sample": f"{cnt} consecutive frames of one 1920x1080 RGB stream (luma, pyramid, detection when due, "
+                      f"LK fwd+bwd, fit, streaming smoothing, RGB warp); {sec:.1f} s"}
+
+
+def run_reference(args):
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return
+    import torch
+    from paper_1701_03572_gb300.synth import CONFIG_SPECS, make_clip
+    import dataclasses
+    A = PARAMS["smooth_window"] // 2
+    ring = 2 * (A + 2)
+    spec = dataclasses.replace(CONFIG_SPECS[2], frames=ring, pingpong=True)
+    frames = make_clip(spec, 2000, device="cpu", dtype=torch.float32,
+                       frames=range(min(ring, args.warmup + args.steps + 1)))["frames"].numpy()
+    cnt, sec = oracle_stream(frames, args.steps, warm=args.warmup)
+    v = cnt / sec
+    print(json.dumps({"impl": "reference", "metric": METRIC, "value": round(v, 4), "unit": "frames/s",
+                      "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
+                      "ms_per_step": round(1e3 * sec / cnt, 2), "higher_is_better": True, "scaling": "weak",
+                      "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": config_dict(STREAMS),
+                      "cpu_baseline": {"value": round(v, 4), "unit": "frames/s", "cores": 1, "kind": "oracle",
+                                       "sample": f"one step = one 1920x1080 RGB frame of one stream through the "
+                                                 f"FP64 C oracle (single thread); {cnt} steps"},
+                      "e2e": {"value": round(v, 4), "unit": "frames/s", "h2d_bytes_per_step": 0,
+                              "d2h_bytes_per_step": 0}}))
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--streams", type=int, default=STREAMS)
+    ap.add_argument("--prof-steps", type=int, default=10)
+    ap.add_argument("--plain-steps", type=int, default=60)
+    ap.add_argument("--e2e-steps", type=int, default=20)
+    ap.add_argument("--cpu-frames", type=int, default=8)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        ap.error("--warmup must be >= 3")
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -65,6 +65,7 @@ def _declare(L):
                            C.c_int, C.c_int, C.c_double, C.c_double, C.c_double, _f64p, _f64p, _f64p, _u8p, _u8p,
                            _i32p]
     L.or_track.restype = C.c_int
+    L.or_grad_planes.argtypes = [_u8p, C.c_int, C.c_int, C.c_int, _f64p, _f64p, _f64p]
     L.or_splitmix64.argtypes = [C.c_uint64]
     L.or_splitmix64.restype = C.c_uint64
     L.or_sample_pair.argtypes = [C.c_uint64, C.c_int, C.c_int, C.c_int, _i32p, _i32p]
@@ -157,6 +158,15 @@ def detect(img, roi, K: int, q: float = 0.01):
 
 
 # --------------------------------------------------------------- tracking --
+def grad_planes(img):
+    """(I, Ix, Iy) of one level: central differences, replicated borders."""
+    img = _c(img, np.uint8)
+    h, w = img.shape
+    I = np.zeros((h, w)); Ix = np.zeros((h, w)); Iy = np.zeros((h, w))
+    lib().or_grad_planes(_p(img, _u8p), w, h, w, _p(I, _f64p), _p(Ix, _f64p), _p(Iy, _f64p))
+    return I, Ix, Iy
+
+
 def track(pyrI: list, pyrJ: list, pts: np.ndarray, win_r=10, max_iters=30, eps=0.01, min_eig=1e-2,
           fb_thresh=1.0) -> dict:
     L = len(pyrI)

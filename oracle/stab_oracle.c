@@ -225,6 +225,19 @@ static double px_at(const plane_t *P, int x, int y)
 static double gx_at(const plane_t *P, int x, int y) { return 0.5 * (px_at(P, x + 1, y) - px_at(P, x - 1, y)); }
 static double gy_at(const plane_t *P, int x, int y) { return 0.5 * (px_at(P, x, y + 1) - px_at(P, x, y - 1)); }
 
+/* The I, Ix, Iy planes of one level as the tracker defines them (central
+ * differences with replicated borders), FP64. */
+void or_grad_planes(const uint8_t *img, int w, int h, int pitch, double *I, double *Ix, double *Iy)
+{
+    plane_t P = {img, w, h, pitch};
+    for (int y = 0; y < h; ++y)
+        for (int x = 0; x < w; ++x) {
+            I[(size_t)y * w + x] = px_at(&P, x, y);
+            Ix[(size_t)y * w + x] = gx_at(&P, x, y);
+            Iy[(size_t)y * w + x] = gy_at(&P, x, y);
+        }
+}
+
 /* bilinear sample of f (one of px_at, gx_at, gy_at) at (x, y); the base is
  * clamped far outside the image, where every tap is a border replica anyway */
 static double bilin(const plane_t *P, double (*f)(const plane_t *, int, int), double x, double y)

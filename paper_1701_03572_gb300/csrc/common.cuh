@@ -1,0 +1,116 @@
+// common.cuh -- device-side data layout shared by the kernels of the stabiliser.
+//
+// One "stream" is one video: its pyramids (two slots, previous and current
+// frame), its feature set, its detection scratch, its trajectory ring and (for
+// the batched pipeline) its input ring and output frame.  Every kernel walks a
+// work list spanning all streams, so one launch serves a whole batch; the
+// single-stream API is the same code with n = 1.
+#pragma once
+
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "stab.h"
+
+#define STAB_MAXL 8          // pyramid levels
+#define STAB_MAXK 2048       // corners per stream
+#define STAB_MAXR 12         // LK window radius
+#define STAB_CRING 64        // trajectory / motion ring (smoothing window <= 63)
+#define STAB_HBINS 4096      // response histogram: top 12 bits of the (non-negative) float score
+#define STAB_HSHIFT 19
+#define STAB_SEL_SMEM 12288  // selection keys held in shared memory
+#define STAB_TW 64           // image tile: 64 x 16 pixels, 256 threads x 4 pixels
+#define STAB_TH 16
+
+// Per-stream mutable state (device memory).
+struct StreamState {
+    long long t;          // index of the frame being stepped (0 = first frame)
+    int n_feat;           // live features (positions in frame t-1)
+    int n_pairs;          // pairs kept by the last track
+    int n_cand;           // NMS survivors of the last detection
+    int n_sel;            // survivors of the histogram cut
+    int blocks_done;      // response CTAs finished (last-CTA threshold step)
+    int due;              // detect on frame t-1 during this step
+    unsigned lam_max;     // bits of the largest score (scores >= 0 order like unsigned)
+    unsigned bin_lo;      // histogram bin where the top-K starts
+    unsigned thr_bits;    // bits of quality * max score
+    int out_frame;        // frame warped by this step (-1 none)
+    int err;              // first device error (stab_status), 0 if none
+    long long iters;      // LK iterations of this step (statistic)
+    long long tpl;        // LK template passes (feature x level x direction) of this step
+    int n_det;            // corners of the last detection
+    int pad_;
+};
+
+struct StreamDev {
+    int w, h, C, L, K;
+    int lw[STAB_MAXL], lh[STAB_MAXL], lp[STAB_MAXL];   // level sizes, pitch (elements)
+    // parameters
+    int r, max_iters, period, min_tracks, min_fit, H, rigid, W, prec;
+    float eps2, min_eig, quality, fb2, tau2;
+    unsigned long long seed;
+    int roi_x0, roi_y0, roi_x1, roi_y1;
+    // pyramids: two slots (frame parity); u8 levels and I / (Ix, Iy) planes
+    uint8_t *u8[2][STAB_MAXL];
+    void *pI[2][STAB_MAXL];   // float or __half
+    void *pG[2][STAB_MAXL];   // float2 or __half2
+    // features and tracks
+    float2 *feat;
+    float2 *fwd, *back;
+    float *fb;
+    uint8_t *status, *status_fwd;
+    float2 *pair_src, *pair_dst;
+    // detection scratch
+    unsigned long long *cand;
+    int cand_cap;
+    unsigned *hist;
+    unsigned long long *sel;
+    float *det_lam;
+    // fit / smoothing
+    stab_motion *mring;   // STAB_CRING motions
+    float4 *cring;        // STAB_CRING trajectory values
+    float *Minv;          // 6 floats: inverse warp of the frame composed this step
+    // batched frames
+    uint8_t *ring;
+    long long slot_bytes;
+    int ring_len, in_pitch;
+    uint8_t *out;
+    int out_pitch;
+    StreamState *st;
+};
+
+// A work list: stream i owns items [prefix[i], prefix[i+1]).
+struct WorkList {
+    const int *prefix;
+    int n;
+    int total;
+};
+
+__device__ __forceinline__ int wl_stream(const WorkList &wl, int item)
+{
+    int lo = 0, hi = wl.n - 1;
+    while (lo < hi) {
+        int mid = (lo + hi + 1) >> 1;
+        if (__ldg(&wl.prefix[mid]) <= item) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
+}
+
+__device__ __forceinline__ void set_err(StreamState *st, int code)
+{
+    atomicCAS(&st->err, 0, code);
+}
+
+__device__ __forceinline__ int clampi(int v, int lo, int hi) { return v < lo ? lo : (v > hi ? hi : v); }
+
+// Plane element access for the two storage precisions.
+__device__ __forceinline__ float ld1(const float *p) { return __ldg(p); }
+__device__ __forceinline__ float ld1(const __half *p) { return __half2float(__ldg(p)); }
+__device__ __forceinline__ float2 ld2(const float2 *p) { return __ldg(p); }
+__device__ __forceinline__ float2 ld2(const __half2 *p) { return __half22float2(__ldg(p)); }
+
+template <typename T> struct Plane2;
+template <> struct Plane2<float> { typedef float2 type; };
+template <> struct Plane2<__half> { typedef __half2 type; };

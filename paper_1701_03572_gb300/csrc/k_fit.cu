@@ -1,0 +1,383 @@
+// k_fit.cu -- pair compaction, robust rigid / similarity fit (Sec. 4 and 4.1,
+// Eq. 7 restricted to 3 or 4 degrees of freedom) and the averaging-window
+// trajectory smoothing of Sec. 5.1 (offline over a clip, or streaming with a
+// W/2-frame lookahead, the GPU form of the paper's motion-compensation thread).
+//
+// The fit runs one CTA per stream.  Hypothesis h draws its two-point sample
+// from the SplitMix64 hash of (seed, t, h) and is scored by its inlier count;
+// model and residual use one fixed IEEE FP32 operation sequence (explicit
+// _rn intrinsics, no contraction), so counts and the winning hypothesis are
+// reproducible bit for bit.  The closed-form least-squares refit on the
+// winner's inliers uses fixed-order FP32 block reductions.
+#include "kernels.cuh"
+
+namespace {
+
+__device__ __forceinline__ unsigned long long splitmix64(unsigned long long x)
+{
+    unsigned long long z = x + 0x9E3779B97F4A7C15ull;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+
+__device__ __forceinline__ void sample_pair(unsigned long long seed, long long t, int h, int n, int &i, int &j)
+{
+    unsigned long long base = seed ^ ((unsigned long long)(unsigned)t << 32) ^ ((unsigned long long)(unsigned)h << 8);
+    unsigned long long r0 = splitmix64(base), r1 = splitmix64(base ^ 1ull);
+    i = (int)(r0 % (unsigned long long)n);
+    int b = (int)(r1 % (unsigned long long)(n - 1));
+    j = b >= i ? b + 1 : b;
+}
+
+// d = [a -b; b a] s + (m2, m3), through (si, di) and (sj, dj)
+__device__ __forceinline__ bool two_point(float2 si, float2 sj, float2 di, float2 dj, int rigid, float m[4])
+{
+    const float vsx = __fsub_rn(sj.x, si.x), vsy = __fsub_rn(sj.y, si.y);
+    const float vdx = __fsub_rn(dj.x, di.x), vdy = __fsub_rn(dj.y, di.y);
+    const float nn = __fmaf_rn(vsx, vsx, __fmul_rn(vsy, vsy));
+    if (!(nn >= 1.0f)) return false;
+    const float dot = __fmaf_rn(vsx, vdx, __fmul_rn(vsy, vdy));
+    const float crs = __fmaf_rn(vsx, vdy, -__fmul_rn(vsy, vdx));
+    float a, b;
+    if (rigid) {
+        const float rr = __fsqrt_rn(__fmaf_rn(dot, dot, __fmul_rn(crs, crs)));
+        if (!(rr > 0.0f)) return false;
+        a = __fdiv_rn(dot, rr); b = __fdiv_rn(crs, rr);
+    } else {
+        a = __fdiv_rn(dot, nn); b = __fdiv_rn(crs, nn);
+    }
+    const float msx = __fmul_rn(0.5f, __fadd_rn(si.x, sj.x)), msy = __fmul_rn(0.5f, __fadd_rn(si.y, sj.y));
+    const float mdx = __fmul_rn(0.5f, __fadd_rn(di.x, dj.x)), mdy = __fmul_rn(0.5f, __fadd_rn(di.y, dj.y));
+    m[0] = a; m[1] = b;
+    m[2] = __fsub_rn(mdx, __fmaf_rn(a, msx, -__fmul_rn(b, msy)));
+    m[3] = __fsub_rn(mdy, __fmaf_rn(b, msx, __fmul_rn(a, msy)));
+    return true;
+}
+
+__device__ __forceinline__ bool is_inlier(const float m[4], float2 s, float2 d, float tau2)
+{
+    const float px = __fmaf_rn(m[0], s.x, __fmaf_rn(-m[1], s.y, m[2]));
+    const float py = __fmaf_rn(m[1], s.x, __fmaf_rn(m[0], s.y, m[3]));
+    const float ex = __fsub_rn(d.x, px), ey = __fsub_rn(d.y, py);
+    return __fmaf_rn(ex, ex, __fmul_rn(ey, ey)) < tau2;
+}
+
+// Fixed-order sum of NV values over the block (512 threads = 16 warps).
+template <int NV>
+__device__ __forceinline__ void block_sum(float v[NV], float (*sred)[NV])
+{
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+#pragma unroll
+    for (int k = 0; k < NV; ++k)
+        for (int o = 16; o; o >>= 1) v[k] += __shfl_xor_sync(0xffffffffu, v[k], o);
+    __syncthreads();
+    if (lane == 0)
+        for (int k = 0; k < NV; ++k) sred[wid][k] = v[k];
+    __syncthreads();
+    for (int k = 0; k < NV; ++k) {
+        float a = 0.f;
+        for (int i = 0; i < nw; ++i) a += sred[i][k];
+        v[k] = a;
+    }
+    __syncthreads();
+}
+
+// Stable compaction of kept tracks: pairs (src = feature, dst = forward
+// result) in feature order; the kept destinations become the next features.
+__global__ void __launch_bounds__(1024) k_compact(const StreamDev *__restrict__ S, CompactIO io)
+{
+    __shared__ int wsum_[32];
+    const StreamDev &D = S[blockIdx.x];
+    StreamState *st = D.st;
+    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+    const int n = st->t >= 1 ? st->n_feat : 0;
+    // two consecutive features per thread (K <= 2048)
+    const int f0 = 2 * tid;
+    const int k0 = (f0 < n) && D.status[f0], k1 = (f0 + 1 < n) && D.status[f0 + 1];
+    const float2 s0 = k0 ? D.feat[f0] : make_float2(0, 0), s1 = k1 ? D.feat[f0 + 1] : make_float2(0, 0);
+    const float2 d0 = k0 ? D.fwd[f0] : make_float2(0, 0), d1 = k1 ? D.fwd[f0 + 1] : make_float2(0, 0);
+    int c = k0 + k1, incl = c;
+    for (int o = 1; o < 32; o <<= 1) {
+        int v = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += v;
+    }
+    if (lane == 31) wsum_[wid] = incl;
+    __syncthreads();
+    if (wid == 0) {
+        int v = wsum_[lane], x = v;
+        for (int o = 1; o < 32; o <<= 1) {
+            int y = __shfl_up_sync(0xffffffffu, x, o);
+            if (lane >= o) x += y;
+        }
+        wsum_[lane] = x - v;   // exclusive prefix of warp totals
+    }
+    __syncthreads();
+    int pos = wsum_[wid] + incl - c;
+    if (k0) { D.pair_src[pos] = s0; D.pair_dst[pos] = d0; ++pos; }
+    if (k1) { D.pair_src[pos] = s1; D.pair_dst[pos] = d1; }
+    if (io.status_out) {
+        if (f0 < D.K) io.status_out[f0] = (uint8_t)k0;
+        if (f0 + 1 < D.K) io.status_out[f0 + 1] = (uint8_t)k1;
+    }
+    __shared__ int s_total;
+    if (tid == blockDim.x - 1) s_total = wsum_[wid] + incl;
+    __syncthreads();
+    const int m = s_total;
+    for (int i = tid; i < m; i += blockDim.x) {
+        float2 sv = D.pair_src[i], dv = D.pair_dst[i];
+        D.feat[i] = dv;
+        if (io.src_out) io.src_out[i] = sv;
+        if (io.dst_out) io.dst_out[i] = dv;
+    }
+    if (tid == 0) {
+        st->n_pairs = m;
+        st->n_feat = m;
+        if (io.n_out) *io.n_out = m;
+    }
+}
+
+// Streaming smoothing step for frame t with motion m (thread-local; one
+// thread per stream).  C_t = C_{t-1} + m_t; when frame u = t - 1 - W/2 >= 0 is
+// ready: S = mean of C over [max(0, u+1 - (W-1)/2), t], m' = m_{u+1} + (S -
+// C_{u+1}), inverse warp of m'.
+__device__ void inverse_warp(float4 mp, int w, int h, float *Minv)
+{
+    const float cx = 0.5f * (float)(w - 1), cy = 0.5f * (float)(h - 1);
+    const float is = expf(-mp.w);
+    float sn, c;
+    sincosf(mp.z, &sn, &c);
+    const float a00 = is * c, a01 = is * sn, a10 = -is * sn, a11 = is * c;
+    const float ux = cx + mp.x, uy = cy + mp.y;
+    Minv[0] = a00; Minv[1] = a01; Minv[2] = cx - (a00 * ux + a01 * uy);
+    Minv[3] = a10; Minv[4] = a11; Minv[5] = cy - (a10 * ux + a11 * uy);
+}
+
+__device__ __forceinline__ float4 add4(float4 a, float4 b)
+{
+    return make_float4(__fadd_rn(a.x, b.x), __fadd_rn(a.y, b.y), __fadd_rn(a.z, b.z), __fadd_rn(a.w, b.w));
+}
+
+__device__ __forceinline__ float4 corrected(float4 m, float4 S, float4 C)
+{
+    return make_float4(__fadd_rn(m.x, __fsub_rn(S.x, C.x)), __fadd_rn(m.y, __fsub_rn(S.y, C.y)),
+                       __fadd_rn(m.z, __fsub_rn(S.z, C.z)), __fadd_rn(m.w, __fsub_rn(S.w, C.w)));
+}
+
+__device__ __forceinline__ float4 mot4(const stab_motion &m) { return make_float4(m.tx, m.ty, m.theta, m.log_scale); }
+
+__device__ int smooth_step(stab_motion *mring, float4 *cring, long long t, int W, int w, int h, float *Minv)
+{
+    const int CR = STAB_CRING;
+    const float4 Cp = t > 0 ? cring[(t - 1) % CR] : make_float4(0.f, 0.f, 0.f, 0.f);
+    const float4 Ct = add4(Cp, mot4(mring[t % CR]));
+    cring[t % CR] = Ct;
+    const long long u = t - 1 - W / 2;
+    if (u < 0) return -1;
+    const long long j = u + 1;
+    long long lo = j - (W - 1) / 2;
+    if (lo < 0) lo = 0;
+    float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
+    for (long long k = lo; k <= t; ++k) acc = add4(acc, cring[k % CR]);
+    const float cnt = (float)(t - lo + 1);
+    const float4 Sm = make_float4(__fdiv_rn(acc.x, cnt), __fdiv_rn(acc.y, cnt), __fdiv_rn(acc.z, cnt),
+                                  __fdiv_rn(acc.w, cnt));
+    inverse_warp(corrected(mot4(mring[j % CR]), Sm, cring[j % CR]), w, h, Minv);
+    return (int)u;
+}
+
+__global__ void __launch_bounds__(512) k_fit(const StreamDev *__restrict__ S, FitIO io, int streaming)
+{
+    __shared__ float2 ss[STAB_MAXK], sd[STAB_MAXK];
+    __shared__ int wbs[16], wbh[16];
+    __shared__ int s_best, s_bh;
+    __shared__ float sred[16][5];
+    const StreamDev &D = S[blockIdx.x];
+    StreamState *st = D.st;
+    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5, nwarps = blockDim.x >> 5;
+    const long long t = io.src ? io.t : st->t;
+    int n = io.src ? *io.n : (t >= 1 ? st->n_pairs : 0);
+    n = min(max(n, 0), D.K);
+    const float2 *src = io.src ? io.src : D.pair_src;
+    const float2 *dst = io.src ? io.dst : D.pair_dst;
+    const int rigid = io.src ? io.rigid : D.rigid;
+    const float cx = __fmul_rn(0.5f, (float)(D.w - 1)), cy = __fmul_rn(0.5f, (float)(D.h - 1));
+    for (int i = tid; i < n; i += blockDim.x) {
+        float2 a = src[i], b = dst[i];
+        ss[i] = make_float2(__fsub_rn(a.x, cx), __fsub_rn(a.y, cy));
+        sd[i] = make_float2(__fsub_rn(b.x, cx), __fsub_rn(b.y, cy));
+    }
+    __syncthreads();
+    stab_motion out;
+    out.tx = out.ty = out.theta = out.log_scale = 0.f;
+    out.inliers = 0;
+    out.n_tracks = n;
+    out.rms = 0.f;
+    out.flags = (!io.src && st->due) ? STAB_FLAG_DETECTED : 0;
+    bool skip = (t < 1) || n < max(2, D.min_fit);
+    if (!skip) {
+        int best = -1, bh = 0x7fffffff;
+        for (int hh = wid; hh < D.H; hh += nwarps) {
+            int i, j;
+            sample_pair(D.seed, t, hh, n, i, j);
+            float m[4];
+            int cnt = -1;
+            if (two_point(ss[i], ss[j], sd[i], sd[j], rigid, m)) {
+                int c = 0;
+                for (int k = lane; k < n; k += 32) c += is_inlier(m, ss[k], sd[k], D.tau2);
+                cnt = __reduce_add_sync(0xffffffffu, c);
+            }
+            if (cnt > best) { best = cnt; bh = hh; }
+        }
+        if (lane == 0) { wbs[wid] = best; wbh[wid] = bh; }
+        __syncthreads();
+        if (tid == 0) {
+            int b = -1, h = 0x7fffffff;
+            for (int k = 0; k < nwarps; ++k)
+                if (wbs[k] > b || (wbs[k] == b && wbh[k] < h)) { b = wbs[k]; h = wbh[k]; }
+            s_best = b; s_bh = h;
+        }
+        __syncthreads();
+        if (s_best < 2) skip = true;
+        if (!skip) {
+            int i, j;
+            sample_pair(D.seed, t, s_bh, n, i, j);
+            float m[4];
+            two_point(ss[i], ss[j], sd[i], sd[j], rigid, m);
+            float v[5] = {0.f, 0.f, 0.f, 0.f, 0.f};
+            for (int k = tid; k < n; k += blockDim.x)
+                if (is_inlier(m, ss[k], sd[k], D.tau2)) {
+                    v[0] += 1.f; v[1] += ss[k].x; v[2] += ss[k].y; v[3] += sd[k].x; v[4] += sd[k].y;
+                }
+            block_sum<5>(v, sred);
+            const float ni = v[0];
+            const float msx = v[1] / ni, msy = v[2] / ni, mdx = v[3] / ni, mdy = v[4] / ni;
+            float u[3] = {0.f, 0.f, 0.f};
+            for (int k = tid; k < n; k += blockDim.x)
+                if (is_inlier(m, ss[k], sd[k], D.tau2)) {
+                    const float x0 = ss[k].x - msx, x1 = ss[k].y - msy;
+                    const float y0 = sd[k].x - mdx, y1 = sd[k].y - mdy;
+                    u[0] += x0 * y0 + x1 * y1;
+                    u[1] += x0 * y1 - x1 * y0;
+                    u[2] += x0 * x0 + x1 * x1;
+                }
+            float u5[5] = {u[0], u[1], u[2], 0.f, 0.f};
+            block_sum<5>(u5, sred);
+            if (!(u5[2] > 0.f)) {
+                skip = true;
+            } else {
+                const float th = atan2f(u5[1], u5[0]);
+                const float sc = rigid ? 1.f : sqrtf(u5[0] * u5[0] + u5[1] * u5[1]) / u5[2];
+                float sn, c;
+                sincosf(th, &sn, &c);
+                const float tx = mdx - sc * (c * msx - sn * msy);
+                const float ty = mdy - sc * (sn * msx + c * msy);
+                float e[5] = {0.f, 0.f, 0.f, 0.f, 0.f};
+                for (int k = tid; k < n; k += blockDim.x)
+                    if (is_inlier(m, ss[k], sd[k], D.tau2)) {
+                        const float px = sc * (c * ss[k].x - sn * ss[k].y) + tx;
+                        const float py = sc * (sn * ss[k].x + c * ss[k].y) + ty;
+                        e[0] += (sd[k].x - px) * (sd[k].x - px) + (sd[k].y - py) * (sd[k].y - py);
+                    }
+                block_sum<5>(e, sred);
+                out.tx = tx; out.ty = ty; out.theta = th; out.log_scale = logf(sc);
+                out.inliers = (int)ni;
+                out.rms = sqrtf(e[0] / ni);
+            }
+        }
+    }
+    if (skip && t >= 1) out.flags |= STAB_FLAG_SKIPPED;
+    if (tid == 0) {
+        if (io.out) *io.out = out;
+        if (!io.src) {
+            D.mring[t % STAB_CRING] = out;
+            if (streaming) st->out_frame = smooth_step(D.mring, D.cring, t, D.W, D.w, D.h, D.Minv);
+        }
+    }
+}
+
+// Offline smoothing in three launches (no scratch beyond the outputs):
+// (1) trajectory C into the Minv buffer, (2) m' from C, (3) Minv from m'.
+__global__ void k_smooth_c(const stab_motion *m, int T, float *Cbuf)
+{
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    float4 C = make_float4(0.f, 0.f, 0.f, 0.f);
+    for (int t = 0; t < T; ++t) {
+        C = add4(C, mot4(m[t]));
+        Cbuf[6 * t + 0] = C.x; Cbuf[6 * t + 1] = C.y; Cbuf[6 * t + 2] = C.z; Cbuf[6 * t + 3] = C.w;
+    }
+}
+
+__global__ void k_smooth_mp(const stab_motion *m, int T, int W, const float *Cbuf, float *mprime)
+{
+    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < T; t += gridDim.x * blockDim.x) {
+        int lo = t - (W - 1) / 2, hi = t + W / 2;
+        if (lo < 0) lo = 0;
+        if (hi > T - 1) hi = T - 1;
+        float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
+        for (int k = lo; k <= hi; ++k) acc = add4(acc, make_float4(Cbuf[6 * k], Cbuf[6 * k + 1], Cbuf[6 * k + 2], Cbuf[6 * k + 3]));
+        const float cnt = (float)(hi - lo + 1);
+        const float4 Sm = make_float4(__fdiv_rn(acc.x, cnt), __fdiv_rn(acc.y, cnt), __fdiv_rn(acc.z, cnt),
+                                      __fdiv_rn(acc.w, cnt));
+        const float4 Ct = make_float4(Cbuf[6 * t], Cbuf[6 * t + 1], Cbuf[6 * t + 2], Cbuf[6 * t + 3]);
+        const float4 mp = corrected(mot4(m[t]), Sm, Ct);
+        mprime[4 * t + 0] = mp.x; mprime[4 * t + 1] = mp.y; mprime[4 * t + 2] = mp.z; mprime[4 * t + 3] = mp.w;
+    }
+}
+
+__global__ void k_smooth_minv(const float *mprime, int T, int w, int h, float *Minv)
+{
+    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < T; t += gridDim.x * blockDim.x)
+        inverse_warp(make_float4(mprime[4 * t], mprime[4 * t + 1], mprime[4 * t + 2], mprime[4 * t + 3]), w, h,
+                     Minv + 6 * t);
+}
+
+__global__ void k_smooth_push(const StreamDev *__restrict__ S, long long t, const stab_motion *m, float *Minv,
+                              int *ready)
+{
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    const StreamDev &D = S[0];
+    D.mring[t % STAB_CRING] = *m;
+    float M[6];
+    int u = smooth_step(D.mring, D.cring, t, D.W, D.w, D.h, M);
+    if (u >= 0)
+        for (int k = 0; k < 6; ++k) Minv[k] = M[k];
+    *ready = u;
+}
+
+__global__ void k_advance(const StreamDev *__restrict__ S, int n)
+{
+    int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s < n) S[s].st->t += 1;
+}
+
+}  // namespace
+
+void launch_compact(const Launch &L, const StreamDev *S, int n, CompactIO io)
+{
+    k_compact<<<n, 1024, 0, L.stream>>>(S, io);
+}
+
+void launch_fit(const Launch &L, const StreamDev *S, int n, FitIO io, int streaming)
+{
+    k_fit<<<n, 512, 0, L.stream>>>(S, io, streaming);
+}
+
+void launch_smooth_offline(const Launch &L, const stab_motion *m, int T, int W, int w, int h, float *mprime,
+                           float *Minv)
+{
+    k_smooth_c<<<1, 32, 0, L.stream>>>(m, T, Minv);
+    k_smooth_mp<<<(T + 255) / 256, 256, 0, L.stream>>>(m, T, W, Minv, mprime);
+    k_smooth_minv<<<(T + 255) / 256, 256, 0, L.stream>>>(mprime, T, w, h, Minv);
+}
+
+void launch_smooth_push(const Launch &L, const StreamDev *S, long long t, const stab_motion *m, float *Minv,
+                        int *ready)
+{
+    k_smooth_push<<<1, 32, 0, L.stream>>>(S, t, m, Minv, ready);
+}
+
+void launch_advance(const Launch &L, const StreamDev *S, int n)
+{
+    k_advance<<<(n + 63) / 64, 64, 0, L.stream>>>(S, n);
+}

@@ -1,0 +1,230 @@
+// k_pyramid.cu -- Gaussian pyramid (Sec. 3.2; Burt-Adelson REDUCE with the
+// generating kernel [1 4 6 4 1] / 16) and the I / Ix / Iy planes the tracker
+// reads (central differences, replicated border), in FP32 or FP16 storage.
+//
+// Both kernels are persistent grid-stride loops over a work list of 64 x 16
+// tiles spanning every stream of the batch.  A tile is staged in shared memory
+// with its halo; each thread then emits 4 consecutive pixels with vector
+// stores (uchar4 for the u8 level, float4 / uint2 for I, 2 x float4 / uint4
+// for the gradient pair).  The integer blur is exact, so every level is
+// bit-identical to the definition; FP16 holds the integers and half-integers
+// of I and its central differences exactly, so both storages carry the same
+// values.
+#include "kernels.cuh"
+
+namespace {
+
+__device__ __forceinline__ int reflect101(int i, int n)
+{
+    if (n == 1) return 0;
+    while (i < 0 || i >= n) {
+        if (i < 0) i = -i;
+        if (i >= n) i = 2 * n - 2 - i;
+    }
+    return i;
+}
+
+__device__ __forceinline__ void store_I(float *p, const float v[4])
+{
+    *reinterpret_cast<float4 *>(p) = make_float4(v[0], v[1], v[2], v[3]);
+}
+__device__ __forceinline__ void store_I(__half *p, const float v[4])
+{
+    __half2 a = __floats2half2_rn(v[0], v[1]), b = __floats2half2_rn(v[2], v[3]);
+    uint2 u;
+    u.x = *reinterpret_cast<unsigned *>(&a);
+    u.y = *reinterpret_cast<unsigned *>(&b);
+    *reinterpret_cast<uint2 *>(p) = u;
+}
+__device__ __forceinline__ void store_G(float2 *p, const float gx[4], const float gy[4])
+{
+    float4 *q = reinterpret_cast<float4 *>(p);
+    q[0] = make_float4(gx[0], gy[0], gx[1], gy[1]);
+    q[1] = make_float4(gx[2], gy[2], gx[3], gy[3]);
+}
+__device__ __forceinline__ void store_G(__half2 *p, const float gx[4], const float gy[4])
+{
+    uint4 u;
+    __half2 h0 = __floats2half2_rn(gx[0], gy[0]), h1 = __floats2half2_rn(gx[1], gy[1]);
+    __half2 h2 = __floats2half2_rn(gx[2], gy[2]), h3 = __floats2half2_rn(gx[3], gy[3]);
+    u.x = *reinterpret_cast<unsigned *>(&h0);
+    u.y = *reinterpret_cast<unsigned *>(&h1);
+    u.z = *reinterpret_cast<unsigned *>(&h2);
+    u.w = *reinterpret_cast<unsigned *>(&h3);
+    *reinterpret_cast<uint4 *>(p) = u;
+}
+
+// Emit 4 pixels (x..x+3, y) of level l from a 3 x 6 neighbourhood v (rows
+// y-1..y+1, columns x-1..x+4, already border-replicated).
+template <typename PT>
+__device__ __forceinline__ void emit4(const StreamDev &D, int slot, int l, int x, int y, const int v[3][6])
+{
+    typedef typename Plane2<PT>::type PT2;
+    size_t o = (size_t)y * D.lp[l] + x;
+    *reinterpret_cast<uchar4 *>(D.u8[slot][l] + o) =
+        make_uchar4((uint8_t)v[1][1], (uint8_t)v[1][2], (uint8_t)v[1][3], (uint8_t)v[1][4]);
+    float I[4], gx[4], gy[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        I[k] = (float)v[1][k + 1];
+        gx[k] = 0.5f * (float)(v[1][k + 2] - v[1][k]);
+        gy[k] = 0.5f * (float)(v[2][k + 1] - v[0][k + 1]);
+    }
+    store_I(reinterpret_cast<PT *>(D.pI[slot][l]) + o, I);
+    store_G(reinterpret_cast<PT2 *>(D.pG[slot][l]) + o, gx, gy);
+}
+
+// Level 0: frame (gray, or RGB converted to luma) -> u8 level 0 + planes.
+template <typename PT>
+__global__ void __launch_bounds__(256) k_level0(const StreamDev *__restrict__ S, WorkList wl, FrameSrc ov)
+{
+    __shared__ uint8_t sm[STAB_TH + 2][STAB_TW + 4];
+    for (int item = blockIdx.x; item < wl.total; item += gridDim.x) {
+        const int s = wl_stream(wl, item);
+        const StreamDev &D = S[s];
+        const int local = item - __ldg(&wl.prefix[s]);
+        const uint8_t *src;
+        int pitch, C, slot;
+        if (ov.ptr) {
+            src = ov.ptr; pitch = ov.pitch; C = ov.channels; slot = ov.slot;
+        } else {
+            long long t = D.st->t;
+            slot = (int)(t & 1);
+            src = D.ring + (t % D.ring_len) * D.slot_bytes;
+            pitch = D.in_pitch; C = D.C;
+        }
+        const int w = D.w, h = D.h;
+        const int tx = (w + STAB_TW - 1) / STAB_TW;
+        const int x0 = (local % tx) * STAB_TW, y0 = (local / tx) * STAB_TH;
+        for (int i = threadIdx.x; i < (STAB_TH + 2) * (STAB_TW + 2); i += blockDim.x) {
+            int ly = i / (STAB_TW + 2), lx = i - ly * (STAB_TW + 2);
+            int gx = clampi(x0 - 1 + lx, 0, w - 1), gy = clampi(y0 - 1 + ly, 0, h - 1);
+            const uint8_t *p = src + (size_t)gy * pitch + (size_t)gx * C;
+            int v;
+            if (C == 1) v = __ldg(p);
+            else v = (77 * __ldg(p) + 150 * __ldg(p + 1) + 29 * __ldg(p + 2) + 128) >> 8;
+            sm[ly][lx] = (uint8_t)v;
+        }
+        __syncthreads();
+        const int row = threadIdx.x >> 4, c4 = (threadIdx.x & 15) * 4;
+        const int y = y0 + row, x = x0 + c4;
+        if (y < h && x < w) {
+            int v[3][6];
+#pragma unroll
+            for (int r = 0; r < 3; ++r)
+#pragma unroll
+                for (int c = 0; c < 6; ++c) v[r][c] = sm[row + r][c4 + c];
+            emit4<PT>(D, slot, 0, x, y, v);
+        }
+        __syncthreads();
+    }
+}
+
+// Level l >= 1 from level l-1: REDUCE over a tile of 64 x 16 outputs plus a
+// one-pixel ring (needed for the central differences of this level).
+template <typename PT>
+__global__ void __launch_bounds__(256) k_pyr_down(const StreamDev *__restrict__ S, WorkList wl, int l, int slot_ov)
+{
+    constexpr int OW = STAB_TW + 2, OH = STAB_TH + 2;   // outputs with ring: 66 x 18
+    constexpr int IW = 2 * OW + 3, IH = 2 * OH + 3;     // input footprint: 135 x 39
+    __shared__ uint8_t sin_[IH][IW + 1];
+    __shared__ uint16_t shs[IH][OW];
+    __shared__ uint8_t sout[OH][OW + 2];
+    for (int item = blockIdx.x; item < wl.total; item += gridDim.x) {
+        const int s = wl_stream(wl, item);
+        const StreamDev &D = S[s];
+        const int local = item - __ldg(&wl.prefix[s]);
+        const int slot = slot_ov >= 0 ? slot_ov : (int)(D.st->t & 1);
+        const uint8_t *in = D.u8[slot][l - 1];
+        const int wi = D.lw[l - 1], hi = D.lh[l - 1], pi = D.lp[l - 1];
+        const int wo = D.lw[l], ho = D.lh[l];
+        const int tx = (wo + STAB_TW - 1) / STAB_TW;
+        const int x0 = (local % tx) * STAB_TW, y0 = (local / tx) * STAB_TH;
+        const int ix0 = 2 * x0 - 4, iy0 = 2 * y0 - 4;
+        for (int i = threadIdx.x; i < IH * IW; i += blockDim.x) {
+            int r = i / IW, c = i - r * IW;
+            sin_[r][c] = __ldg(in + (size_t)reflect101(iy0 + r, hi) * pi + reflect101(ix0 + c, wi));
+        }
+        __syncthreads();
+        for (int i = threadIdx.x; i < IH * OW; i += blockDim.x) {
+            int r = i / OW, c = i - r * OW;
+            const uint8_t *q = &sin_[r][2 * c];
+            shs[r][c] = (uint16_t)(q[0] + 4 * q[1] + 6 * q[2] + 4 * q[3] + q[4]);
+        }
+        __syncthreads();
+        for (int i = threadIdx.x; i < OH * OW; i += blockDim.x) {
+            int r = i / OW, c = i - r * OW;
+            int sum = shs[2 * r][c] + 4 * shs[2 * r + 1][c] + 6 * shs[2 * r + 2][c] + 4 * shs[2 * r + 3][c] +
+                      shs[2 * r + 4][c];
+            sout[r][c] = (uint8_t)((sum + 128) >> 8);
+        }
+        __syncthreads();
+        const int row = threadIdx.x >> 4, c4 = (threadIdx.x & 15) * 4;
+        const int y = y0 + row, x = x0 + c4;
+        if (y < ho && x < wo) {
+            int v[3][6];
+#pragma unroll
+            for (int r = 0; r < 3; ++r) {
+                int sr = clampi(y + r - 1, 0, ho - 1) - (y0 - 1);
+#pragma unroll
+                for (int c = 0; c < 6; ++c) v[r][c] = sout[sr][clampi(x + c - 1, 0, wo - 1) - (x0 - 1)];
+            }
+            emit4<PT>(D, slot, l, x, y, v);
+        }
+        __syncthreads();
+    }
+}
+
+template <typename PT>
+__global__ void k_plane_f32(const StreamDev *__restrict__ S, int slot, int l, float *I, float *Ix, float *Iy)
+{
+    typedef typename Plane2<PT>::type PT2;
+    const StreamDev &D = S[0];
+    const int w = D.lw[l], h = D.lh[l];
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < w * h; i += gridDim.x * blockDim.x) {
+        int y = i / w, x = i - y * w;
+        size_t o = (size_t)y * D.lp[l] + x;
+        if (I) I[i] = ld1(reinterpret_cast<const PT *>(D.pI[slot][l]) + o);
+        float2 g = ld2(reinterpret_cast<const PT2 *>(D.pG[slot][l]) + o);
+        if (Ix) Ix[i] = g.x;
+        if (Iy) Iy[i] = g.y;
+    }
+}
+
+}  // namespace
+
+void launch_level0(const Launch &L, int prec, const StreamDev *S, WorkList wl, FrameSrc ov)
+{
+    int g = grid_for(L, wl.total, prec ? occ_level0_h() : occ_level0_f());
+    if (prec) k_level0<__half><<<g, 256, 0, L.stream>>>(S, wl, ov);
+    else k_level0<float><<<g, 256, 0, L.stream>>>(S, wl, ov);
+}
+
+void launch_pyr_down(const Launch &L, int prec, const StreamDev *S, WorkList wl, int l, int slot_ov)
+{
+    int g = grid_for(L, wl.total, prec ? occ_pyr_h() : occ_pyr_f());
+    if (prec) k_pyr_down<__half><<<g, 256, 0, L.stream>>>(S, wl, l, slot_ov);
+    else k_pyr_down<float><<<g, 256, 0, L.stream>>>(S, wl, l, slot_ov);
+}
+
+void launch_plane_f32(const Launch &L, int prec, const StreamDev *S, int slot, int l, float *I, float *Ix, float *Iy)
+{
+    if (prec) k_plane_f32<__half><<<4 * L.sms, 256, 0, L.stream>>>(S, slot, l, I, Ix, Iy);
+    else k_plane_f32<float><<<4 * L.sms, 256, 0, L.stream>>>(S, slot, l, I, Ix, Iy);
+}
+
+#define OCC_FN(name, kern)                                                        \
+    int name()                                                                    \
+    {                                                                             \
+        static int v = 0;                                                         \
+        if (!v) {                                                                 \
+            if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, kern, 256, 0) != \
+                cudaSuccess || v < 1)                                             \
+                v = 1;                                                            \
+        }                                                                         \
+        return v;                                                                 \
+    }
+OCC_FN(occ_level0_f, k_level0<float>)
+OCC_FN(occ_level0_h, k_level0<__half>)
+OCC_FN(occ_pyr_f, k_pyr_down<float>)
+OCC_FN(occ_pyr_h, k_pyr_down<__half>)

@@ -1,0 +1,107 @@
+// kernels.cuh -- launch interface between the host runtime and the kernels.
+#pragma once
+
+#include "common.cuh"
+
+struct Launch {
+    cudaStream_t stream;
+    int sms;
+};
+
+static inline int grid_for(const Launch &L, int total, int occ)
+{
+    long long g = (long long)L.sms * (occ < 1 ? 1 : occ);
+    if (g > total) g = total;
+    if (g < 1) g = 1;
+    return (int)g;
+}
+
+// Source of level 0: an explicit frame for stream 0 (single-stream calls,
+// ptr != NULL) or the stream's input ring slot t % ring (batched step).
+struct FrameSrc {
+    const uint8_t *ptr;
+    int pitch, channels, slot;
+};
+
+// Tracker I/O: explicit points and outputs (single-stream test hook) or the
+// stream's own feature set and track buffers (pts == NULL).
+struct LkIO {
+    const float2 *pts;
+    int n;
+    int slot_prev;
+    float2 *fwd, *back;
+    float *fb;
+    uint8_t *status, *status_fwd;
+};
+
+// Detection: explicit gray frame (gray != NULL, stream 0) or the previous
+// frame's level 0 of each stream when its detection is due.
+struct DetIO {
+    const uint8_t *gray;
+    int pitch;
+    float2 *pts_out;
+    float *lam_out;
+    int *n_out, *ncand_out;
+};
+
+struct CompactIO {
+    float2 *src_out, *dst_out;
+    int *n_out;
+    uint8_t *status_out;
+};
+
+struct FitIO {
+    const float2 *src, *dst;
+    const int *n;
+    int rigid;
+    long long t;
+    stab_motion *out;
+};
+
+struct WarpIO {
+    const uint8_t *src;
+    int sp;
+    uint8_t *dst;
+    int dp, C;
+    const float *Minv;
+};
+
+void launch_level0(const Launch &L, int prec, const StreamDev *S, WorkList wl, FrameSrc ov);
+void launch_pyr_down(const Launch &L, int prec, const StreamDev *S, WorkList wl, int l, int slot_ov);
+void launch_plane_f32(const Launch &L, int prec, const StreamDev *S, int slot, int l, float *I, float *Ix,
+                      float *Iy);
+int occ_level0_f();
+int occ_level0_h();
+int occ_pyr_f();
+int occ_pyr_h();
+
+// Occupancy queries and attributes, done once outside any graph capture.
+void warm_detect();
+void warm_warp();
+void warm_lk();
+
+void launch_begin(const Launch &L, const StreamDev *S, int n, long long t_ov, int force_due);
+void launch_response(const Launch &L, const StreamDev *S, WorkList wl, DetIO io);
+void launch_filter(const Launch &L, const StreamDev *S, WorkList wl);
+void launch_select(const Launch &L, const StreamDev *S, int n, DetIO io);
+
+void launch_lk(const Launch &L, int prec, int r, int wpf, const StreamDev *S, WorkList wl, LkIO io);
+
+void launch_compact(const Launch &L, const StreamDev *S, int n, CompactIO io);
+void launch_fit(const Launch &L, const StreamDev *S, int n, FitIO io, int streaming);
+void launch_smooth_offline(const Launch &L, const stab_motion *m, int T, int W, int w, int h, float *mprime,
+                           float *Minv);
+void launch_smooth_push(const Launch &L, const StreamDev *S, long long t, const stab_motion *m, float *Minv,
+                        int *ready);
+void launch_advance(const Launch &L, const StreamDev *S, int n);
+
+void launch_warp(const Launch &L, const StreamDev *S, WorkList wl, WarpIO io);
+
+void launch_charb_forward(const Launch &L, const float *It, const float *Ip, int w, int h, int P,
+                          const float *theta, int margin, float eps, float *loss, float *dtheta, float *gn,
+                          float *partials);
+void launch_charb_backward_image(const Launch &L, const float *It, const float *Ip, int w, int h, int P,
+                                 const float *theta, int margin, float eps, const float *gout, float *dIt,
+                                 float *dIp);
+void launch_charb_gn_update(const Launch &L, int P, const float *gn, float *theta);
+int charb_partials_per_pair(int w, int h, int margin);

@@ -1,0 +1,668 @@
+// runtime.cu -- host side of the C ABI declared in include/stab.h.
+//
+// A Pipeline holds n streams: one device arena carved into every stream's
+// buffers, the per-stream descriptors (StreamDev) in device memory, and the
+// work lists of each kernel.  The single-stream context is a Pipeline with
+// n = 1 driven call by call; the batch enqueues the whole frame step once
+// into a CUDA graph and replays it (the per-step frame index lives on the
+// device, so the graph never changes).
+#include <algorithm>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "kernels.cuh"
+
+namespace {
+
+const char *kVersion = "gb300-stab 0.1 (sm_103a)";
+
+struct Pipeline {
+    int n = 0;
+    int prec = 0, rmax = 10, Lmax = 1, sms = 0, ring = 1;
+    std::vector<StreamDev> hs;
+    std::vector<stab_params> P;
+    StreamDev *ds = nullptr;
+    char *arena = nullptr;
+    size_t arena_bytes = 0;
+    int *prefix = nullptr;
+    WorkList wl_l0{}, wl_pyr[STAB_MAXL]{}, wl_resp{}, wl_filter{}, wl_lk{}, wl_warp{};
+    std::string err;
+    cudaStream_t last = nullptr;
+    cudaStream_t cap = nullptr;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t gexec = nullptr;
+    long long t_host = 0;
+
+    ~Pipeline()
+    {
+        if (gexec) cudaGraphExecDestroy(gexec);
+        if (graph) cudaGraphDestroy(graph);
+        if (cap) cudaStreamDestroy(cap);
+        if (prefix) cudaFree(prefix);
+        if (ds) cudaFree(ds);
+        if (arena) cudaFree(arena);
+    }
+};
+
+inline int up(int v, int a) { return (v + a - 1) / a * a; }
+inline int tiles(int w, int h) { return ((w + STAB_TW - 1) / STAB_TW) * ((h + STAB_TH - 1) / STAB_TH); }
+
+stab_status fail(std::string &err, stab_status code, const std::string &msg)
+{
+    err = msg;
+    return code;
+}
+
+stab_status cuda_check(std::string &err, const char *what)
+{
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) {
+        err = std::string(what) + ": " + cudaGetErrorString(e);
+        return STAB_ERR_CUDA;
+    }
+    return STAB_OK;
+}
+
+stab_status check_params(const stab_params &p, int w, int h, std::string &err)
+{
+    if (w < 16 || h < 16 || w > 8192 || h > 8192) return fail(err, STAB_ERR_INVALID_ARG, "frame size out of [16, 8192]");
+    if (p.max_corners < 1 || p.max_corners > STAB_MAXK) return fail(err, STAB_ERR_INVALID_ARG, "max_corners out of [1, 2048]");
+    if (p.levels < 1 || p.levels > STAB_MAXL) return fail(err, STAB_ERR_INVALID_ARG, "levels out of [1, 8]");
+    if (p.win_radius < 1 || p.win_radius > STAB_MAXR) return fail(err, STAB_ERR_INVALID_ARG, "win_radius out of [1, 12]");
+    if (p.max_iters < 1 || p.max_iters > 1000) return fail(err, STAB_ERR_INVALID_ARG, "max_iters out of [1, 1000]");
+    if (!(p.eps >= 0.f) || !(p.min_eig >= 0.f) || !(p.quality >= 0.f) || !(p.fb_thresh >= 0.f) ||
+        !(p.inlier_thresh > 0.f))
+        return fail(err, STAB_ERR_INVALID_ARG, "negative threshold");
+    if (p.redetect_period < 1) return fail(err, STAB_ERR_INVALID_ARG, "redetect_period < 1");
+    if (p.hypotheses < 1 || p.hypotheses > 1 << 20) return fail(err, STAB_ERR_INVALID_ARG, "hypotheses out of range");
+    if (p.smooth_window < 1 || p.smooth_window >= STAB_CRING) return fail(err, STAB_ERR_INVALID_ARG, "smooth_window out of [1, 63]");
+    if (p.model != STAB_RIGID && p.model != STAB_SIMILARITY) return fail(err, STAB_ERR_INVALID_ARG, "bad model");
+    if (p.precision != STAB_FP32 && p.precision != STAB_FP16_STORAGE) return fail(err, STAB_ERR_INVALID_ARG, "bad precision");
+    int lw = w, lh = h;
+    for (int l = 1; l < p.levels; ++l) { lw = (lw + 1) / 2; lh = (lh + 1) / 2; }
+    if (lw < 2 || lh < 2) return fail(err, STAB_ERR_INVALID_ARG, "too many levels for the frame size");
+    int mx = p.roi_margin_x < 0 ? std::max(w / 10, p.win_radius + 2) : p.roi_margin_x;
+    int my = p.roi_margin_y < 0 ? std::max(h / 10, p.win_radius + 2) : p.roi_margin_y;
+    if (mx < 3 || my < 3 || w - 2 * mx < 1 || h - 2 * my < 1) return fail(err, STAB_ERR_INVALID_ARG, "bad ROI margins");
+    return STAB_OK;
+}
+
+// Build a pipeline; C[i] = channels of stream i's ring frames (0 = no ring).
+stab_status build(Pipeline &pp, int n, const int *w, const int *h, const int *C, const stab_params *P, int ring)
+{
+    pp.n = n;
+    pp.ring = std::max(ring, 1);
+    pp.P.assign(P, P + n);
+    pp.hs.assign(n, StreamDev{});
+    pp.prec = P[0].precision;
+    for (int i = 0; i < n; ++i) {
+        stab_status s = check_params(P[i], w[i], h[i], pp.err);
+        if (s) return s;
+        if (P[i].precision != pp.prec) return fail(pp.err, STAB_ERR_INVALID_ARG, "all streams of a batch share one precision");
+        pp.rmax = std::max(pp.rmax, P[i].win_radius);
+        pp.Lmax = std::max(pp.Lmax, P[i].levels);
+    }
+    cudaDeviceGetAttribute(&pp.sms, cudaDevAttrMultiProcessorCount, 0);
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&pp.sms, cudaDevAttrMultiProcessorCount, dev);
+    const size_t psz = pp.prec ? 2 : 4;
+    // two passes: size, then carve
+    for (int pass = 0; pass < 2; ++pass) {
+        size_t off = 0;
+        auto take = [&](size_t bytes) -> char * {
+            off = (off + 255) & ~size_t(255);
+            char *p = pass ? pp.arena + off : nullptr;
+            off += bytes;
+            return p;
+        };
+        for (int i = 0; i < n; ++i) {
+            StreamDev &D = pp.hs[i];
+            const stab_params &p = P[i];
+            D.w = w[i]; D.h = h[i]; D.C = C[i] ? C[i] : 1; D.L = p.levels; D.K = p.max_corners;
+            D.lw[0] = w[i]; D.lh[0] = h[i];
+            for (int l = 1; l < D.L; ++l) { D.lw[l] = (D.lw[l - 1] + 1) / 2; D.lh[l] = (D.lh[l - 1] + 1) / 2; }
+            for (int l = 0; l < D.L; ++l) D.lp[l] = up(D.lw[l], 64);
+            D.r = p.win_radius; D.max_iters = p.max_iters; D.period = p.redetect_period;
+            D.min_tracks = p.min_tracks; D.min_fit = p.min_fit; D.H = p.hypotheses;
+            D.rigid = p.model == STAB_RIGID; D.W = p.smooth_window; D.prec = p.precision;
+            D.eps2 = p.eps * p.eps; D.min_eig = p.min_eig; D.quality = p.quality;
+            D.fb2 = p.fb_thresh * p.fb_thresh;
+            {
+                float tau = p.inlier_thresh;
+                volatile float t2 = tau * tau;   // the FP32 product, as the oracle forms it
+                D.tau2 = t2;
+            }
+            D.seed = p.seed;
+            int mx = p.roi_margin_x < 0 ? std::max(w[i] / 10, p.win_radius + 2) : p.roi_margin_x;
+            int my = p.roi_margin_y < 0 ? std::max(h[i] / 10, p.win_radius + 2) : p.roi_margin_y;
+            D.roi_x0 = mx; D.roi_y0 = my; D.roi_x1 = w[i] - mx; D.roi_y1 = h[i] - my;
+            for (int s = 0; s < 2; ++s)
+                for (int l = 0; l < D.L; ++l) {
+                    size_t px = (size_t)D.lp[l] * D.lh[l];
+                    D.u8[s][l] = (uint8_t *)take(px);
+                    D.pI[s][l] = take(px * psz);
+                    D.pG[s][l] = take(px * psz * 2);
+                }
+            const size_t K = (size_t)D.K;
+            D.feat = (float2 *)take(K * 8);
+            D.fwd = (float2 *)take(K * 8);
+            D.back = (float2 *)take(K * 8);
+            D.fb = (float *)take(K * 4);
+            D.status = (uint8_t *)take(K);
+            D.status_fwd = (uint8_t *)take(K);
+            D.pair_src = (float2 *)take(K * 8);
+            D.pair_dst = (float2 *)take(K * 8);
+            D.cand_cap = ((D.roi_x1 - D.roi_x0 + 1) / 2) * ((D.roi_y1 - D.roi_y0 + 1) / 2) + 64;
+            D.cand = (unsigned long long *)take((size_t)D.cand_cap * 8);
+            D.sel = (unsigned long long *)take((size_t)D.cand_cap * 8);
+            D.hist = (unsigned *)take(STAB_HBINS * 4);
+            D.det_lam = (float *)take(K * 4);
+            D.mring = (stab_motion *)take(STAB_CRING * sizeof(stab_motion));
+            D.cring = (float4 *)take(STAB_CRING * sizeof(float4));
+            D.Minv = (float *)take(8 * 4);
+            D.ring_len = pp.ring;
+            D.in_pitch = up(D.w * D.C, 64);
+            D.slot_bytes = (long long)D.in_pitch * D.h;
+            D.out_pitch = D.in_pitch;
+            if (C[i]) {
+                D.ring = (uint8_t *)take((size_t)D.slot_bytes * pp.ring);
+                D.out = (uint8_t *)take((size_t)D.slot_bytes);
+            } else {
+                D.ring = nullptr;
+                D.out = nullptr;
+            }
+            D.st = (StreamState *)take(sizeof(StreamState));
+        }
+        if (!pass) {
+            pp.arena_bytes = off;
+            if (cudaMalloc(&pp.arena, off) != cudaSuccess) {
+                cudaGetLastError();
+                pp.arena = nullptr;
+                return fail(pp.err, STAB_ERR_OOM, "cudaMalloc of " + std::to_string(off) + " bytes failed");
+            }
+            if (cudaMemset(pp.arena, 0, off) != cudaSuccess) return cuda_check(pp.err, "cudaMemset");
+        }
+    }
+    if (cudaMalloc(&pp.ds, sizeof(StreamDev) * n) != cudaSuccess) return fail(pp.err, STAB_ERR_OOM, "cudaMalloc");
+    if (cudaMemcpy(pp.ds, pp.hs.data(), sizeof(StreamDev) * n, cudaMemcpyHostToDevice) != cudaSuccess)
+        return cuda_check(pp.err, "cudaMemcpy");
+    // work lists
+    std::vector<int> all;
+    std::vector<std::pair<WorkList *, std::vector<int>>> lists;
+    auto mk = [&](WorkList *wl, auto count) {
+        std::vector<int> pre(n + 1, 0);
+        for (int i = 0; i < n; ++i) pre[i + 1] = pre[i] + count(pp.hs[i]);
+        wl->n = n;
+        wl->total = pre[n];
+        lists.push_back({wl, pre});
+    };
+    mk(&pp.wl_l0, [](const StreamDev &D) { return tiles(D.w, D.h); });
+    for (int l = 1; l < STAB_MAXL; ++l)
+        mk(&pp.wl_pyr[l], [l](const StreamDev &D) { return l < D.L ? tiles(D.lw[l], D.lh[l]) : 0; });
+    mk(&pp.wl_resp, [](const StreamDev &D) { return tiles(D.roi_x1 - D.roi_x0, D.roi_y1 - D.roi_y0); });
+    mk(&pp.wl_filter, [](const StreamDev &D) { return (D.cand_cap + 2047) / 2048; });
+    mk(&pp.wl_lk, [](const StreamDev &D) { return D.K; });
+    mk(&pp.wl_warp, [](const StreamDev &D) { return tiles(D.w, D.h); });
+    for (auto &e : lists) all.insert(all.end(), e.second.begin(), e.second.end());
+    if (cudaMalloc(&pp.prefix, all.size() * sizeof(int)) != cudaSuccess) return fail(pp.err, STAB_ERR_OOM, "cudaMalloc");
+    cudaMemcpy(pp.prefix, all.data(), all.size() * sizeof(int), cudaMemcpyHostToDevice);
+    size_t o = 0;
+    for (auto &e : lists) {
+        e.first->prefix = pp.prefix + o;
+        o += e.second.size();
+    }
+    // kernel attributes and occupancy queries happen here, outside any capture
+    occ_level0_f(); occ_level0_h(); occ_pyr_f(); occ_pyr_h();
+    warm_detect(); warm_warp(); warm_lk();
+    return cuda_check(pp.err, "create");
+}
+
+void build_pyr(Pipeline &pp, const Launch &L, const uint8_t *frame, int pitch, int C, int slot)
+{
+    launch_level0(L, pp.prec, pp.ds, pp.wl_l0, FrameSrc{frame, pitch, C, slot});
+    for (int l = 1; l < pp.Lmax; ++l) launch_pyr_down(L, pp.prec, pp.ds, pp.wl_pyr[l], l, slot);
+}
+
+void detect_chain(Pipeline &pp, const Launch &L, DetIO io)
+{
+    launch_response(L, pp.ds, pp.wl_resp, io);
+    launch_filter(L, pp.ds, pp.wl_filter);
+    launch_select(L, pp.ds, pp.n, io);
+}
+
+// Optional per-kernel event brackets (profiled steps only; never captured).
+struct Prof {
+    std::vector<std::string> names;
+    std::vector<cudaEvent_t> ev;
+    cudaStream_t s = nullptr;
+    void mark(const char *name)
+    {
+        cudaEvent_t e;
+        cudaEventCreate(&e);
+        cudaEventRecord(e, s);
+        ev.push_back(e);
+        names.push_back(name ? name : "");
+    }
+};
+
+void enqueue_step(Pipeline &pp, cudaStream_t s, Prof *pf = nullptr)
+{
+    Launch L{s, pp.sms};
+    static const char *pyr_names[STAB_MAXL] = {"", "pyr_down_1", "pyr_down_2", "pyr_down_3", "pyr_down_4",
+                                                "pyr_down_5", "pyr_down_6", "pyr_down_7"};
+    auto mark = [&](const char *n) { if (pf) pf->mark(n); };
+    mark(nullptr);
+    launch_begin(L, pp.ds, pp.n, -1, 0);
+    mark("begin");
+    launch_level0(L, pp.prec, pp.ds, pp.wl_l0, FrameSrc{nullptr, 0, 0, 0});
+    mark("level0");
+    for (int l = 1; l < pp.Lmax; ++l) {
+        launch_pyr_down(L, pp.prec, pp.ds, pp.wl_pyr[l], l, -1);
+        mark(pyr_names[l]);
+    }
+    launch_response(L, pp.ds, pp.wl_resp, DetIO{});
+    mark("response");
+    launch_filter(L, pp.ds, pp.wl_filter);
+    mark("filter");
+    launch_select(L, pp.ds, pp.n, DetIO{});
+    mark("select");
+    launch_lk(L, pp.prec, pp.rmax, 1, pp.ds, pp.wl_lk, LkIO{});
+    mark("lk");
+    launch_compact(L, pp.ds, pp.n, CompactIO{});
+    mark("compact");
+    launch_fit(L, pp.ds, pp.n, FitIO{}, 1);
+    mark("fit");
+    launch_warp(L, pp.ds, pp.wl_warp, WarpIO{});
+    mark("warp");
+    launch_advance(L, pp.ds, pp.n);
+    mark("advance");
+}
+
+stab_status read_err(Pipeline &pp)
+{
+    stab_status res = STAB_OK;
+    for (int i = 0; i < pp.n; ++i) {
+        int e = 0;
+        if (cudaMemcpy(&e, &pp.hs[i].st->err, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess)
+            return cuda_check(pp.err, "reading the device error word");
+        if (e) {
+            cudaMemset(&pp.hs[i].st->err, 0, sizeof(int));
+            if (res == STAB_OK) {
+                res = (stab_status)e;
+                pp.err = "device error " + std::to_string(e) + " on stream " + std::to_string(i);
+            }
+        }
+    }
+    return res;
+}
+
+}  // namespace
+
+struct stab_ctx {
+    Pipeline pp;
+    long long t_track = 0, t_push = 0;
+};
+
+struct stab_batch {
+    Pipeline pp;
+    std::vector<int> C;
+    std::vector<std::string> knames;
+};
+
+extern "C" {
+
+const char *stab_version(void) { return kVersion; }
+
+stab_status stab_default_params(stab_params *o)
+{
+    if (!o) return STAB_ERR_INVALID_ARG;
+    std::memset(o, 0, sizeof(*o));
+    o->max_corners = 200;
+    o->levels = 3;
+    o->win_radius = 10;
+    o->max_iters = 30;
+    o->eps = 0.01f;
+    o->min_eig = 0.01f;
+    o->quality = 0.01f;
+    o->roi_margin_x = -1;
+    o->roi_margin_y = -1;
+    o->redetect_period = 5;
+    o->min_tracks = 10;
+    o->fb_thresh = 1.0f;
+    o->inlier_thresh = 1.0f;
+    o->hypotheses = 100;
+    o->seed = 0;
+    o->min_fit = 10;
+    o->smooth_window = 15;
+    o->model = STAB_SIMILARITY;
+    o->precision = STAB_FP32;
+    return STAB_OK;
+}
+
+stab_status stab_create(int w, int h, const stab_params *p, stab_ctx **out)
+{
+    if (!out) return STAB_ERR_INVALID_ARG;
+    *out = nullptr;
+    stab_params d;
+    if (!p) { stab_default_params(&d); p = &d; }
+    stab_ctx *c = new stab_ctx();
+    int C0 = 0;
+    stab_status s = build(c->pp, 1, &w, &h, &C0, p, 1);
+    if (s != STAB_OK) {
+        fprintf(stderr, "stab_create: %s\n", c->pp.err.c_str());
+        delete c;
+        return s;
+    }
+    *out = c;
+    return STAB_OK;
+}
+
+void stab_destroy(stab_ctx *c)
+{
+    if (!c) return;
+    if (c->pp.last) cudaStreamSynchronize(c->pp.last);
+    delete c;
+}
+
+const char *stab_last_error(const stab_ctx *c) { return c ? c->pp.err.c_str() : "null context"; }
+
+stab_status stab_sync(stab_ctx *c)
+{
+    if (!c) return STAB_ERR_INVALID_ARG;
+    if (cudaStreamSynchronize(c->pp.last) != cudaSuccess) return cuda_check(c->pp.err, "stream synchronize");
+    return read_err(c->pp);
+}
+
+#define CTX_LAUNCH(c, stream)                                   \
+    Pipeline &pp = (c)->pp;                                     \
+    pp.last = (cudaStream_t)(stream);                           \
+    Launch L{(cudaStream_t)(stream), pp.sms};
+
+stab_status stab_pyramid(stab_ctx *c, const uint8_t *frame, int pitch, int channels, uint8_t *out, void *stream)
+{
+    if (!c || !frame || !out || (channels != 1 && channels != 3)) return STAB_ERR_INVALID_ARG;
+    if (pitch < c->pp.hs[0].w * channels) return fail(c->pp.err, STAB_ERR_INVALID_ARG, "pitch < w * channels");
+    CTX_LAUNCH(c, stream);
+    const StreamDev &D = pp.hs[0];
+    build_pyr(pp, L, frame, pitch, channels, 0);
+    size_t off = 0;
+    for (int l = 0; l < D.L; ++l) {
+        cudaMemcpy2DAsync(out + off, D.lw[l], D.u8[0][l], D.lp[l], D.lw[l], D.lh[l], cudaMemcpyDeviceToDevice, L.stream);
+        off += (size_t)D.lw[l] * D.lh[l];
+    }
+    return cuda_check(pp.err, "stab_pyramid");
+}
+
+stab_status stab_planes(stab_ctx *c, int level, float *I, float *Ix, float *Iy, void *stream)
+{
+    if (!c || level < 0 || level >= c->pp.hs[0].L) return STAB_ERR_INVALID_ARG;
+    CTX_LAUNCH(c, stream);
+    launch_plane_f32(L, pp.prec, pp.ds, 0, level, I, Ix, Iy);
+    return cuda_check(pp.err, "stab_planes");
+}
+
+stab_status stab_detect(stab_ctx *c, const uint8_t *gray, int pitch, float *pts, float *lam, int *n, int *ncand,
+                        void *stream)
+{
+    if (!c || !gray || pitch < c->pp.hs[0].w) return STAB_ERR_INVALID_ARG;
+    CTX_LAUNCH(c, stream);
+    launch_begin(L, pp.ds, 1, 0, 1);
+    detect_chain(pp, L, DetIO{gray, pitch, (float2 *)pts, lam, n, ncand});
+    return cuda_check(pp.err, "stab_detect");
+}
+
+stab_status stab_lk(stab_ctx *c, const uint8_t *prev, const uint8_t *next, int pitch, const float *pts, int n,
+                    float *fwd, float *back, float *fb, uint8_t *status, uint8_t *status_fwd, void *stream)
+{
+    if (!c || !prev || !next || !pts || !fwd || !back || !fb || !status) return STAB_ERR_INVALID_ARG;
+    if (n < 0 || n > c->pp.hs[0].K || pitch < c->pp.hs[0].w) return STAB_ERR_INVALID_ARG;
+    CTX_LAUNCH(c, stream);
+    build_pyr(pp, L, prev, pitch, 1, 0);
+    build_pyr(pp, L, next, pitch, 1, 1);
+    if (n > 0) {
+        WorkList wl = pp.wl_lk;
+        wl.total = n;
+        LkIO io{(const float2 *)pts, n, 0, (float2 *)fwd, (float2 *)back, fb, status, status_fwd};
+        uint8_t *scratch_status_fwd = nullptr;
+        if (!status_fwd) {
+            scratch_status_fwd = pp.hs[0].status_fwd;
+            io.status_fwd = scratch_status_fwd;
+        }
+        launch_lk(L, pp.prec, pp.rmax, 1, pp.ds, wl, io);
+    }
+    return cuda_check(pp.err, "stab_lk");
+}
+
+stab_status stab_track(stab_ctx *c, const uint8_t *prev, const uint8_t *next, int pitch, int channels, int flags,
+                       float *pts_prev, float *pts_next, uint8_t *status, int *n, void *stream)
+{
+    if (!c || !prev || !next || (channels != 1 && channels != 3)) return STAB_ERR_INVALID_ARG;
+    if (pitch < c->pp.hs[0].w * channels) return STAB_ERR_INVALID_ARG;
+    CTX_LAUNCH(c, stream);
+    const long long t = ++c->t_track;
+    const int sp = (int)((t - 1) & 1), sn = (int)(t & 1);
+    if (!(flags & STAB_TRACK_CONTINUE) || t == 1) build_pyr(pp, L, prev, pitch, channels, sp);
+    build_pyr(pp, L, next, pitch, channels, sn);
+    launch_begin(L, pp.ds, 1, t, 0);
+    detect_chain(pp, L, DetIO{});
+    launch_lk(L, pp.prec, pp.rmax, 1, pp.ds, pp.wl_lk, LkIO{});
+    launch_compact(L, pp.ds, 1, CompactIO{(float2 *)pts_prev, (float2 *)pts_next, n, status});
+    return cuda_check(pp.err, "stab_track");
+}
+
+stab_status stab_fit(stab_ctx *c, const float *src, const float *dst, const int *n, int model, int t,
+                     stab_motion *out, void *stream)
+{
+    if (!c || !src || !dst || !n || !out || (model != STAB_RIGID && model != STAB_SIMILARITY))
+        return STAB_ERR_INVALID_ARG;
+    CTX_LAUNCH(c, stream);
+    launch_fit(L, pp.ds, 1, FitIO{(const float2 *)src, (const float2 *)dst, n, model == STAB_RIGID, t, out}, 0);
+    return cuda_check(pp.err, "stab_fit");
+}
+
+stab_status stab_smooth(stab_ctx *c, const stab_motion *m, int T, int W, float *mprime, float *Minv, void *stream)
+{
+    if (!c || !m || !mprime || !Minv || T < 1 || W < 1) return STAB_ERR_INVALID_ARG;
+    CTX_LAUNCH(c, stream);
+    launch_smooth_offline(L, m, T, W, pp.hs[0].w, pp.hs[0].h, mprime, Minv);
+    return cuda_check(pp.err, "stab_smooth");
+}
+
+stab_status stab_smooth_push(stab_ctx *c, const stab_motion *m, float *Minv, int *ready, void *stream)
+{
+    if (!c || !m || !Minv || !ready) return STAB_ERR_INVALID_ARG;
+    CTX_LAUNCH(c, stream);
+    launch_smooth_push(L, pp.ds, ++c->t_push, m, Minv, ready);
+    return cuda_check(pp.err, "stab_smooth_push");
+}
+
+stab_status stab_warp(stab_ctx *c, const uint8_t *src, int sp, uint8_t *dst, int dp, int channels, const float *Minv,
+                      void *stream)
+{
+    if (!c || !src || !dst || !Minv || (channels != 1 && channels != 3)) return STAB_ERR_INVALID_ARG;
+    if (sp < c->pp.hs[0].w * channels || dp < c->pp.hs[0].w * channels) return STAB_ERR_INVALID_ARG;
+    CTX_LAUNCH(c, stream);
+    launch_warp(L, pp.ds, pp.wl_warp, WarpIO{src, sp, dst, dp, channels, Minv});
+    return cuda_check(pp.err, "stab_warp");
+}
+
+// ------------------------------------------------------------------ batch --
+stab_status stab_batch_create(int n, const stab_stream_desc *d, int ring, stab_batch **out)
+{
+    if (!out || n < 1 || n > 4096 || !d) return STAB_ERR_INVALID_ARG;
+    *out = nullptr;
+    std::vector<int> w(n), h(n), C(n);
+    std::vector<stab_params> P(n);
+    int need = 2;
+    for (int i = 0; i < n; ++i) {
+        if (d[i].channels != 1 && d[i].channels != 3) return STAB_ERR_INVALID_ARG;
+        w[i] = d[i].w; h[i] = d[i].h; C[i] = d[i].channels; P[i] = d[i].params;
+        need = std::max(need, P[i].smooth_window / 2 + 2);
+    }
+    if (ring <= 0) ring = need;
+    if (ring < need) return STAB_ERR_INVALID_ARG;
+    stab_batch *b = new stab_batch();
+    b->C = C;
+    stab_status s = build(b->pp, n, w.data(), h.data(), C.data(), P.data(), ring);
+    if (s == STAB_OK && cudaStreamCreateWithFlags(&b->pp.cap, cudaStreamNonBlocking) != cudaSuccess)
+        s = cuda_check(b->pp.err, "stream create");
+    if (s != STAB_OK) {
+        fprintf(stderr, "stab_batch_create: %s\n", b->pp.err.c_str());
+        delete b;
+        return s;
+    }
+    *out = b;
+    return STAB_OK;
+}
+
+void stab_batch_destroy(stab_batch *b)
+{
+    if (!b) return;
+    if (b->pp.last) cudaStreamSynchronize(b->pp.last);
+    delete b;
+}
+
+uint8_t *stab_batch_input(stab_batch *b, int i, int slot)
+{
+    if (!b || i < 0 || i >= b->pp.n || slot < 0 || slot >= b->pp.ring) return nullptr;
+    return b->pp.hs[i].ring + (size_t)slot * b->pp.hs[i].slot_bytes;
+}
+
+uint8_t *stab_batch_output(stab_batch *b, int i)
+{
+    if (!b || i < 0 || i >= b->pp.n) return nullptr;
+    return b->pp.hs[i].out;
+}
+
+int stab_batch_pitch(const stab_batch *b, int i) { return (b && i >= 0 && i < b->pp.n) ? b->pp.hs[i].in_pitch : 0; }
+int stab_batch_ring(const stab_batch *b) { return b ? b->pp.ring : 0; }
+int64_t stab_batch_frame(const stab_batch *b) { return b ? b->pp.t_host : -1; }
+const char *stab_batch_last_error(const stab_batch *b) { return b ? b->pp.err.c_str() : "null batch"; }
+
+stab_status stab_batch_step(stab_batch *b, int use_graph, void *stream)
+{
+    if (!b) return STAB_ERR_INVALID_ARG;
+    Pipeline &pp = b->pp;
+    cudaStream_t s = (cudaStream_t)stream;
+    pp.last = s;
+    if (use_graph) {
+        if (!pp.gexec) {
+            if (cudaStreamBeginCapture(pp.cap, cudaStreamCaptureModeThreadLocal) != cudaSuccess)
+                return cuda_check(pp.err, "begin capture");
+            enqueue_step(pp, pp.cap);
+            if (cudaStreamEndCapture(pp.cap, &pp.graph) != cudaSuccess) return cuda_check(pp.err, "end capture");
+            if (cudaGraphInstantiate(&pp.gexec, pp.graph, 0) != cudaSuccess) return cuda_check(pp.err, "instantiate");
+        }
+        if (cudaGraphLaunch(pp.gexec, s) != cudaSuccess) return cuda_check(pp.err, "graph launch");
+    } else {
+        enqueue_step(pp, s);
+    }
+    ++pp.t_host;
+    return cuda_check(pp.err, "stab_batch_step");
+}
+
+stab_status stab_batch_step_profiled(stab_batch *b, void *stream, float *ms, int n_ms, int *n_kernels)
+{
+    if (!b || !n_kernels) return STAB_ERR_INVALID_ARG;
+    Pipeline &pp = b->pp;
+    Prof pf;
+    pf.s = (cudaStream_t)stream;
+    pp.last = pf.s;
+    enqueue_step(pp, pf.s, &pf);
+    ++pp.t_host;
+    stab_status st = cuda_check(pp.err, "stab_batch_step_profiled");
+    cudaStreamSynchronize(pf.s);
+    const int nk = (int)pf.ev.size() - 1;
+    *n_kernels = nk;
+    b->knames.assign(pf.names.begin() + 1, pf.names.end());
+    for (int k = 0; k < nk && ms && k < n_ms; ++k) {
+        float v = 0.f;
+        cudaEventElapsedTime(&v, pf.ev[k], pf.ev[k + 1]);
+        ms[k] = v;
+    }
+    for (auto e : pf.ev) cudaEventDestroy(e);
+    if (st == STAB_OK) st = cuda_check(pp.err, "stab_batch_step_profiled");
+    return st;
+}
+
+const char *stab_batch_kernel_name(const stab_batch *b, int i)
+{
+    if (!b || i < 0 || i >= (int)b->knames.size()) return "";
+    return b->knames[i].c_str();
+}
+
+stab_status stab_batch_lk_work(stab_batch *b, int64_t *iterations, int64_t *templates)
+{
+    if (!b || !iterations || !templates) return STAB_ERR_INVALID_ARG;
+    Pipeline &pp = b->pp;
+    if (cudaStreamSynchronize(pp.last) != cudaSuccess) return cuda_check(pp.err, "stream synchronize");
+    *iterations = 0;
+    *templates = 0;
+    for (int i = 0; i < pp.n; ++i) {
+        long long it = 0, tp = 0;
+        cudaMemcpy(&it, &pp.hs[i].st->iters, sizeof(it), cudaMemcpyDeviceToHost);
+        cudaMemcpy(&tp, &pp.hs[i].st->tpl, sizeof(tp), cudaMemcpyDeviceToHost);
+        *iterations += it;
+        *templates += tp;
+    }
+    return cuda_check(pp.err, "stab_batch_lk_work");
+}
+
+stab_status stab_batch_step_host(stab_batch *b, const uint8_t *const *frames, uint8_t *const *outs, void *stream)
+{
+    if (!b || !frames) return STAB_ERR_INVALID_ARG;
+    Pipeline &pp = b->pp;
+    cudaStream_t s = (cudaStream_t)stream;
+    const long long t = pp.t_host;
+    for (int i = 0; i < pp.n; ++i) {
+        const StreamDev &D = pp.hs[i];
+        if (!frames[i]) return STAB_ERR_INVALID_ARG;
+        cudaMemcpy2DAsync(D.ring + (size_t)(t % pp.ring) * D.slot_bytes, D.in_pitch, frames[i], (size_t)D.w * D.C,
+                          (size_t)D.w * D.C, D.h, cudaMemcpyHostToDevice, s);
+    }
+    stab_status st = stab_batch_step(b, 1, stream);
+    if (st != STAB_OK) return st;
+    if (outs)
+        for (int i = 0; i < pp.n; ++i) {
+            const StreamDev &D = pp.hs[i];
+            if (outs[i] && t - 1 - pp.P[i].smooth_window / 2 >= 0)
+                cudaMemcpy2DAsync(outs[i], (size_t)D.w * D.C, D.out, D.out_pitch, (size_t)D.w * D.C, D.h,
+                                  cudaMemcpyDeviceToHost, s);
+        }
+    return cuda_check(pp.err, "stab_batch_step_host");
+}
+
+stab_status stab_batch_sync(stab_batch *b)
+{
+    if (!b) return STAB_ERR_INVALID_ARG;
+    if (cudaStreamSynchronize(b->pp.last) != cudaSuccess) return cuda_check(b->pp.err, "stream synchronize");
+    return read_err(b->pp);
+}
+
+stab_status stab_batch_motions(stab_batch *b, stab_motion *out)
+{
+    if (!b || !out) return STAB_ERR_INVALID_ARG;
+    Pipeline &pp = b->pp;
+    if (cudaStreamSynchronize(pp.last) != cudaSuccess) return cuda_check(pp.err, "stream synchronize");
+    const long long t = pp.t_host - 1;
+    for (int i = 0; i < pp.n; ++i) {
+        if (t < 0) { std::memset(&out[i], 0, sizeof(stab_motion)); continue; }
+        cudaMemcpy(&out[i], pp.hs[i].mring + (t % STAB_CRING), sizeof(stab_motion), cudaMemcpyDeviceToHost);
+    }
+    return cuda_check(pp.err, "stab_batch_motions");
+}
+
+stab_status stab_batch_features(stab_batch *b, int i, float *pts, int *n)
+{
+    if (!b || i < 0 || i >= b->pp.n || !pts || !n) return STAB_ERR_INVALID_ARG;
+    Pipeline &pp = b->pp;
+    if (cudaStreamSynchronize(pp.last) != cudaSuccess) return cuda_check(pp.err, "stream synchronize");
+    cudaMemcpy(n, &pp.hs[i].st->n_feat, sizeof(int), cudaMemcpyDeviceToHost);
+    cudaMemcpy(pts, pp.hs[i].feat, sizeof(float2) * pp.hs[i].K, cudaMemcpyDeviceToHost);
+    return cuda_check(pp.err, "stab_batch_features");
+}
+
+}  // extern "C"

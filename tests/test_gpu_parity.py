@@ -1,0 +1,322 @@
+"""GPU path vs the CPU oracle, row by row, on identical seeded inputs.
+
+Every call goes through the C ABI (libstab.so) via the ctypes binding.  Each
+step is fed the oracle's own inputs for that step, so that a difference is
+attributable to that step alone.  Bars:
+  * pyramid, planes, corners, warp: bit-exact (integer work, or FP32
+    decisions taken with one fixed operation order on both sides);
+  * robust fit: identical inlier counts and winning sample; parameters within
+    1e-4 (angle, log-scale) and 0.02 px (translation);
+  * tracker: positions within 0.01 px where both sides keep the point, status
+    agreement >= 99 %;
+  * smoothing: FP32 vs FP64 within the bounds derived in each test.
+"""
+import dataclasses
+import math
+
+import numpy as np
+import pytest
+import torch
+
+from oracle import oracle as O
+from paper_1701_03572_gb300 import stab as S
+from paper_1701_03572_gb300.synth import CONFIG_SPECS, ClipSpec, make_clip
+
+pytestmark = pytest.mark.gpu
+
+DEV = "cuda"
+
+
+def _clip(cfg, frames, seed):
+    spec = dataclasses.replace(CONFIG_SPECS[cfg], frames=frames)
+    return make_clip(spec, seed)
+
+
+def _params(**kw):
+    return S.default_params(**kw)
+
+
+def _cuda(a):
+    return torch.as_tensor(np.ascontiguousarray(a)).to(DEV)
+
+
+# ----------------------------------------------------------------- pyramid --
+@pytest.mark.parametrize("w,h,L,prec", [(320, 240, 3, 0), (640, 480, 4, 1), (333, 257, 4, 0), (17, 16, 1, 1),
+                                        (131, 67, 5, 0)])
+def test_pyramid_and_planes_bit_exact(w, h, L, prec):
+    rng = np.random.default_rng(w * 7 + h)
+    img = rng.integers(0, 256, (h, w), dtype=np.uint8)
+    ctx = S.Context(w, h, _params(levels=L, precision=prec))
+    levels = ctx.pyramid(_cuda(img))
+    ref = O.pyramid(img, L)
+    for l in range(L):
+        assert np.array_equal(levels[l].cpu().numpy(), ref[l]), f"level {l}"
+        I, Ix, Iy = ctx.planes(l)
+        rI, rIx, rIy = O.grad_planes(ref[l])
+        assert np.array_equal(I.cpu().numpy(), rI) and np.array_equal(Ix.cpu().numpy(), rIx)
+        assert np.array_equal(Iy.cpu().numpy(), rIy)
+    assert ctx.sync() == 0
+
+
+def test_pyramid_rgb_luma_1080p():
+    clip = _clip(2, 1, 2)
+    rgb = clip["frames"][0].numpy()
+    ctx = S.Context(1920, 1080, _params(levels=5))
+    levels = ctx.pyramid(_cuda(rgb))
+    ref = O.pyramid(O.luma(rgb), 5)
+    for l in range(5):
+        assert np.array_equal(levels[l].cpu().numpy(), ref[l]), f"level {l}"
+
+
+# ---------------------------------------------------------------- corners --
+@pytest.mark.parametrize("cfg,K", [(0, 200), (1, 500), (2, 1000)])
+def test_detect_bit_exact(cfg, K):
+    clip = _clip(cfg, 1, 10 + cfg)
+    f = clip["frames"][0].numpy()
+    g = O.luma(f) if f.ndim == 3 else f
+    h, w = g.shape
+    ctx = S.Context(w, h, _params(max_corners=K, levels=3))
+    pts, lam, n = ctx.detect(_cuda(g))
+    torch.cuda.synchronize()
+    rp, rl, nc = O.detect(g, O.roi_of(w, h), K)
+    n = n.cpu().numpy()
+    assert n[0] == len(rp) and n[1] == nc
+    assert np.array_equal(pts.cpu().numpy()[:n[0]], rp)
+    assert np.array_equal(lam.cpu().numpy()[:n[0]], rl)
+
+
+def test_detect_ties_flat_and_tiny_k():
+    w, h = 96, 80
+    img = np.full((h, w), 40, np.uint8)
+    ctx = S.Context(w, h, _params(max_corners=7))
+    pts, lam, n = ctx.detect(_cuda(img))          # flat: no corner at all
+    torch.cuda.synchronize()
+    assert n.cpu().numpy()[0] == 0
+    for k in range(6):                             # identical squares: equal scores, raster-order ties
+        x, y = 16 + 12 * k, 30
+        img[y:y + 6, x:x + 6] = 200
+    pts, lam, n = ctx.detect(_cuda(img))
+    torch.cuda.synchronize()
+    rp, rl, nc = O.detect(img, O.roi_of(w, h), 7)
+    assert n.cpu().numpy()[0] == len(rp)
+    assert np.array_equal(pts.cpu().numpy()[:len(rp)], rp)
+
+
+# --------------------------------------------------------------- tracking --
+def _lk_case(cfg, seed, K, L):
+    clip = _clip(cfg, 2, seed)
+    f0, f1 = clip["frames"][0].numpy(), clip["frames"][1].numpy()
+    if f0.ndim == 3:
+        f0, f1 = O.luma(f0), O.luma(f1)
+    h, w = f0.shape
+    pts, _, _ = O.detect(f0, O.roi_of(w, h), K)
+    return f0, f1, pts, w, h
+
+
+@pytest.mark.parametrize("cfg,K,L", [(0, 200, 3), (1, 500, 4), (2, 1000, 5)])
+def test_lk_parity(cfg, K, L):
+    f0, f1, pts, w, h = _lk_case(cfg, 20 + cfg, K, L)
+    ref = O.track(O.pyramid(f0, L), O.pyramid(f1, L), pts)
+    res = {}
+    for prec in (0, 1):
+        ctx = S.Context(w, h, _params(max_corners=K, levels=L, precision=prec))
+        r = ctx.lk(_cuda(f0), _cuda(f1), _cuda(pts))
+        torch.cuda.synchronize()
+        res[prec] = {k: v.cpu().numpy() for k, v in r.items()}
+    # FP16 storage holds the same plane values: identical results
+    for k in res[0]:
+        assert np.array_equal(res[0][k], res[1][k]), k
+    g = res[0]
+    agree = (g["status"] == ref["status"]).mean()
+    assert agree >= 0.99
+    both = (g["status"] == 1) & (ref["status"] == 1)
+    assert both.sum() >= 0.8 * len(pts)
+    d = np.hypot(*(g["fwd"][both] - ref["fwd"][both]).T)
+    assert d.max() < 0.01, d.max()
+    db = np.hypot(*(g["back"][both] - ref["back"][both]).T)
+    assert db.max() < 0.02
+
+
+def test_lk_edge_cases():
+    w, h = 64, 48
+    rng = np.random.default_rng(3)
+    img = rng.integers(0, 256, (h, w), dtype=np.uint8)
+    ctx = S.Context(w, h, _params(max_corners=16, levels=2))
+    r = ctx.lk(_cuda(img), _cuda(img), torch.zeros((0, 2), device=DEV))        # no points
+    # one point on a flat patch (lost) and one at the image corner (window clamped)
+    flat = img.copy()
+    flat[10:40, 10:40] = 7
+    pts = np.array([[25.0, 25.0], [0.0, 0.0], [63.0, 47.0]], np.float32)
+    r = ctx.lk(_cuda(flat), _cuda(flat), _cuda(pts))
+    torch.cuda.synchronize()
+    ref = O.track(O.pyramid(flat, 2), O.pyramid(flat, 2), pts)
+    assert np.array_equal(r["status"].cpu().numpy(), ref["status"])
+    assert np.abs(r["fwd"].cpu().numpy() - ref["fwd"]).max() < 1e-4
+
+
+# -------------------------------------------------------------------- fit --
+@pytest.mark.parametrize("cfg,rigid,H", [(0, False, 100), (1, True, 256), (1, False, 256), (2, False, 100)])
+def test_fit_parity(cfg, rigid, H):
+    K, L = {0: (200, 3), 1: (500, 4), 2: (1000, 5)}[cfg]
+    f0, f1, pts, w, h = _lk_case(cfg, 30 + cfg, K, L)
+    tr = O.track(O.pyramid(f0, L), O.pyramid(f1, L), pts)
+    keep = tr["status"] == 1
+    src = pts[keep].astype(np.float32)
+    dst = tr["fwd"][keep].astype(np.float32)
+    ref = O.fit(src, dst, w, h, rigid, H, 7, 1, 1.0, 10)
+    ctx = S.Context(w, h, _params(max_corners=K, hypotheses=H, seed=7, model=0 if rigid else 1))
+    n = torch.tensor([len(src)], dtype=torch.int32, device=DEV)
+    out = ctx.fit(_cuda(src), _cuda(dst), n, 0 if rigid else 1, 1)
+    torch.cuda.synchronize()
+    m = S.motions_from_raw(out.view(1, 8))
+    assert m["flags"][0] == 0 and ref["flags"] == 0
+    assert m["inliers"][0] == ref["inliers"]
+    assert m["n_tracks"][0] == len(src)
+    g = m["m"][0]
+    assert abs(g[2] - ref["m"][2]) < 1e-4 and abs(g[3] - ref["m"][3]) < 1e-4
+    assert np.abs(g[:2] - ref["m"][:2]).max() < 0.02
+    assert abs(m["rms"][0] - ref["rms"]) < 1e-3
+
+
+def test_fit_skip_and_degenerate():
+    ctx = S.Context(100, 100, _params(max_corners=32))
+    src = np.array([[10, 10], [50, 60], [80, 20]], np.float32)
+    n = torch.tensor([3], dtype=torch.int32, device=DEV)
+    out = ctx.fit(_cuda(src), _cuda(src + 1), n, 1, 1)
+    # all points identical: every sample degenerate
+    same = np.tile([[40.0, 40.0]], (20, 1)).astype(np.float32)
+    n2 = torch.tensor([20], dtype=torch.int32, device=DEV)
+    out2 = ctx.fit(_cuda(same), _cuda(same), n2, 1, 2)
+    torch.cuda.synchronize()
+    for o in (out, out2):
+        m = S.motions_from_raw(o.view(1, 8))
+        assert m["flags"][0] & S.STAB_FLAG_SKIPPED and np.all(m["m"][0] == 0)
+
+
+# -------------------------------------------------------------- smoothing --
+@pytest.mark.parametrize("T,W", [(60, 15), (300, 30), (5, 1), (7, 20)])
+def test_smoothing_parity(T, W):
+    rng = np.random.default_rng(T + W)
+    m = np.zeros((T, 4))
+    m[1:] = np.stack([0.5 + rng.normal(0, 2, T - 1), rng.normal(0, 2, T - 1), rng.normal(0, 0.01, T - 1),
+                      rng.normal(0, 0.005, T - 1)], 1)
+    m32 = m.astype(np.float32)
+    raw = np.zeros((T, 8), np.float32)
+    raw[:, :4] = m32
+    ctx = S.Context(640, 480, _params(smooth_window=W))
+    mp, Minv = ctx.smooth(_cuda(raw), W)
+    torch.cuda.synchronize()
+    _, _, ref = O.smooth(m32.astype(np.float64), W)
+    # FP32 prefix sums of |C| <= ~T px: error <= T * ulp(T) per sum
+    tol_t = 4 * T * np.spacing(np.float32(max(T, 1))) + 1e-4
+    assert np.abs(mp.cpu().numpy()[:, :2] - ref[:, :2]).max() < tol_t
+    assert np.abs(mp.cpu().numpy()[:, 2:] - ref[:, 2:]).max() < 1e-5
+    refM = np.stack([O.warp_inverse(ref[t], 640, 480) for t in range(T)])
+    assert np.abs(Minv.cpu().numpy() - refM).max() < 1e-3 + tol_t
+    # streaming form = offline form (same FP32 sequence) for every frame it emits
+    ctx2 = S.Context(640, 480, _params(smooth_window=W))
+    Mo = Minv.cpu().numpy()
+    for t in range(1, T):
+        M, ready = ctx2.smooth_push(_cuda(raw[t]))
+        torch.cuda.synchronize()
+        u = int(ready.item())
+        assert u == (t - 1 - W // 2 if t - 1 - W // 2 >= 0 else -1)
+        if u >= 0 and u + 1 + W // 2 <= T - 1:
+            assert np.array_equal(M.cpu().numpy(), Mo[u + 1])
+
+
+# ------------------------------------------------------------------- warp --
+@pytest.mark.parametrize("w,h,C", [(320, 240, 1), (643, 481, 1), (1920, 1080, 3), (77, 53, 3)])
+def test_warp_bit_exact(w, h, C):
+    rng = np.random.default_rng(w + C)
+    shape = (h, w) if C == 1 else (h, w, C)
+    img = rng.integers(0, 256, shape, dtype=np.uint8)
+    ctx = S.Context(w, h, _params())
+    for m in ([0, 0, 0, 0], [3.7, -2.2, 0.02, 0.01], [-40.0, 25.0, -0.05, -0.03], [0, 0, math.pi / 2, 0]):
+        Minv = O.warp_inverse(np.array(m, np.float64), w, h)
+        out = ctx.warp(_cuda(img), _cuda(Minv))
+        torch.cuda.synchronize()
+        assert np.array_equal(out.cpu().numpy(), O.warp(img, Minv)), m
+
+
+# ------------------------------------------------------------ whole path --
+def _gpu_clip(frames, p, T):
+    h, w = frames.shape[1:3]
+    ctx = S.Context(w, h, p)
+    raw = torch.zeros((T, 8), dtype=torch.float32, device=DEV)
+    fr = _cuda(frames)
+    for t in range(1, T):
+        src, dst, status, n = ctx.track(fr[t - 1], fr[t], cont=t > 1)
+        ctx.fit(src, dst, n, p.model, t, out=raw[t])
+    mp, Minv = ctx.smooth(raw, p.smooth_window)
+    outs = torch.zeros_like(fr)
+    for t in range(1, T):
+        ctx.warp(fr[t - 1], Minv[t], out=outs[t - 1])
+    torch.cuda.synchronize()
+    assert ctx.sync() == 0
+    return raw, Minv, outs
+
+
+@pytest.mark.parametrize("cfg,T", [(0, 16), (1, 8)])
+def test_pipeline_vs_oracle_and_ground_truth(cfg, T):
+    clip = _clip(cfg, T, 40 + cfg)
+    frames = clip["frames"].numpy()
+    spec = CONFIG_SPECS[cfg]
+    if cfg == 0:
+        op = O.Params(max_corners=200, levels=3, hypotheses=100, smooth_window=15, rigid=False)
+    else:
+        op = O.Params(max_corners=500, levels=4, hypotheses=256, smooth_window=30, rigid=True)
+    gp = _params(max_corners=op.max_corners, levels=op.levels, hypotheses=op.hypotheses,
+                 smooth_window=op.smooth_window, model=0 if op.rigid else 1)
+    ref = O.run_clip(frames, op)
+    raw, Minv, outs = _gpu_clip(frames, gp, T)
+    m = S.motions_from_raw(raw)
+    gt = clip["incs"]
+    assert (m["flags"][1:] & S.STAB_FLAG_SKIPPED == 0).all()
+    assert np.abs(m["m"][1:, 2:] - ref["incs"][1:, 2:]).max() < 2e-4
+    assert np.abs(m["m"][1:, :2] - ref["incs"][1:, :2]).max() < 0.05
+    # ground truth (the generator's exact increments); rigid: the scale part is not modelled
+    tol_a = 1e-3 if cfg == 0 else 6e-3
+    assert np.abs(m["m"][1:, 2] - gt[1:, 2]).max() < tol_a
+    if cfg == 0:
+        assert np.abs(m["m"][1:, 3] - gt[1:, 3]).max() < 1e-3
+        assert np.abs(m["m"][1:, :2] - gt[1:, :2]).max() < 0.1
+    # composed frames: small differences of the FP32 matrices flip rare roundings
+    d = np.abs(outs.cpu().numpy()[:T - 1].astype(int) - ref["out"][:T - 1].astype(int))
+    assert (d > 1).mean() < 0.02 and d.mean() < 0.3
+
+
+def test_batch_graph_equals_single_stream_path():
+    """The batched graph step (FP16 planes, two streams of different size)
+    reproduces the single-stream FP32 path bit for bit: same kernels, same
+    FP32 arithmetic, plane values identical in both storages."""
+    T = 14
+    specs = [(0, 50), (1, 51)]
+    clips = [_clip(c, T, s)["frames"].numpy() for c, s in specs]
+    params = [_params(max_corners=200, levels=3, smooth_window=9, precision=1),
+              _params(max_corners=300, levels=4, smooth_window=9, model=0, hypotheses=128, precision=1)]
+    descs = [(f.shape[2], f.shape[1], 1, p) for f, p in zip(clips, params)]
+    b = S.Batch(descs)
+    outs = [[] for _ in specs]
+    motions = [[] for _ in specs]
+    for t in range(T):
+        for i, f in enumerate(clips):
+            b.input_slot(i, t % b.ring).copy_(_cuda(f[t]))
+        b.step(use_graph=True)
+        torch.cuda.synchronize()
+        for i in range(len(specs)):
+            motions[i].append(b.motions()[i])
+            if t - 1 - 9 // 2 >= 0:
+                outs[i].append(b.output(i).cpu().numpy().copy())
+    assert b.sync() == 0
+    for i, f in enumerate(clips):
+        p32 = _params(**{k: getattr(params[i], k) for k, _ in S.StabParams._fields_})
+        p32.precision = 0
+        raw, Minv, o = _gpu_clip(f, p32, T)
+        m = S.motions_from_raw(raw)
+        for t in range(1, T):
+            assert np.array_equal(np.array(motions[i][t]["m"], np.float32), m["m"][t].astype(np.float32)), (i, t)
+            assert motions[i][t]["inliers"] == m["inliers"][t]
+        oc = o.cpu().numpy()
+        for k, frame in enumerate(outs[i]):
+            assert np.array_equal(frame, oc[k]), (i, k)

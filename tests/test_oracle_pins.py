@@ -200,6 +200,18 @@ def test_detect_square_corners():
 
 
 # -------------------------------------------------------------- tracking --
+def test_grad_planes_vs_numpy_gradient():
+    rng = np.random.default_rng(8)
+    img = rng.integers(0, 256, (13, 17), dtype=np.uint8)
+    I, Ix, Iy = O.grad_planes(img)
+    gy, gx = np.gradient(img.astype(np.float64))
+    assert np.array_equal(I, img)
+    # interior: numpy's central difference; borders: half the one-sided difference
+    assert np.array_equal(Ix[:, 1:-1], gx[:, 1:-1]) and np.array_equal(Iy[1:-1], gy[1:-1])
+    assert np.array_equal(Ix[:, 0], gx[:, 0] / 2) and np.array_equal(Ix[:, -1], gx[:, -1] / 2)
+    assert np.array_equal(Iy[0], gy[0] / 2) and np.array_equal(Iy[-1], gy[-1] / 2)
+
+
 def test_lk_zero_motion_is_exact():
     img = np.clip(smooth_texture(96, 128, 7), 0, 255).astype(np.uint8)
     pyr = O.pyramid(img, 3)
