@@ -127,7 +127,8 @@ stab_status stab_planes(stab_ctx *ctx, int level, float *I_dev, float *Ix_dev, f
  * non-maximum suppression, threshold q * max, strongest max_corners first
  * (ties: lower raster index).  Writes pts_dev (2 * max_corners floats),
  * optional lam_dev (max_corners scores), n_dev (count), optional
- * ncand_dev (candidates before the cut).  Counts are device ints. */
+ * ncand_dev (NMS survivors above the threshold, before the top-K cut).
+ * Counts are device ints.  Also replaces the context's feature set. */
 stab_status stab_detect(stab_ctx *ctx, const uint8_t *gray_dev, int pitch, float *pts_dev, float *lam_dev,
                         int *n_dev, int *ncand_dev, void *stream);
 

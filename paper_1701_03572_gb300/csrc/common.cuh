@@ -40,7 +40,7 @@ struct StreamState {
     long long iters;      // LK iterations of this step (statistic)
     long long tpl;        // LK template passes (feature x level x direction) of this step
     int n_det;            // corners of the last detection
-    int pad_;
+    int n_above;          // candidates above the quality threshold (before the top-K cut)
 };
 
 struct StreamDev {

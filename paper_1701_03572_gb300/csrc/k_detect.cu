@@ -47,6 +47,7 @@ __global__ void k_begin(const StreamDev *__restrict__ S, int n, long long t_ov, 
     st->due = due;
     st->n_cand = 0;
     st->n_sel = 0;
+    st->n_above = 0;
     st->lam_max = 0;
     st->blocks_done = 0;
     st->iters = 0;
@@ -222,14 +223,17 @@ __global__ void __launch_bounds__(256) k_filter(const StreamDev *__restrict__ S,
         for (int b0 = c0; b0 < end; b0 += blockDim.x) {
             int i = b0 + tid;
             unsigned long long key = 0;
-            bool pass = false;
+            bool pass = false, above = false;
             if (i < end) {
                 key = D.cand[i];
                 unsigned lb = (unsigned)(key >> 32);
-                pass = (lb >> STAB_HSHIFT) >= bin_lo && lb > thr;
+                above = lb > thr;
+                pass = above && (lb >> STAB_HSHIFT) >= bin_lo;
             }
             unsigned m = __ballot_sync(0xffffffffu, pass);
+            unsigned ma = __ballot_sync(0xffffffffu, above);
             int base = 0;
+            if (lane == 0 && ma) atomicAdd(&st->n_above, __popc(ma));
             if (lane == 0 && m) base = atomicAdd(&st->n_sel, __popc(m));
             base = __shfl_sync(0xffffffffu, base, 0);
             if (pass) D.sel[base + __popc(m & ((1u << lane) - 1u))] = key;
@@ -332,7 +336,7 @@ __global__ void __launch_bounds__(1024) k_select(const StreamDev *__restrict__ S
         st->n_feat = Kp;
         st->n_det = Kp;
         if (io.n_out) *io.n_out = Kp;
-        if (io.ncand_out) *io.ncand_out = st->n_cand;
+        if (io.ncand_out) *io.ncand_out = st->n_above;
     }
     for (int b = tid; b < STAB_HBINS; b += blockDim.x) D.hist[b] = 0u;
     (void)lane;

@@ -97,11 +97,8 @@ void launch_advance(const Launch &L, const StreamDev *S, int n);
 
 void launch_warp(const Launch &L, const StreamDev *S, WorkList wl, WarpIO io);
 
-void launch_charb_forward(const Launch &L, const float *It, const float *Ip, int w, int h, int P,
-                          const float *theta, int margin, float eps, float *loss, float *dtheta, float *gn,
-                          float *partials);
+void launch_charb_forward(const Launch &L, const float *It, const float *Ip, int w, int h, int P, float *theta,
+                          int margin, float eps, float *loss, float *dtheta, float *gn, int update);
 void launch_charb_backward_image(const Launch &L, const float *It, const float *Ip, int w, int h, int P,
                                  const float *theta, int margin, float eps, const float *gout, float *dIt,
                                  float *dIp);
-void launch_charb_gn_update(const Launch &L, int P, const float *gn, float *theta);
-int charb_partials_per_pair(int w, int h, int margin);

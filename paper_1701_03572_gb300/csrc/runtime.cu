@@ -417,7 +417,7 @@ stab_status stab_detect(stab_ctx *c, const uint8_t *gray, int pitch, float *pts,
 stab_status stab_lk(stab_ctx *c, const uint8_t *prev, const uint8_t *next, int pitch, const float *pts, int n,
                     float *fwd, float *back, float *fb, uint8_t *status, uint8_t *status_fwd, void *stream)
 {
-    if (!c || !prev || !next || !pts || !fwd || !back || !fb || !status) return STAB_ERR_INVALID_ARG;
+    if (!c || !prev || !next || (n > 0 && (!pts || !fwd || !back || !fb || !status))) return STAB_ERR_INVALID_ARG;
     if (n < 0 || n > c->pp.hs[0].K || pitch < c->pp.hs[0].w) return STAB_ERR_INVALID_ARG;
     CTX_LAUNCH(c, stream);
     build_pyr(pp, L, prev, pitch, 1, 0);
@@ -663,6 +663,62 @@ stab_status stab_batch_features(stab_batch *b, int i, float *pts, int *n)
     cudaMemcpy(n, &pp.hs[i].st->n_feat, sizeof(int), cudaMemcpyDeviceToHost);
     cudaMemcpy(pts, pp.hs[i].feat, sizeof(float2) * pp.hs[i].K, cudaMemcpyDeviceToHost);
     return cuda_check(pp.err, "stab_batch_features");
+}
+
+// ------------------------------------------------- photometric refinement --
+static stab_status charb_args(const float *It, const float *Ip, int w, int h, int P, const void *theta, int margin,
+                              float eps)
+{
+    if (!It || !Ip || !theta || w < 4 || h < 4 || P < 1 || P > (1 << 20) || margin < 0 || 2 * margin >= w ||
+        2 * margin >= h || !(eps > 0.f))
+        return STAB_ERR_INVALID_ARG;
+    return STAB_OK;
+}
+
+static Launch plain_launch(void *stream)
+{
+    static int sms = 0;
+    if (!sms) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    }
+    return Launch{(cudaStream_t)stream, sms};
+}
+
+stab_status stab_charb_forward(const float *It, const float *Ip, int w, int h, int P, const float *theta, int margin,
+                               float eps, float *loss, float *dtheta, float *gn, void *stream)
+{
+    stab_status st = charb_args(It, Ip, w, h, P, theta, margin, eps);
+    if (st) return st;
+    std::string err;
+    launch_charb_forward(plain_launch(stream), It, Ip, w, h, P, const_cast<float *>(theta), margin, eps, loss, dtheta,
+                         gn, 0);
+    return cuda_check(err, "stab_charb_forward");
+}
+
+stab_status stab_charb_backward_image(const float *It, const float *Ip, int w, int h, int P, const float *theta,
+                                      int margin, float eps, const float *gout, float *dIt, float *dIp, void *stream)
+{
+    stab_status st = charb_args(It, Ip, w, h, P, theta, margin, eps);
+    if (st) return st;
+    if (!dIt && !dIp) return STAB_ERR_INVALID_ARG;
+    std::string err;
+    launch_charb_backward_image(plain_launch(stream), It, Ip, w, h, P, theta, margin, eps, gout, dIt, dIp);
+    return cuda_check(err, "stab_charb_backward_image");
+}
+
+stab_status stab_charb_gauss_newton(const float *It, const float *Ip, int w, int h, int P, float *theta, int margin,
+                                    float eps, int steps, void *stream)
+{
+    stab_status st = charb_args(It, Ip, w, h, P, theta, margin, eps);
+    if (st) return st;
+    if (steps < 0 || steps > 1000) return STAB_ERR_INVALID_ARG;
+    std::string err;
+    const Launch L = plain_launch(stream);
+    for (int k = 0; k < steps; ++k)
+        launch_charb_forward(L, It, Ip, w, h, P, theta, margin, eps, nullptr, nullptr, nullptr, 1);
+    return cuda_check(err, "stab_charb_gauss_newton");
 }
 
 }  // extern "C"

@@ -82,6 +82,9 @@ def lib():
             "stab_batch_kernel_name": ([_vp, _i], C.c_char_p),
             "stab_batch_lk_work": ([_vp, C.POINTER(_i64), C.POINTER(_i64)], _i),
             "stab_batch_last_error": ([_vp], C.c_char_p),
+            "stab_charb_forward": ([_vp, _vp, _i, _i, _i, _vp, _i, _f, _vp, _vp, _vp, _vp], _i),
+            "stab_charb_backward_image": ([_vp, _vp, _i, _i, _i, _vp, _i, _f, _vp, _vp, _vp, _vp], _i),
+            "stab_charb_gauss_newton": ([_vp, _vp, _i, _i, _i, _vp, _i, _f, _i, _vp], _i),
         }
         for name, (args, res) in sig.items():
             fn = getattr(L, name)
@@ -337,3 +340,76 @@ class Batch:
         n = C.c_int(0)
         self._chk(lib().stab_batch_features(self._h, i, _vp(pts.data_ptr()), C.byref(n)), "stab_batch_features")
         return pts[:n.value].clone()
+
+
+# ----------------------------------------------------- photometric refinement --
+def _pairs(It, Ip, theta):
+    if It.dim() == 2:
+        It, Ip = It.unsqueeze(0), Ip.unsqueeze(0)
+    if It.shape != Ip.shape or It.dtype != torch.float32 or Ip.dtype != torch.float32:
+        raise ValueError("I_t and I_prev must be float32 tensors of one shape (P, h, w)")
+    P, h, w = It.shape
+    theta = theta.reshape(P, 4)
+    if theta.dtype != torch.float32:
+        raise ValueError("theta must be float32")
+    return It.contiguous(), Ip.contiguous(), theta.contiguous(), P, h, w
+
+
+def _chk_plain(st, what):
+    if st < 0:
+        raise StabError(f"{what}: status {st}")
+
+
+def charb_forward(It, Ip, theta, margin=48, eps=1e-3, want_gn=False):
+    """Loss (P,), dL/dtheta (P, 4) and optionally the IRLS Gauss-Newton system (P, 14)."""
+    It, Ip, theta, P, h, w = _pairs(It, Ip, theta)
+    loss = torch.empty(P, dtype=torch.float32, device=It.device)
+    dth = torch.empty((P, 4), dtype=torch.float32, device=It.device)
+    gn = torch.empty((P, 14), dtype=torch.float32, device=It.device) if want_gn else None
+    _chk_plain(lib().stab_charb_forward(_p(It), _p(Ip), w, h, P, _p(theta), margin, eps, _p(loss), _p(dth), _p(gn),
+                                        _s()), "stab_charb_forward")
+    return loss, dth, gn
+
+
+def charb_backward_image(It, Ip, theta, margin=48, eps=1e-3, gout=None, want_prev=True):
+    """dL/dI_t and dL/dI_prev (P, h, w), each scaled by gout (P,)."""
+    It, Ip, theta, P, h, w = _pairs(It, Ip, theta)
+    dIt = torch.empty_like(It)
+    dIp = torch.empty_like(Ip) if want_prev else None
+    g = gout.contiguous().float() if gout is not None else None
+    _chk_plain(lib().stab_charb_backward_image(_p(It), _p(Ip), w, h, P, _p(theta), margin, eps, _p(g), _p(dIt),
+                                               _p(dIp), _s()), "stab_charb_backward_image")
+    return dIt, dIp
+
+
+def charb_gauss_newton(It, Ip, theta, steps=10, margin=48, eps=1e-3):
+    """`steps` IRLS Gauss-Newton updates; returns the refined parameters (P, 4)."""
+    It, Ip, theta, P, h, w = _pairs(It, Ip, theta)
+    th = theta.clone()
+    _chk_plain(lib().stab_charb_gauss_newton(_p(It), _p(Ip), w, h, P, _p(th), margin, eps, steps, _s()),
+               "stab_charb_gauss_newton")
+    return th
+
+
+class WarpCharbonnier(torch.autograd.Function):
+    """loss_p = sum_Omega sqrt((I_t(W(x; theta_p)) - I_prev(x))^2 + eps^2), with
+    the hand-written adjoint for theta, I_t and I_prev."""
+
+    @staticmethod
+    def forward(ctx, It, Ip, theta, margin=48, eps=1e-3):
+        loss, dth, _ = charb_forward(It, Ip, theta, margin, eps)
+        ctx.save_for_backward(It, Ip, theta, dth)
+        ctx.margin, ctx.eps, ctx.shape = margin, eps, It.shape
+        return loss
+
+    @staticmethod
+    def backward(ctx, gl):
+        It, Ip, theta, dth = ctx.saved_tensors
+        gl = gl.reshape(-1).contiguous().float()
+        dIt = dIp = dtheta = None
+        if ctx.needs_input_grad[0] or ctx.needs_input_grad[1]:
+            dIt, dIp = charb_backward_image(It, Ip, theta, ctx.margin, ctx.eps, gl, ctx.needs_input_grad[1])
+            dIt, dIp = dIt.reshape(ctx.shape), (dIp.reshape(ctx.shape) if dIp is not None else None)
+        if ctx.needs_input_grad[2]:
+            dtheta = (dth * gl[:, None]).reshape(theta.shape)
+        return dIt, dIp, dtheta, None, None

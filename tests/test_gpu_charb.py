@@ -1,0 +1,132 @@
+"""Photometric refinement on the GPU (warp adjoint, Charbonnier loss,
+Gauss-Newton) against the FP64 oracle, on seeded 640x480 FP32 frame pairs.
+
+Conditioning sets the bars.  With eps = 1e-3 the slope psi = r / sqrt(r^2 +
+eps^2) moves by up to |grad I| / eps ~ 5e4 per pixel of sample position where
+|r| < eps, and FP32 positions carry ~1e-6 px of rounding; per-pixel image
+gradients are therefore compared where every contributing sample has
+|r| >= 0.05 (slope change <= eps^2 / |r|^3 = 8e-3 per unit of r), and over the
+whole image in relative L2.  The IRLS weights 1 / rho move by up to
+0.38 / eps^2 per unit of r; summed over the frame the normal matrix keeps
+~1e-3 relative accuracy.  Loss and dL/dtheta (bounded slopes) are held to 1e-4.
+"""
+import numpy as np
+import pytest
+import torch
+
+from oracle import oracle as O
+from paper_1701_03572_gb300 import stab as S
+from paper_1701_03572_gb300.synth import make_pair_f32
+
+pytestmark = pytest.mark.gpu
+W, H, M, EPS = 640, 480, 48, 1e-3
+
+
+def _pairs(n, seed0=100):
+    ps = [make_pair_f32(W, H, seed0 + k) for k in range(n)]
+    It = torch.stack([p["cur"] for p in ps]).cuda()
+    Ip = torch.stack([p["prev"] for p in ps]).cuda()
+    truth = np.stack([p["theta"] for p in ps])
+    return It, Ip, truth
+
+
+def test_loss_and_theta_gradient_vs_oracle():
+    It, Ip, truth = _pairs(4)
+    rng = np.random.default_rng(5)
+    th = (truth + rng.normal(0, [0.5, 0.5, 0.003, 0.003], truth.shape)).astype(np.float32)
+    loss, dth, gn = S.charb_forward(It, Ip, torch.as_tensor(th).cuda(), M, EPS, want_gn=True)
+    torch.cuda.synchronize()
+    for p in range(4):
+        r = O.charb(It[p].cpu().numpy(), Ip[p].cpu().numpy(), th[p].astype(np.float64), M, EPS, want_gn=True)
+        assert abs(loss[p].item() - r["loss"]) <= 1e-4 * abs(r["loss"])
+        assert np.abs(dth[p].cpu().numpy() - r["dtheta"]).max() <= 1e-4 * np.abs(r["dtheta"]).max()
+        Hu = r["H"][np.triu_indices(4)]
+        g = gn[p].cpu().numpy()
+        assert np.abs(g[:10] - Hu).max() <= 2e-3 * np.abs(Hu).max()
+        assert np.abs(g[10:] - r["g"]).max() <= 2e-3 * np.abs(r["g"]).max()
+
+
+def _ill_conditioned(It, Ip, th, thr=0.05):
+    """Pixels q of I_t that receive a sample with |r| < thr (FP64 positions)."""
+    h, w = It.shape
+    cx, cy = (w - 1) / 2, (h - 1) / 2
+    Y, X = np.mgrid[M:h - M, M:w - M].astype(np.float64)
+    s, c, sn = np.exp(th[3]), np.cos(th[2]), np.sin(th[2])
+    dx, dy = X - cx, Y - cy
+    Wx = cx + s * (c * dx - sn * dy) + th[0]
+    Wy = cy + s * (sn * dx + c * dy) + th[1]
+    x0, y0 = np.floor(Wx).astype(int), np.floor(Wy).astype(int)
+    ax, ay = Wx - x0, Wy - y0
+    pad = np.pad(It.astype(np.float64), 2)
+    t = lambda xx, yy: pad[yy + 2, xx + 2]
+    v = (1 - ax) * (1 - ay) * t(x0, y0) + ax * (1 - ay) * t(x0 + 1, y0) + (1 - ax) * ay * t(x0, y0 + 1) + \
+        ax * ay * t(x0 + 1, y0 + 1)
+    ill = np.abs(v - Ip[M:h - M, M:w - M]) < thr
+    bad = np.zeros((h + 4, w + 4), bool)
+    for ddx in (0, 1):
+        for ddy in (0, 1):
+            bad[y0[ill] + ddy + 2, x0[ill] + ddx + 2] = True
+    return bad[2:-2, 2:-2], ill
+
+
+def test_image_gradients_vs_oracle():
+    It, Ip, truth = _pairs(2, 300)
+    th = truth.astype(np.float32)
+    gout = torch.tensor([1.0, -0.5], device="cuda")
+    dIt, dIp = S.charb_backward_image(It, Ip, torch.as_tensor(th).cuda(), M, EPS, gout)
+    torch.cuda.synchronize()
+    for p in range(2):
+        Itn, Ipn = It[p].cpu().numpy(), Ip[p].cpu().numpy()
+        r = O.charb(Itn, Ipn, th[p].astype(np.float64), M, EPS, want_dI=True)
+        g = gout[p].item()
+        bad, ill = _ill_conditioned(Itn, Ipn, th[p].astype(np.float64))
+        assert ill.mean() < 0.05
+        ref_t, got_t = g * r["dIt"], dIt[p].cpu().numpy()
+        scale = np.abs(ref_t).max()
+        assert np.abs(got_t - ref_t)[~bad].max() <= 1e-4 * scale
+        assert np.linalg.norm(got_t - ref_t) <= 1e-2 * np.linalg.norm(ref_t)
+        ref_p, got_p = g * r["dIp"], dIp[p].cpu().numpy()
+        okp = np.ones_like(bad)
+        okp[M:-M, M:-M] = ~ill
+        assert np.abs(got_p - ref_p)[okp].max() <= 1e-4 * np.abs(ref_p).max()
+        assert np.linalg.norm(got_p - ref_p) <= 1e-2 * np.linalg.norm(ref_p)
+
+
+def test_autograd_function_matches_direct_calls():
+    It, Ip, truth = _pairs(2, 400)
+    th = torch.as_tensor(truth.astype(np.float32)).cuda().requires_grad_(True)
+    It = It.clone().requires_grad_(True)
+    loss = S.WarpCharbonnier.apply(It, Ip, th, M, EPS)
+    (loss * torch.tensor([2.0, 3.0], device="cuda")).sum().backward()
+    _, dth, _ = S.charb_forward(It.detach(), Ip, th.detach(), M, EPS)
+    dIt, _ = S.charb_backward_image(It.detach(), Ip, th.detach(), M, EPS, torch.tensor([2.0, 3.0], device="cuda"))
+    assert torch.allclose(th.grad, dth * torch.tensor([[2.0], [3.0]], device="cuda"))
+    assert torch.equal(It.grad, dIt)
+
+
+def test_gauss_newton_refines_the_tracker_estimate():
+    """Start from the feature-based estimate (tracker + fit on the quantised
+    pair) and refine with 10 photometric Gauss-Newton steps."""
+    P = 8
+    It, Ip, truth = _pairs(P, 500)
+    est = np.zeros((P, 4), np.float32)
+    for p in range(P):
+        a = np.clip(np.floor(Ip[p].cpu().numpy() + 0.5), 0, 255).astype(np.uint8)
+        b = np.clip(np.floor(It[p].cpu().numpy() + 0.5), 0, 255).astype(np.uint8)
+        ctx = S.Context(W, H, S.default_params(max_corners=500, levels=4, hypotheses=256))
+        src, dst, status, n = ctx.track(torch.as_tensor(a).cuda(), torch.as_tensor(b).cuda())
+        out = ctx.fit(src, dst, n, S.STAB_SIMILARITY, 1)
+        est[p] = S.motions_from_raw(out.view(1, 8))["m"][0]
+    th0 = torch.as_tensor(est).cuda()
+    th = S.charb_gauss_newton(It, Ip, th0, 10, M, EPS)
+    torch.cuda.synchronize()
+    e0 = np.abs(est - truth)
+    e1 = np.abs(th.cpu().numpy() - truth)
+    # error in pixels at the image corner: translation plus r * angle / log-scale
+    r = np.hypot(W, H) / 2
+    px0 = e0[:, :2].max(1) + r * e0[:, 2:].max(1)
+    px1 = e1[:, :2].max(1) + r * e1[:, 2:].max(1)
+    assert (px1 <= px0).mean() >= 0.95 or (px1 < 0.05).all()
+    # the GPU's 10 steps land where the oracle's do
+    ref = O.gauss_newton(It[0].cpu().numpy(), Ip[0].cpu().numpy(), est[0].astype(np.float64), 10, M, EPS)
+    assert np.abs(th[0].cpu().numpy() - ref)[:2].max() < 2e-3 and np.abs(th[0].cpu().numpy() - ref)[2:].max() < 1e-5

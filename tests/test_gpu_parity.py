@@ -46,7 +46,8 @@ def _cuda(a):
 def test_pyramid_and_planes_bit_exact(w, h, L, prec):
     rng = np.random.default_rng(w * 7 + h)
     img = rng.integers(0, 256, (h, w), dtype=np.uint8)
-    ctx = S.Context(w, h, _params(levels=L, precision=prec))
+    small = dict(win_radius=2, roi_margin_x=3, roi_margin_y=3) if min(w, h) < 40 else {}
+    ctx = S.Context(w, h, _params(levels=L, precision=prec, **small))
     levels = ctx.pyramid(_cuda(img))
     ref = O.pyramid(img, L)
     for l in range(L):
