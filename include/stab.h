@@ -132,6 +132,27 @@ stab_status stab_planes(stab_ctx *ctx, int level, float *I_dev, float *Ix_dev, f
 stab_status stab_detect(stab_ctx *ctx, const uint8_t *gray_dev, int pitch, float *pts_dev, float *lam_dev,
                         int *n_dev, int *ncand_dev, void *stream);
 
+/* Corner detection that allocates nothing, for callers that cannot call
+ * cudaMalloc: code whose device memory belongs to a host application's own
+ * pool allocator, or a real-time loop that must not call cudaMalloc / cudaFree
+ * (they can synchronise the device and stall the frame cadence).  The paper has
+ * no counterpart; this is a deployment variant of stab_detect.
+ * Same result as stab_detect for the same frame, ROI [roi_x0, roi_x1) x
+ * [roi_y0, roi_y1) (at least 3 px from every border), quality and
+ * max_corners, without a context: all scratch lives in one fixed device array
+ * of about 5.4 MB inside the library, held by every GPU that loads it until
+ * the process exits.  Limits: ROI at most 1536 x 864 pixels, max_corners at
+ * most 2048; larger requests return STAB_ERR_CAPACITY (with a message on
+ * stderr).  The caller passes the gray frame and the outputs (as for
+ * stab_detect).  The first call on a device looks up the array's device
+ * address; make that first call before any stream capture.  Every call
+ * shares the one array: calls whose work overlaps on the GPU (different
+ * streams, different host threads) race and must be serialised by the
+ * caller. */
+stab_status stab_detect_noalloc(const uint8_t *gray_dev, int w, int h, int pitch, int roi_x0, int roi_y0,
+                                int roi_x1, int roi_y1, float quality, int max_corners, float *pts_dev,
+                                float *lam_dev, int *n_dev, int *ncand_dev, void *stream);
+
 /* Pyramidal Lucas-Kanade (Sec. 3.2, Eq. 3-6) of n given points from frame
  * `prev` to frame `next` (gray, same size as the context), followed by the
  * backward pass of the forward-backward check (Sec. 4.1).  Outputs (n each):

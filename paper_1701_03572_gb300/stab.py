@@ -60,6 +60,7 @@ def lib():
             "stab_pyramid": ([_vp, _vp, _i, _i, _vp, _vp], _i),
             "stab_planes": ([_vp, _i, _vp, _vp, _vp, _vp], _i),
             "stab_detect": ([_vp, _vp, _i, _vp, _vp, _vp, _vp, _vp], _i),
+            "stab_detect_noalloc": ([_vp, _i, _i, _i, _i, _i, _i, _i, _f, _i, _vp, _vp, _vp, _vp, _vp], _i),
             "stab_lk": ([_vp, _vp, _vp, _i, _vp, _i, _vp, _vp, _vp, _vp, _vp, _vp], _i),
             "stab_track": ([_vp, _vp, _vp, _i, _i, _i, _vp, _vp, _vp, _vp, _vp], _i),
             "stab_fit": ([_vp, _vp, _vp, _vp, _i, _i, _vp, _vp], _i),
@@ -340,6 +341,21 @@ class Batch:
         n = C.c_int(0)
         self._chk(lib().stab_batch_features(self._h, i, _vp(pts.data_ptr()), C.byref(n)), "stab_batch_features")
         return pts[:n.value].clone()
+
+
+def detect_noalloc(gray: torch.Tensor, roi, quality: float, max_corners: int, pts=None, lam=None, n=None):
+    """stab_detect_noalloc: corners without a context or any allocation inside
+    the library (outputs are allocated here unless given).  Returns
+    (status, pts (K, 2), lam (K,), counts [n, n_above_threshold])."""
+    gray = gray.contiguous()
+    h, w = gray.shape
+    dev = gray.device
+    pts = pts if pts is not None else torch.zeros((max_corners, 2), dtype=torch.float32, device=dev)
+    lam = lam if lam is not None else torch.zeros(max_corners, dtype=torch.float32, device=dev)
+    n = n if n is not None else torch.zeros(2, dtype=torch.int32, device=dev)
+    st = lib().stab_detect_noalloc(_p(gray), w, h, w, roi[0], roi[1], roi[2], roi[3], quality, max_corners,
+                                   _p(pts), _p(lam), _p(n[0:1]), _p(n[1:2]), _s())
+    return st, pts, lam, n
 
 
 # ----------------------------------------------------- photometric refinement --
