@@ -161,7 +161,7 @@ def run_ours(args):
     B = args.streams
     A = PARAMS["smooth_window"] // 2
     ring = 2 * (A + 2)                      # >= A + 2 and even for the retracing clip
-    clips = make_frames(min(4, B), ring, dev)
+    clips = make_frames(min(args.clips, B), ring, dev)
     p16 = S.default_params(**PARAMS, precision=S.STAB_FP16_STORAGE)
     batch = S.Batch([(W, H, CH, p16) for _ in range(B)], ring=ring)
     offs = [(i // len(clips)) * 3 % ring for i in range(B)]
@@ -169,8 +169,15 @@ def run_ours(args):
         for s in range(ring):
             batch.input_slot(i, s).copy_(clips[i % len(clips)][(s + offs[i]) % ring])
     stream = torch.cuda.current_stream()
-    # prime the smoother's lookahead (no composed frame before step A + 1), then warm up
-    for _ in range(A + 2 + args.warmup):
+    # prime the smoother's lookahead (no composed frame before step A + 1),
+    # pick the tracker variant for this GPU and batch shape, then warm up
+    for _ in range(A + 2):
+        batch.step(True)
+    tuned = None
+    if not args.no_autotune:
+        v, ms = batch.autotune(None)
+        tuned = {"lk_variant": v, "lk_variant_ms": {str(k): round(x, 4) for k, x in ms.items()}}
+    for _ in range(args.warmup):
         batch.step(True)
     torch.cuda.synchronize()
     n_k = 11 + (PARAMS["levels"] - 1)       # kernels per step
@@ -205,13 +212,13 @@ def run_ours(args):
             kt.setdefault(name, []).append(ms)
         lkw.append(batch.lk_work())
     kavg = {k: sum(v) / len(v) for k, v in kt.items()}
-    roof = roofline(kavg, lkw, B)
+    roof = roofline(kavg, lkw, B) if kavg else None
 
     # ---- plain single-stream path, FP32 planes
-    plain = run_plain(S, clips[0], ring, args.plain_steps, dev)
+    plain = run_plain(S, clips[0], ring, args.plain_steps, dev) if args.plain_steps > 0 else None
 
     # ---- end to end through host buffers
-    e2e = run_e2e(S, batch, clips, offs, ring, args.e2e_steps, B)
+    e2e = run_e2e(S, batch, clips, offs, ring, args.e2e_steps, B) if args.e2e_steps > 0 else None
 
     out = {"metric": METRIC, "value": round(value, 1), "unit": "frames/s", "n_gpus": ws, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": round(total_ms / args.steps, 4), "higher_is_better": True,
@@ -220,7 +227,7 @@ def run_ours(args):
            "latency_ms": {"p50": round(p50, 4), "p99": round(p99, 4), "per": "batch step (16 frames)"},
            "plain": plain, "e2e": e2e, "roofline": roof,
            "kernels_ms": {k: round(v, 4) for k, v in kavg.items()},
-           "gpu_launches": n_k * args.steps, "clocks": clk, "wall_s": round(wall, 3)}
+           "gpu_launches": n_k * args.steps, "clocks": clk, "wall_s": round(wall, 3), "autotune": tuned}
     if ws == 1 and rank == 0 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(clips[0].cpu().numpy(), args.cpu_frames)
     if rank == 0:
@@ -462,7 +469,9 @@ def main():
     ap.add_argument("--plain-steps", type=int, default=60)
     ap.add_argument("--e2e-steps", type=int, default=20)
     ap.add_argument("--cpu-frames", type=int, default=8)
+    ap.add_argument("--clips", type=int, default=4, help="distinct seeded clips shared round-robin by the streams")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-autotune", action="store_true")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")

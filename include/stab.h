@@ -242,6 +242,18 @@ stab_status stab_batch_step(stab_batch *b, int use_graph, void *stream);
  * synchronises `stream` before reading out_host. */
 stab_status stab_batch_step_host(stab_batch *b, const uint8_t *const *frames_host, uint8_t *const *out_host,
                                  void *stream);
+/* Autotuner of the batched step: times each variant of the tracker kernel
+ * (one or two warps per feature, register budgets) on the batch's current
+ * state with CUDA events and keeps the fastest for later steps.  cache_path
+ * (may be NULL) names a JSON file of earlier choices keyed by GPU name and
+ * batch shape; a cached choice is applied without timing and new choices are
+ * added to it.  Needs at least two steps run; synchronous on `stream`.
+ * *variant (may be NULL) receives the choice; ms_out (may be NULL, one float
+ * per variant) the measured mean ms per launch (-1 when taken from the cache). */
+stab_status stab_batch_autotune(stab_batch *b, const char *cache_path, int *variant, float *ms_out, void *stream);
+/* Force a tracker variant (0..3) for a batch or a single-stream context. */
+stab_status stab_batch_set_lk_variant(stab_batch *b, int variant);
+stab_status stab_set_lk_variant(stab_ctx *ctx, int variant);
 /* Copy the motions of the last step (n entries) to host memory (synchronous). */
 stab_status stab_batch_motions(stab_batch *b, stab_motion *out_host);
 /* Copy stream i's current feature set (2 * max_corners floats) and its count. */

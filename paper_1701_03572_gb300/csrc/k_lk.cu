@@ -2,15 +2,16 @@
 // Bouguet's pyramidal implementation cited there) with the forward-backward
 // check of Sec. 4.1.
 //
-// One warp tracks one feature.  The (2r+1)^2 window is spread over the 32
-// lanes (NS samples per lane).  At each level the template I, Ix, Iy is
-// sampled once, bilinearly, with weights shared by every sample (the window
-// sits at integer offsets from the point), and kept in registers; each
-// iteration samples the next frame at the displaced window, accumulates
-// b = sum e [Ix, Iy], and solves the 2x2 system.  The three G sums and the
-// two b sums are reduced with xor-butterfly shuffles, which leave the same
-// bits in every lane, so the convergence test is warp-uniform.  Arithmetic
-// is FP32 for both storage precisions of the planes.
+// A group of WPF warps (WPF = 1 or 2, chosen by the autotuner) tracks one
+// feature.  At each level the group stages the (2r+2)^2 patch of I and of
+// (Ix, Iy) under the window into shared memory (coalesced row loads, FP32,
+// border taps replicated, so sampling is branch-free), samples the (2r+1)^2
+// template bilinearly with weights shared by every sample, and keeps T, Tx,
+// Ty in registers (NS samples per thread).  Each iteration stages the next
+// frame's patch at the displaced window, accumulates b = sum e [Tx, Ty] and
+// solves the 2x2 system.  Sums are reduced with xor-butterfly shuffles (same
+// bits in every lane) and, for two warps, combined through shared memory in a
+// fixed order, so every thread of the group takes the same branch.
 #include "kernels.cuh"
 
 namespace {
@@ -22,15 +23,74 @@ __device__ __forceinline__ float wsum(float v)
     return v;
 }
 
-template <typename PT, int NS>
+// Synchronise the threads of one feature group.
+template <int WPF>
+__device__ __forceinline__ void group_sync(int grp)
+{
+    if (WPF == 1) __syncwarp();
+    else asm volatile("bar.sync %0, %1;" ::"r"(1 + grp), "r"(32 * WPF) : "memory");
+}
+
+// Group-wide sums of three values (fixed order: warp 0 + warp 1).
+template <int WPF>
+__device__ __forceinline__ void group_sum3(float &a, float &b, float &c, float *red, int wig, int grp)
+{
+    a = wsum(a); b = wsum(b); c = wsum(c);
+    if (WPF > 1) {
+        const int lane = threadIdx.x & 31;
+        group_sync<WPF>(grp);   // previous readers of red are done
+        if (lane == 0) { red[3 * wig] = a; red[3 * wig + 1] = b; red[3 * wig + 2] = c; }
+        group_sync<WPF>(grp);
+        a = red[0]; b = red[1]; c = red[2];
+#pragma unroll
+        for (int w = 1; w < WPF; ++w) { a += red[3 * w]; b += red[3 * w + 1]; c += red[3 * w + 2]; }
+    }
+}
+
+// Stage the pw x pw patch with top-left (x0, y0) of a plane into shared
+// memory as FP32 (border taps replicated when the patch leaves the image).
+template <typename PT, int NT>
+__device__ __forceinline__ void stage1(const PT *__restrict__ P, int pitch, int wl, int hl, int x0, int y0, int pw,
+                                       bool inside, float *dst, int tig)
+{
+    const int n = pw * pw, q = NT / pw, rr = NT - q * pw;
+    int row = tig / pw, col = tig - row * pw;
+    for (int e = tig; e < n; e += NT) {
+        int xx = x0 + col, yy = y0 + row;
+        if (!inside) { xx = clampi(xx, 0, wl - 1); yy = clampi(yy, 0, hl - 1); }
+        dst[e] = ld1(P + (size_t)yy * pitch + xx);
+        col += rr; row += q;
+        if (col >= pw) { col -= pw; ++row; }
+    }
+}
+
+template <typename PT2, int NT>
+__device__ __forceinline__ void stage2(const PT2 *__restrict__ P, int pitch, int wl, int hl, int x0, int y0, int pw,
+                                       bool inside, float2 *dst, int tig)
+{
+    const int n = pw * pw, q = NT / pw, rr = NT - q * pw;
+    int row = tig / pw, col = tig - row * pw;
+    for (int e = tig; e < n; e += NT) {
+        int xx = x0 + col, yy = y0 + row;
+        if (!inside) { xx = clampi(xx, 0, wl - 1); yy = clampi(yy, 0, hl - 1); }
+        dst[e] = ld2(P + (size_t)yy * pitch + xx);
+        col += rr; row += q;
+        if (col >= pw) { col -= pw; ++row; }
+    }
+}
+
+// Track one feature from pyramid slot sa to slot sb.  RC = compile-time
+// radius (0: runtime D.r).  sI: pw^2 floats, sG: pw^2 float2, red: 3 * WPF.
+template <typename PT, int NS, int RC, int WPF>
 __device__ bool lk_track(const StreamDev &D, int sa, int sb, float ux, float uy, float &vx, float &vy, int &iters,
-                         int &tpl)
+                         int &tpl, float *sI, float2 *sG, float *red, int tig, int grp)
 {
     typedef typename Plane2<PT>::type PT2;
-    const int lane = threadIdx.x & 31;
-    const int r = D.r, ww = 2 * r + 1, N = ww * ww;
-    const int q32 = 32 / ww, r32 = 32 - q32 * ww;
-    const int i_l0 = lane % ww, j_l0 = lane / ww;
+    constexpr int NT = 32 * WPF;
+    const int wig = tig >> 5;
+    const int r = RC ? RC : D.r, ww = 2 * r + 1, pw = ww + 1, N = ww * ww;
+    const int qn = NT / ww, rn = NT - qn * ww;
+    const int i_l0 = tig % ww, j_l0 = tig / ww;
     float gx = 0.f, gy = 0.f, dx = 0.f, dy = 0.f;
     float T[NS], TX[NS], TY[NS];
     for (int l = D.L - 1; l >= 0; --l) {
@@ -40,101 +100,104 @@ __device__ bool lk_track(const StreamDev &D, int sa, int sb, float ux, float uy,
         const int wl = D.lw[l], hl = D.lh[l], p = D.lp[l];
         const float sc = __int_as_float((127 - l) << 23);   // 2^-l
         const float px = ux * sc, py = uy * sc;
-        {
-            const float bx = fminf(fmaxf(px, -64.f), (float)wl + 64.f);
-            const float by = fminf(fmaxf(py, -64.f), (float)hl + 64.f);
-            const float fx = floorf(bx), fy = floorf(by);
-            const float ax = bx - fx, ay = by - fy;
-            const int ix = (int)fx - r, iy = (int)fy - r;
-            const float w00 = (1.f - ax) * (1.f - ay), w01 = ax * (1.f - ay);
-            const float w10 = (1.f - ax) * ay, w11 = ax * ay;
-            const bool inside = ix >= 0 && ix + ww <= wl - 1 && iy >= 0 && iy + ww <= hl - 1;
-            float gxx = 0.f, gxy = 0.f, gyy = 0.f;
-            int i = i_l0, j = j_l0;
+        const float bx = fminf(fmaxf(px, -64.f), (float)wl + 64.f);
+        const float by = fminf(fmaxf(py, -64.f), (float)hl + 64.f);
+        const float fx = floorf(bx), fy = floorf(by);
+        const float ax = bx - fx, ay = by - fy;
+        const int ix = (int)fx - r, iy = (int)fy - r;
+        const float w00 = (1.f - ax) * (1.f - ay), w01 = ax * (1.f - ay);
+        const float w10 = (1.f - ax) * ay, w11 = ax * ay;
+        const bool inside = ix >= 0 && ix + ww <= wl - 1 && iy >= 0 && iy + ww <= hl - 1;
+        group_sync<WPF>(grp);
+        stage1<PT, NT>(Ia, p, wl, hl, ix, iy, pw, inside, sI, tig);
+        stage2<PT2, NT>(Ga, p, wl, hl, ix, iy, pw, inside, sG, tig);
+        group_sync<WPF>(grp);
+        float gxx = 0.f, gxy = 0.f, gyy = 0.f;
+        int i = i_l0, j = j_l0;
+#pragma unroll
+        for (int m = 0; m < NS; ++m) {
+            const int k = tig + NT * m;
+            T[m] = 0.f; TX[m] = 0.f; TY[m] = 0.f;
+            if (k < N) {
+                const int o = j * pw + i;
+                const float t = w00 * sI[o] + w01 * sI[o + 1] + w10 * sI[o + pw] + w11 * sI[o + pw + 1];
+                const float2 g00 = sG[o], g01 = sG[o + 1], g10 = sG[o + pw], g11 = sG[o + pw + 1];
+                const float tx = w00 * g00.x + w01 * g01.x + w10 * g10.x + w11 * g11.x;
+                const float ty = w00 * g00.y + w01 * g01.y + w10 * g10.y + w11 * g11.y;
+                T[m] = t; TX[m] = tx; TY[m] = ty;
+                gxx += tx * tx; gxy += tx * ty; gyy += ty * ty;
+            }
+            i += rn; j += qn;
+            if (i >= ww) { i -= ww; ++j; }
+        }
+        group_sum3<WPF>(gxx, gxy, gyy, red, wig, grp);
+        ++tpl;
+        const float lam = 0.5f * ((gxx + gyy) - sqrtf((gxx - gyy) * (gxx - gyy) + 4.f * gxy * gxy));
+        const float det = gxx * gyy - gxy * gxy;
+        if (!(lam >= D.min_eig * (float)N) || !(det > 0.f)) {
+            vx = ux; vy = uy;
+            return false;
+        }
+        const float idet = 1.f / det;
+        float nx = 0.f, ny = 0.f;
+        for (int it = 0; it < D.max_iters; ++it) {
+            const float qx = fminf(fmaxf(px + gx + nx, -64.f), (float)wl + 64.f);
+            const float qy = fminf(fmaxf(py + gy + ny, -64.f), (float)hl + 64.f);
+            const float fqx = floorf(qx), fqy = floorf(qy);
+            const float cx = qx - fqx, cy = qy - fqy;
+            const int jx = (int)fqx - r, jy = (int)fqy - r;
+            const float v00 = (1.f - cx) * (1.f - cy), v01 = cx * (1.f - cy);
+            const float v10 = (1.f - cx) * cy, v11 = cx * cy;
+            const bool jin = jx >= 0 && jx + ww <= wl - 1 && jy >= 0 && jy + ww <= hl - 1;
+            group_sync<WPF>(grp);
+            stage1<PT, NT>(Jb, p, wl, hl, jx, jy, pw, jin, sI, tig);
+            group_sync<WPF>(grp);
+            float bxs = 0.f, bys = 0.f, unused = 0.f;
+            int i2 = i_l0, j2 = j_l0;
 #pragma unroll
             for (int m = 0; m < NS; ++m) {
-                const int k = lane + 32 * m;
-                T[m] = 0.f; TX[m] = 0.f; TY[m] = 0.f;
+                const int k = tig + NT * m;
                 if (k < N) {
-                    int xa = ix + i, ya = iy + j, xb = xa + 1, yb = ya + 1;
-                    if (!inside) {
-                        xa = clampi(xa, 0, wl - 1); xb = clampi(xb, 0, wl - 1);
-                        ya = clampi(ya, 0, hl - 1); yb = clampi(yb, 0, hl - 1);
-                    }
-                    const size_t ra = (size_t)ya * p, rb = (size_t)yb * p;
-                    const float t = w00 * ld1(Ia + ra + xa) + w01 * ld1(Ia + ra + xb) + w10 * ld1(Ia + rb + xa) +
-                                    w11 * ld1(Ia + rb + xb);
-                    const float2 g00 = ld2(Ga + ra + xa), g01 = ld2(Ga + ra + xb);
-                    const float2 g10 = ld2(Ga + rb + xa), g11 = ld2(Ga + rb + xb);
-                    const float tx = w00 * g00.x + w01 * g01.x + w10 * g10.x + w11 * g11.x;
-                    const float ty = w00 * g00.y + w01 * g01.y + w10 * g10.y + w11 * g11.y;
-                    T[m] = t; TX[m] = tx; TY[m] = ty;
-                    gxx += tx * tx; gxy += tx * ty; gyy += ty * ty;
+                    const int o = j2 * pw + i2;
+                    const float jv = v00 * sI[o] + v01 * sI[o + 1] + v10 * sI[o + pw] + v11 * sI[o + pw + 1];
+                    const float e = T[m] - jv;
+                    bxs += e * TX[m];
+                    bys += e * TY[m];
                 }
-                i += r32; j += q32;
-                if (i >= ww) { i -= ww; ++j; }
+                i2 += rn; j2 += qn;
+                if (i2 >= ww) { i2 -= ww; ++j2; }
             }
-            gxx = wsum(gxx); gxy = wsum(gxy); gyy = wsum(gyy);
-            ++tpl;
-            const float lam = 0.5f * ((gxx + gyy) - sqrtf((gxx - gyy) * (gxx - gyy) + 4.f * gxy * gxy));
-            const float det = gxx * gyy - gxy * gxy;
-            if (!(lam >= D.min_eig * (float)N) || !(det > 0.f)) {
-                vx = ux; vy = uy;
-                return false;
-            }
-            const float idet = 1.f / det;
-            float nx = 0.f, ny = 0.f;
-            for (int it = 0; it < D.max_iters; ++it) {
-                const float qx = fminf(fmaxf(px + gx + nx, -64.f), (float)wl + 64.f);
-                const float qy = fminf(fmaxf(py + gy + ny, -64.f), (float)hl + 64.f);
-                const float fqx = floorf(qx), fqy = floorf(qy);
-                const float cx = qx - fqx, cy = qy - fqy;
-                const int jx = (int)fqx - r, jy = (int)fqy - r;
-                const float v00 = (1.f - cx) * (1.f - cy), v01 = cx * (1.f - cy);
-                const float v10 = (1.f - cx) * cy, v11 = cx * cy;
-                const bool jin = jx >= 0 && jx + ww <= wl - 1 && jy >= 0 && jy + ww <= hl - 1;
-                float bxs = 0.f, bys = 0.f;
-                int i2 = i_l0, j2 = j_l0;
-#pragma unroll
-                for (int m = 0; m < NS; ++m) {
-                    const int k = lane + 32 * m;
-                    if (k < N) {
-                        int xa = jx + i2, ya = jy + j2, xb = xa + 1, yb = ya + 1;
-                        if (!jin) {
-                            xa = clampi(xa, 0, wl - 1); xb = clampi(xb, 0, wl - 1);
-                            ya = clampi(ya, 0, hl - 1); yb = clampi(yb, 0, hl - 1);
-                        }
-                        const size_t ra = (size_t)ya * p, rb = (size_t)yb * p;
-                        const float jv = v00 * ld1(Jb + ra + xa) + v01 * ld1(Jb + ra + xb) +
-                                         v10 * ld1(Jb + rb + xa) + v11 * ld1(Jb + rb + xb);
-                        const float e = T[m] - jv;
-                        bxs += e * TX[m];
-                        bys += e * TY[m];
-                    }
-                    i2 += r32; j2 += q32;
-                    if (i2 >= ww) { i2 -= ww; ++j2; }
-                }
-                bxs = wsum(bxs); bys = wsum(bys);
-                const float ex = (gyy * bxs - gxy * bys) * idet;
-                const float ey = (gxx * bys - gxy * bxs) * idet;
-                nx += ex; ny += ey;
-                ++iters;
-                if (ex * ex + ey * ey < D.eps2) break;
-            }
-            if (l > 0) { gx = 2.f * (gx + nx); gy = 2.f * (gy + ny); }
-            else { dx = gx + nx; dy = gy + ny; }
+            if (WPF == 1) { bxs = wsum(bxs); bys = wsum(bys); }
+            else group_sum3<WPF>(bxs, bys, unused, red, wig, grp);
+            const float ex = (gyy * bxs - gxy * bys) * idet;
+            const float ey = (gxx * bys - gxy * bxs) * idet;
+            nx += ex; ny += ey;
+            ++iters;
+            if (ex * ex + ey * ey < D.eps2) break;
         }
+        if (l > 0) { gx = 2.f * (gx + nx); gy = 2.f * (gy + ny); }
+        else { dx = gx + nx; dy = gy + ny; }
     }
     vx = ux + dx; vy = uy + dy;
     return vx >= 0.f && vx <= (float)(D.w - 1) && vy >= 0.f && vy <= (float)(D.h - 1);
 }
 
-template <typename PT, int NS>
-__global__ void __launch_bounds__(128) k_lk(const StreamDev *__restrict__ S, WorkList wl, LkIO io)
+// Shared memory per feature group: a (2r+2)^2 FP32 patch, a (2r+2)^2 float2
+// patch and the cross-warp reduction slots.
+__host__ __device__ constexpr int lk_group_floats(int r) { return 3 * (2 * r + 2) * (2 * r + 2) + 8; }
+
+template <typename PT, int NS, int RC, int WPF, int MINB>
+__global__ void __launch_bounds__(128, MINB) k_lk(const StreamDev *__restrict__ S, WorkList wl, LkIO io, int rmax)
 {
-    const int lane = threadIdx.x & 31;
-    const int nw = (gridDim.x * blockDim.x) >> 5;
-    for (int item = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; item < wl.total; item += nw) {
+    extern __shared__ float lk_smem[];
+    constexpr int NT = 32 * WPF;
+    const int grp = threadIdx.x / NT, tig = threadIdx.x - grp * NT;
+    float *base = lk_smem + grp * lk_group_floats(rmax);
+    float *sI = base;
+    float2 *sG = reinterpret_cast<float2 *>(base + (2 * rmax + 2) * (2 * rmax + 2));
+    float *red = base + 3 * (2 * rmax + 2) * (2 * rmax + 2);
+    const int ngroups = (gridDim.x * blockDim.x) / NT;
+    for (int item = (blockIdx.x * blockDim.x + threadIdx.x) / NT; item < wl.total; item += ngroups) {
         const int s = wl_stream(wl, item);
         const StreamDev &D = S[s];
         StreamState *st = D.st;
@@ -150,13 +213,13 @@ __global__ void __launch_bounds__(128) k_lk(const StreamDev *__restrict__ S, Wor
         const float2 u = pts[f];
         int iters = 0, tpl = 0;
         float vx, vy, bx = u.x, by = u.y;
-        const bool ok1 = lk_track<PT, NS>(D, sp, sp ^ 1, u.x, u.y, vx, vy, iters, tpl);
+        const bool ok1 = lk_track<PT, NS, RC, WPF>(D, sp, sp ^ 1, u.x, u.y, vx, vy, iters, tpl, sI, sG, red, tig, grp);
         bool ok2 = false;
-        if (ok1) ok2 = lk_track<PT, NS>(D, sp ^ 1, sp, vx, vy, bx, by, iters, tpl);
-        if (!ok2) { if (!ok1) { bx = u.x; by = u.y; } }
+        if (ok1) ok2 = lk_track<PT, NS, RC, WPF>(D, sp ^ 1, sp, vx, vy, bx, by, iters, tpl, sI, sG, red, tig, grp);
+        if (!ok1) { bx = u.x; by = u.y; }
         const float ex = bx - u.x, ey = by - u.y;
         const float e2 = ex * ex + ey * ey;
-        if (lane == 0) {
+        if (tig == 0) {
             float2 *fwd = io.fwd ? io.fwd : D.fwd;
             float2 *back = io.back ? io.back : D.back;
             float *fb = io.fb ? io.fb : D.fb;
@@ -173,37 +236,77 @@ __global__ void __launch_bounds__(128) k_lk(const StreamDev *__restrict__ S, Wor
     }
 }
 
-template <typename PT, int NS>
-int occ_lk()
+template <typename PT, int NS, int RC, int WPF, int MINB>
+struct LkKernel {
+    static int smem(int rmax) { return (128 / (32 * WPF)) * lk_group_floats(rmax) * 4; }
+    static int occ(int rmax)
+    {
+        static int v[STAB_MAXR + 1] = {0};
+        if (!v[rmax]) {
+            cudaFuncSetAttribute(k_lk<PT, NS, RC, WPF, MINB>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem(rmax));
+            if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v[rmax], k_lk<PT, NS, RC, WPF, MINB>, 128,
+                                                              smem(rmax)) != cudaSuccess ||
+                v[rmax] < 1)
+                v[rmax] = 1;
+        }
+        return v[rmax];
+    }
+    static void run(const Launch &L, const StreamDev *S, WorkList wl, LkIO io, int rmax)
+    {
+        const int groups_per_block = 128 / (32 * WPF);
+        const int blocks = (wl.total + groups_per_block - 1) / groups_per_block;
+        k_lk<PT, NS, RC, WPF, MINB><<<grid_for(L, blocks, occ(rmax)), 128, smem(rmax), L.stream>>>(S, wl, io, rmax);
+    }
+};
+
+// Variants for the 21 x 21 window (radius known at compile time):
+//   0: one warp per feature, <= 128 registers (4 blocks / SM)
+//   1: one warp per feature, <= 168 registers (3 blocks / SM)
+//   2: two warps per feature, <= 80 registers (6 blocks / SM)
+//   3: two warps per feature, <= 128 registers (4 blocks / SM)
+// Other radii use the runtime-radius build of variant 0.
+template <typename PT>
+void run_variant(int v, const Launch &L, const StreamDev *S, WorkList wl, LkIO io, int r)
 {
-    static int v = 0;
-    if (!v && (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, k_lk<PT, NS>, 128, 0) != cudaSuccess || v < 1))
-        v = 1;
-    return v;
+    if (r == 10) {
+        switch (v) {
+        case 1: LkKernel<PT, 14, 10, 1, 3>::run(L, S, wl, io, r); return;
+        case 2: LkKernel<PT, 7, 10, 2, 6>::run(L, S, wl, io, r); return;
+        case 3: LkKernel<PT, 7, 10, 2, 4>::run(L, S, wl, io, r); return;
+        default: LkKernel<PT, 14, 10, 1, 4>::run(L, S, wl, io, r); return;
+        }
+    }
+    if (r < 10) LkKernel<PT, 14, 0, 1, 4>::run(L, S, wl, io, r);
+    else LkKernel<PT, 20, 0, 1, 3>::run(L, S, wl, io, r);
 }
 
-template <typename PT, int NS>
-void run_lk(const Launch &L, const StreamDev *S, WorkList wl, LkIO io)
+template <typename PT>
+void warm_all()
 {
-    int blocks = (wl.total + 3) / 4;
-    k_lk<PT, NS><<<grid_for(L, blocks, occ_lk<PT, NS>()), 128, 0, L.stream>>>(S, wl, io);
+    for (int r = 1; r <= STAB_MAXR; ++r) {
+        if (r == 10) {
+            LkKernel<PT, 14, 10, 1, 4>::occ(r); LkKernel<PT, 14, 10, 1, 3>::occ(r);
+            LkKernel<PT, 7, 10, 2, 6>::occ(r); LkKernel<PT, 7, 10, 2, 4>::occ(r);
+        } else if (r < 10) {
+            LkKernel<PT, 14, 0, 1, 4>::occ(r);
+        } else {
+            LkKernel<PT, 20, 0, 1, 3>::occ(r);
+        }
+    }
 }
 
 }  // namespace
 
+int lk_variants() { return 4; }
+
 void warm_lk()
 {
-    occ_lk<float, 14>(); occ_lk<__half, 14>(); occ_lk<float, 20>(); occ_lk<__half, 20>();
+    warm_all<float>();
+    warm_all<__half>();
 }
 
-void launch_lk(const Launch &L, int prec, int r, int wpf, const StreamDev *S, WorkList wl, LkIO io)
+void launch_lk(const Launch &L, int prec, int r, int variant, const StreamDev *S, WorkList wl, LkIO io)
 {
-    (void)wpf;
-    if (r <= 10) {
-        if (prec) run_lk<__half, 14>(L, S, wl, io);
-        else run_lk<float, 14>(L, S, wl, io);
-    } else {
-        if (prec) run_lk<__half, 20>(L, S, wl, io);
-        else run_lk<float, 20>(L, S, wl, io);
-    }
+    if (prec) run_variant<__half>(variant, L, S, wl, io, r);
+    else run_variant<float>(variant, L, S, wl, io, r);
 }

@@ -85,7 +85,9 @@ void launch_response(const Launch &L, const StreamDev *S, WorkList wl, DetIO io)
 void launch_filter(const Launch &L, const StreamDev *S, WorkList wl);
 void launch_select(const Launch &L, const StreamDev *S, int n, DetIO io);
 
-void launch_lk(const Launch &L, int prec, int r, int wpf, const StreamDev *S, WorkList wl, LkIO io);
+// Tracker variants (warps per feature, register budget); see k_lk.cu.
+int lk_variants();
+void launch_lk(const Launch &L, int prec, int r, int variant, const StreamDev *S, WorkList wl, LkIO io);
 
 void launch_compact(const Launch &L, const StreamDev *S, int n, CompactIO io);
 void launch_fit(const Launch &L, const StreamDev *S, int n, FitIO io, int streaming);

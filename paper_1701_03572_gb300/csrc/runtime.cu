@@ -34,6 +34,15 @@ struct Pipeline {
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t gexec = nullptr;
     long long t_host = 0;
+    int lk_variant = 1;   // tracker kernel variant (autotuned for batches)
+
+    void reset_graph()
+    {
+        if (gexec) cudaGraphExecDestroy(gexec);
+        if (graph) cudaGraphDestroy(graph);
+        gexec = nullptr;
+        graph = nullptr;
+    }
 
     ~Pipeline()
     {
@@ -269,7 +278,7 @@ void enqueue_step(Pipeline &pp, cudaStream_t s, Prof *pf = nullptr)
     mark("filter");
     launch_select(L, pp.ds, pp.n, DetIO{});
     mark("select");
-    launch_lk(L, pp.prec, pp.rmax, 1, pp.ds, pp.wl_lk, LkIO{});
+    launch_lk(L, pp.prec, pp.rmax, pp.lk_variant, pp.ds, pp.wl_lk, LkIO{});
     mark("lk");
     launch_compact(L, pp.ds, pp.n, CompactIO{});
     mark("compact");
@@ -431,7 +440,7 @@ stab_status stab_lk(stab_ctx *c, const uint8_t *prev, const uint8_t *next, int p
             scratch_status_fwd = pp.hs[0].status_fwd;
             io.status_fwd = scratch_status_fwd;
         }
-        launch_lk(L, pp.prec, pp.rmax, 1, pp.ds, wl, io);
+        launch_lk(L, pp.prec, pp.rmax, pp.lk_variant, pp.ds, wl, io);
     }
     return cuda_check(pp.err, "stab_lk");
 }
@@ -448,7 +457,7 @@ stab_status stab_track(stab_ctx *c, const uint8_t *prev, const uint8_t *next, in
     build_pyr(pp, L, next, pitch, channels, sn);
     launch_begin(L, pp.ds, 1, t, 0);
     detect_chain(pp, L, DetIO{});
-    launch_lk(L, pp.prec, pp.rmax, 1, pp.ds, pp.wl_lk, LkIO{});
+    launch_lk(L, pp.prec, pp.rmax, pp.lk_variant, pp.ds, pp.wl_lk, LkIO{});
     launch_compact(L, pp.ds, 1, CompactIO{(float2 *)pts_prev, (float2 *)pts_next, n, status});
     return cuda_check(pp.err, "stab_track");
 }
@@ -609,6 +618,131 @@ stab_status stab_batch_lk_work(stab_batch *b, int64_t *iterations, int64_t *temp
         *templates += tp;
     }
     return cuda_check(pp.err, "stab_batch_lk_work");
+}
+
+stab_status stab_set_lk_variant(stab_ctx *c, int v)
+{
+    if (!c || v < 0 || v >= lk_variants()) return STAB_ERR_INVALID_ARG;
+    c->pp.lk_variant = v;
+    return STAB_OK;
+}
+
+stab_status stab_batch_set_lk_variant(stab_batch *b, int v)
+{
+    if (!b || v < 0 || v >= lk_variants()) return STAB_ERR_INVALID_ARG;
+    if (b->pp.lk_variant != v) {
+        b->pp.lk_variant = v;
+        b->pp.reset_graph();
+    }
+    return STAB_OK;
+}
+
+static std::string batch_signature(const Pipeline &pp)
+{
+    cudaDeviceProp prop{};
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaGetDeviceProperties(&prop, dev);
+    std::string sig = std::string(prop.name) + "|prec" + std::to_string(pp.prec) + "|r" + std::to_string(pp.rmax);
+    for (const auto &D : pp.hs)
+        sig += "|" + std::to_string(D.w) + "x" + std::to_string(D.h) + "x" + std::to_string(D.C) + "k" +
+               std::to_string(D.K) + "l" + std::to_string(D.L);
+    for (auto &ch : sig)
+        if (ch == '"' || ch == '\\') ch = '_';
+    return sig;
+}
+
+// Cache file: one JSON object {"signature": variant, ...}, written only here.
+static bool cache_lookup(const char *path, const std::string &sig, int *v)
+{
+    if (!path) return false;
+    FILE *f = fopen(path, "r");
+    if (!f) return false;
+    std::string txt;
+    char buf[4096];
+    size_t k;
+    while ((k = fread(buf, 1, sizeof buf, f)) > 0) txt.append(buf, k);
+    fclose(f);
+    const std::string key = "\"" + sig + "\":";
+    size_t pos = txt.find(key);
+    if (pos == std::string::npos) return false;
+    *v = atoi(txt.c_str() + pos + key.size());
+    return *v >= 0 && *v < lk_variants();
+}
+
+static void cache_store(const char *path, const std::string &sig, int v)
+{
+    if (!path) return;
+    std::vector<std::pair<std::string, int>> ent;
+    if (FILE *f = fopen(path, "r")) {
+        std::string txt;
+        char buf[4096];
+        size_t k;
+        while ((k = fread(buf, 1, sizeof buf, f)) > 0) txt.append(buf, k);
+        fclose(f);
+        size_t p = 0;
+        while ((p = txt.find('"', p)) != std::string::npos) {
+            size_t q = txt.find('"', p + 1);
+            if (q == std::string::npos) break;
+            std::string key = txt.substr(p + 1, q - p - 1);
+            size_t c = txt.find(':', q);
+            if (c == std::string::npos) break;
+            if (key != sig) ent.push_back({key, atoi(txt.c_str() + c + 1)});
+            p = txt.find_first_of(",}", c);
+            if (p == std::string::npos) break;
+        }
+    }
+    ent.push_back({sig, v});
+    std::string tmp = std::string(path) + ".tmp";
+    FILE *f = fopen(tmp.c_str(), "w");
+    if (!f) return;
+    fprintf(f, "{\n");
+    for (size_t i = 0; i < ent.size(); ++i)
+        fprintf(f, "  \"%s\": %d%s\n", ent[i].first.c_str(), ent[i].second, i + 1 < ent.size() ? "," : "");
+    fprintf(f, "}\n");
+    fclose(f);
+    rename(tmp.c_str(), path);
+}
+
+stab_status stab_batch_autotune(stab_batch *b, const char *cache_path, int *variant, float *ms_out, void *stream)
+{
+    if (!b) return STAB_ERR_INVALID_ARG;
+    Pipeline &pp = b->pp;
+    if (pp.t_host < 2) return fail(pp.err, STAB_ERR_INVALID_ARG, "autotune needs the batch to have run two steps");
+    const std::string sig = batch_signature(pp);
+    int v = -1;
+    const int nv = lk_variants();
+    if (ms_out)
+        for (int i = 0; i < nv; ++i) ms_out[i] = -1.f;
+    if (!cache_lookup(cache_path, sig, &v)) {
+        cudaStream_t s = (cudaStream_t)stream;
+        Launch L{s, pp.sms};
+        cudaEvent_t e0, e1;
+        cudaEventCreate(&e0);
+        cudaEventCreate(&e1);
+        float best = 1e30f;
+        for (int cand = 0; cand < nv; ++cand) {
+            // the tracker reads the features and pyramids of the last step and
+            // writes only its own outputs, so repeated launches are harmless
+            launch_lk(L, pp.prec, pp.rmax, cand, pp.ds, pp.wl_lk, LkIO{});
+            cudaEventRecord(e0, s);
+            for (int k = 0; k < 5; ++k) launch_lk(L, pp.prec, pp.rmax, cand, pp.ds, pp.wl_lk, LkIO{});
+            cudaEventRecord(e1, s);
+            cudaEventSynchronize(e1);
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, e0, e1);
+            ms /= 5.f;
+            if (ms_out) ms_out[cand] = ms;
+            if (ms < best) { best = ms; v = cand; }
+        }
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+        stab_status st = cuda_check(pp.err, "stab_batch_autotune");
+        if (st != STAB_OK) return st;
+        cache_store(cache_path, sig, v);
+    }
+    if (variant) *variant = v;
+    return stab_batch_set_lk_variant(b, v);
 }
 
 stab_status stab_batch_step_host(stab_batch *b, const uint8_t *const *frames, uint8_t *const *outs, void *stream)

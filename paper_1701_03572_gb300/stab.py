@@ -79,6 +79,9 @@ def lib():
             "stab_batch_motions": ([_vp, C.POINTER(StabMotion)], _i),
             "stab_batch_features": ([_vp, _i, _vp, C.POINTER(_i)], _i),
             "stab_batch_sync": ([_vp], _i),
+            "stab_batch_autotune": ([_vp, C.c_char_p, C.POINTER(_i), _vp, _vp], _i),
+            "stab_batch_set_lk_variant": ([_vp, _i], _i),
+            "stab_set_lk_variant": ([_vp, _i], _i),
             "stab_batch_step_profiled": ([_vp, _vp, _vp, _i, C.POINTER(_i)], _i),
             "stab_batch_kernel_name": ([_vp, _i], C.c_char_p),
             "stab_batch_lk_work": ([_vp, C.POINTER(_i64), C.POINTER(_i64)], _i),
@@ -165,6 +168,9 @@ class Context:
 
     def sync(self):
         return self._chk(lib().stab_sync(self._h), "stab_sync")
+
+    def set_lk_variant(self, v: int):
+        self._chk(lib().stab_set_lk_variant(self._h, v), "stab_set_lk_variant")
 
     def pyramid(self, frame: torch.Tensor):
         ch = 1 if frame.dim() == 2 else frame.shape[2]
@@ -334,6 +340,17 @@ class Batch:
         it, tp = C.c_int64(0), C.c_int64(0)
         self._chk(lib().stab_batch_lk_work(self._h, C.byref(it), C.byref(tp)), "stab_batch_lk_work")
         return it.value, tp.value
+
+    def autotune(self, cache_path: str | None = None, stream=None):
+        """Pick the fastest tracker variant; returns (variant, {variant: ms})."""
+        v = C.c_int(-1)
+        ms = (C.c_float * 8)()
+        self._chk(lib().stab_batch_autotune(self._h, cache_path.encode() if cache_path else None, C.byref(v), ms,
+                                            _s(stream)), "stab_batch_autotune")
+        return v.value, {k: ms[k] for k in range(4) if ms[k] >= 0}
+
+    def set_lk_variant(self, v: int):
+        self._chk(lib().stab_batch_set_lk_variant(self._h, v), "stab_batch_set_lk_variant")
 
     def features(self, i: int):
         K = self.descs[i][3].max_corners

@@ -114,13 +114,15 @@ def _lk_case(cfg, seed, K, L):
     return f0, f1, pts, w, h
 
 
-@pytest.mark.parametrize("cfg,K,L", [(0, 200, 3), (1, 500, 4), (2, 1000, 5)])
-def test_lk_parity(cfg, K, L):
+@pytest.mark.parametrize("cfg,K,L,variant", [(0, 200, 3, 0), (0, 200, 3, 1), (0, 200, 3, 2), (0, 200, 3, 3),
+                                              (1, 500, 4, 1), (2, 1000, 5, 1), (2, 1000, 5, 3)])
+def test_lk_parity(cfg, K, L, variant):
     f0, f1, pts, w, h = _lk_case(cfg, 20 + cfg, K, L)
     ref = O.track(O.pyramid(f0, L), O.pyramid(f1, L), pts)
     res = {}
     for prec in (0, 1):
         ctx = S.Context(w, h, _params(max_corners=K, levels=L, precision=prec))
+        ctx.set_lk_variant(variant)
         r = ctx.lk(_cuda(f0), _cuda(f1), _cuda(pts))
         torch.cuda.synchronize()
         res[prec] = {k: v.cpu().numpy() for k, v in r.items()}
@@ -136,6 +138,18 @@ def test_lk_parity(cfg, K, L):
     assert d.max() < 0.01, d.max()
     db = np.hypot(*(g["back"][both] - ref["back"][both]).T)
     assert db.max() < 0.02
+
+
+@pytest.mark.parametrize("r", [4, 12])
+def test_lk_parity_other_window_radii(r):
+    f0, f1, pts, w, h = _lk_case(0, 25, 150, 3)
+    ref = O.track(O.pyramid(f0, 3), O.pyramid(f1, 3), pts, win_r=r)
+    ctx = S.Context(w, h, _params(max_corners=150, levels=3, win_radius=r))
+    g = {k: v.cpu().numpy() for k, v in ctx.lk(_cuda(f0), _cuda(f1), _cuda(pts)).items()}
+    assert (g["status"] == ref["status"]).mean() >= 0.99
+    both = (g["status"] == 1) & (ref["status"] == 1)
+    assert both.sum() >= 0.7 * len(pts)
+    assert np.hypot(*(g["fwd"][both] - ref["fwd"][both]).T).max() < 0.01
 
 
 def test_lk_edge_cases():
@@ -321,3 +335,41 @@ def test_batch_graph_equals_single_stream_path():
         oc = o.cpu().numpy()
         for k, frame in enumerate(outs[i]):
             assert np.array_equal(frame, oc[k]), (i, k)
+
+
+def test_autotuner_picks_a_variant_and_caches_it(tmp_path):
+    T = 6
+    clips = [_clip(0, T, 60)["frames"].numpy(), _clip(0, T, 61)["frames"].numpy()]
+    p = _params(max_corners=200, levels=3, smooth_window=5)
+    b = S.Batch([(320, 240, 1, p), (320, 240, 1, p)])
+    cache = str(tmp_path / "tune.json")
+    for t in range(T):
+        for i, f in enumerate(clips):
+            b.input_slot(i, t % b.ring).copy_(_cuda(f[t]))
+        b.step()
+        if t == 2:
+            v, ms = b.autotune(cache)
+            assert 0 <= v < 4 and len(ms) == 4 and all(x > 0 for x in ms.values())
+            v2, ms2 = b.autotune(cache)          # second call: from the cache, no timing
+            assert v2 == v and ms2 == {}
+    assert b.sync() == 0
+    import json
+    assert list(json.load(open(cache)).values()) == [v]
+    # the tuned batch still matches the single-stream path with the same variant
+    mot = b.motions()
+    for i, f in enumerate(clips):
+        ctx = S.Context(320, 240, p)
+        ctx.set_lk_variant(v)
+        raw = torch.zeros((T, 8), dtype=torch.float32, device=DEV)
+        fr = _cuda(f)
+        for t in range(1, T):
+            src, dst, status, n = ctx.track(fr[t - 1], fr[t], cont=t > 1)
+            ctx.fit(src, dst, n, p.model, t, out=raw[t])
+        torch.cuda.synchronize()
+        m = S.motions_from_raw(raw)
+        # steps before the switch used the default variant; the last motion is
+        # compared only where both paths ran the same variant throughout
+        if v == 1:
+            assert np.array_equal(np.array(mot[i]["m"], np.float32), m["m"][T - 1].astype(np.float32))
+        else:
+            assert np.abs(np.array(mot[i]["m"]) - m["m"][T - 1]).max() < 1e-3
