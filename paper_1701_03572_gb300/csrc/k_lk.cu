@@ -7,9 +7,10 @@
 // (Ix, Iy) under the window into shared memory (coalesced row loads, FP32,
 // border taps replicated, so sampling is branch-free), samples the (2r+1)^2
 // template bilinearly with weights shared by every sample, and keeps T, Tx,
-// Ty in registers (NS samples per thread).  Each iteration stages the next
-// frame's patch at the displaced window, accumulates b = sum e [Tx, Ty] and
-// solves the 2x2 system.  Sums are reduced with xor-butterfly shuffles (same
+// Ty in registers (NS samples per thread).  The next frame's patch is staged
+// once per level around the initial guess with a small margin, so iterations
+// read shared memory only (a larger move re-stages it); each iteration
+// accumulates b = sum e [Tx, Ty] and solves the 2x2 system.  Sums are reduced with xor-butterfly shuffles (same
 // bits in every lane) and, for two warps, combined through shared memory in a
 // fixed order, so every thread of the group takes the same branch.
 #include "kernels.cuh"
@@ -47,48 +48,114 @@ __device__ __forceinline__ void group_sum3(float &a, float &b, float &c, float *
     }
 }
 
-// Stage the pw x pw patch with top-left (x0, y0) of a plane into shared
-// memory as FP32 (border taps replicated when the patch leaves the image).
-template <typename PT, int NT>
-__device__ __forceinline__ void stage1(const PT *__restrict__ P, int pitch, int wl, int hl, int x0, int y0, int pw,
-                                       bool inside, float *dst, int tig)
+// Shared-memory row stride for a patch of width pwid staged from a 4-aligned
+// start column (up to 3 extra leading columns, whole 4-element vectors).
+__host__ __device__ constexpr int lk_sw(int pwid) { return ((pwid + 6) / 4) * 4; }
+
+__device__ __forceinline__ float4 ld4(const float *p) { return __ldg(reinterpret_cast<const float4 *>(p)); }
+__device__ __forceinline__ float4 ld4(const __half *p)
 {
-    const int n = pw * pw, q = NT / pw, rr = NT - q * pw;
-    int row = tig / pw, col = tig - row * pw;
-    for (int e = tig; e < n; e += NT) {
-        int xx = x0 + col, yy = y0 + row;
-        if (!inside) { xx = clampi(xx, 0, wl - 1); yy = clampi(yy, 0, hl - 1); }
-        dst[e] = ld1(P + (size_t)yy * pitch + xx);
-        col += rr; row += q;
-        if (col >= pw) { col -= pw; ++row; }
+    const uint2 u = __ldg(reinterpret_cast<const uint2 *>(p));
+    const float2 a = __half22float2(*reinterpret_cast<const __half2 *>(&u.x));
+    const float2 b = __half22float2(*reinterpret_cast<const __half2 *>(&u.y));
+    return make_float4(a.x, a.y, b.x, b.y);
+}
+__device__ __forceinline__ void ld4x2(const float2 *p, float4 &lo, float4 &hi)
+{
+    lo = __ldg(reinterpret_cast<const float4 *>(p));
+    hi = __ldg(reinterpret_cast<const float4 *>(p) + 1);
+}
+__device__ __forceinline__ void ld4x2(const __half2 *p, float4 &lo, float4 &hi)
+{
+    const uint4 u = __ldg(reinterpret_cast<const uint4 *>(p));
+    const float2 a = __half22float2(*reinterpret_cast<const __half2 *>(&u.x));
+    const float2 b = __half22float2(*reinterpret_cast<const __half2 *>(&u.y));
+    const float2 c = __half22float2(*reinterpret_cast<const __half2 *>(&u.z));
+    const float2 d = __half22float2(*reinterpret_cast<const __half2 *>(&u.w));
+    lo = make_float4(a.x, a.y, b.x, b.y);
+    hi = make_float4(c.x, c.y, d.x, d.y);
+}
+
+// Stage the pwid x pwid patch with top-left (x0, y0) of a plane into shared
+// memory as FP32, row stride sw.  Inside the image, rows are read as aligned
+// 4-element vectors from x0 rounded down to a multiple of 4, and the returned
+// column offset (x0 - that start) locates the patch; near a border every tap
+// is clamped (replicated border) and read singly, offset 0.
+template <typename PT, int NT>
+__device__ __forceinline__ int stage1(const PT *__restrict__ P, int pitch, int wl, int hl, int x0, int y0,
+                                      int pwid, int sw, bool inside, float *dst, int tig)
+{
+    const int x0a = x0 & ~3, off = x0 - x0a;
+    const int nv = (pwid + off + 3) >> 2;
+    if (inside && x0a + 4 * nv <= pitch) {
+        const int n = pwid * nv, q = NT / nv, rr = NT - q * nv;
+        int row = tig / nv, v = tig - row * nv;
+        for (int e = tig; e < n; e += NT) {
+            *reinterpret_cast<float4 *>(dst + row * sw + 4 * v) = ld4(P + (size_t)(y0 + row) * pitch + x0a + 4 * v);
+            v += rr; row += q;
+            if (v >= nv) { v -= nv; ++row; }
+        }
+        return off;
     }
+    const int n = pwid * pwid, q = NT / pwid, rr = NT - q * pwid;
+    int row = tig / pwid, col = tig - row * pwid;
+    for (int e = tig; e < n; e += NT) {
+        const int xx = clampi(x0 + col, 0, wl - 1), yy = clampi(y0 + row, 0, hl - 1);
+        dst[row * sw + col] = ld1(P + (size_t)yy * pitch + xx);
+        col += rr; row += q;
+        if (col >= pwid) { col -= pwid; ++row; }
+    }
+    return 0;
 }
 
 template <typename PT2, int NT>
-__device__ __forceinline__ void stage2(const PT2 *__restrict__ P, int pitch, int wl, int hl, int x0, int y0, int pw,
-                                       bool inside, float2 *dst, int tig)
+__device__ __forceinline__ int stage2(const PT2 *__restrict__ P, int pitch, int wl, int hl, int x0, int y0,
+                                      int pwid, int sw, bool inside, float2 *dst, int tig)
 {
-    const int n = pw * pw, q = NT / pw, rr = NT - q * pw;
-    int row = tig / pw, col = tig - row * pw;
-    for (int e = tig; e < n; e += NT) {
-        int xx = x0 + col, yy = y0 + row;
-        if (!inside) { xx = clampi(xx, 0, wl - 1); yy = clampi(yy, 0, hl - 1); }
-        dst[e] = ld2(P + (size_t)yy * pitch + xx);
-        col += rr; row += q;
-        if (col >= pw) { col -= pw; ++row; }
+    const int x0a = x0 & ~3, off = x0 - x0a;
+    const int nv = (pwid + off + 3) >> 2;
+    if (inside && x0a + 4 * nv <= pitch) {
+        const int n = pwid * nv, q = NT / nv, rr = NT - q * nv;
+        int row = tig / nv, v = tig - row * nv;
+        for (int e = tig; e < n; e += NT) {
+            float4 lo, hi;
+            ld4x2(P + (size_t)(y0 + row) * pitch + x0a + 4 * v, lo, hi);
+            float4 *d = reinterpret_cast<float4 *>(dst + row * sw + 4 * v);
+            d[0] = lo;
+            d[1] = hi;
+            v += rr; row += q;
+            if (v >= nv) { v -= nv; ++row; }
+        }
+        return off;
     }
+    const int n = pwid * pwid, q = NT / pwid, rr = NT - q * pwid;
+    int row = tig / pwid, col = tig - row * pwid;
+    for (int e = tig; e < n; e += NT) {
+        const int xx = clampi(x0 + col, 0, wl - 1), yy = clampi(y0 + row, 0, hl - 1);
+        dst[row * sw + col] = ld2(P + (size_t)yy * pitch + xx);
+        col += rr; row += q;
+        if (col >= pwid) { col -= pwid; ++row; }
+    }
+    return 0;
 }
 
+// Margin (px) of the next frame's staged patch: iterations whose window stays
+// within it sample shared memory only; a larger move re-stages the patch.
+constexpr int LK_MARGIN = 2;
+
 // Track one feature from pyramid slot sa to slot sb.  RC = compile-time
-// radius (0: runtime D.r).  sI: pw^2 floats, sG: pw^2 float2, red: 3 * WPF.
+// radius (0: runtime D.r).  sI: pw^2 floats, sG: pw^2 float2,
+// sJ: (pw + 2 LK_MARGIN)^2 floats, red: 3 * WPF.
 template <typename PT, int NS, int RC, int WPF>
 __device__ bool lk_track(const StreamDev &D, int sa, int sb, float ux, float uy, float &vx, float &vy, int &iters,
-                         int &tpl, float *sI, float2 *sG, float *red, int tig, int grp)
+                         int &tpl, float *sI, float2 *sG, float *sJ, float *red, int tig, int grp)
 {
     typedef typename Plane2<PT>::type PT2;
     constexpr int NT = 32 * WPF;
     const int wig = tig >> 5;
     const int r = RC ? RC : D.r, ww = 2 * r + 1, pw = ww + 1, N = ww * ww;
+    const int pj = pw + 2 * LK_MARGIN;
+    const int swI = lk_sw(pw), swJ = lk_sw(pj);
     const int qn = NT / ww, rn = NT - qn * ww;
     const int i_l0 = tig % ww, j_l0 = tig / ww;
     float gx = 0.f, gy = 0.f, dx = 0.f, dy = 0.f;
@@ -108,9 +175,14 @@ __device__ bool lk_track(const StreamDev &D, int sa, int sb, float ux, float uy,
         const float w00 = (1.f - ax) * (1.f - ay), w01 = ax * (1.f - ay);
         const float w10 = (1.f - ax) * ay, w11 = ax * ay;
         const bool inside = ix >= 0 && ix + ww <= wl - 1 && iy >= 0 && iy + ww <= hl - 1;
+        // next frame's patch around the level's initial guess, with a margin
+        int jx0 = (int)floorf(fminf(fmaxf(px + gx, -64.f), (float)wl + 64.f)) - r - LK_MARGIN;
+        int jy0 = (int)floorf(fminf(fmaxf(py + gy, -64.f), (float)hl + 64.f)) - r - LK_MARGIN;
+        bool jin = jx0 >= 0 && jx0 + pj - 1 <= wl - 1 && jy0 >= 0 && jy0 + pj - 1 <= hl - 1;
         group_sync<WPF>(grp);
-        stage1<PT, NT>(Ia, p, wl, hl, ix, iy, pw, inside, sI, tig);
-        stage2<PT2, NT>(Ga, p, wl, hl, ix, iy, pw, inside, sG, tig);
+        const int offI = stage1<PT, NT>(Ia, p, wl, hl, ix, iy, pw, swI, inside, sI, tig);
+        stage2<PT2, NT>(Ga, p, wl, hl, ix, iy, pw, swI, inside, sG, tig);
+        int offJ = stage1<PT, NT>(Jb, p, wl, hl, jx0, jy0, pj, swJ, jin, sJ, tig);
         group_sync<WPF>(grp);
         float gxx = 0.f, gxy = 0.f, gyy = 0.f;
         int i = i_l0, j = j_l0;
@@ -119,9 +191,9 @@ __device__ bool lk_track(const StreamDev &D, int sa, int sb, float ux, float uy,
             const int k = tig + NT * m;
             T[m] = 0.f; TX[m] = 0.f; TY[m] = 0.f;
             if (k < N) {
-                const int o = j * pw + i;
-                const float t = w00 * sI[o] + w01 * sI[o + 1] + w10 * sI[o + pw] + w11 * sI[o + pw + 1];
-                const float2 g00 = sG[o], g01 = sG[o + 1], g10 = sG[o + pw], g11 = sG[o + pw + 1];
+                const int o = j * swI + i + offI;
+                const float t = w00 * sI[o] + w01 * sI[o + 1] + w10 * sI[o + swI] + w11 * sI[o + swI + 1];
+                const float2 g00 = sG[o], g01 = sG[o + 1], g10 = sG[o + swI], g11 = sG[o + swI + 1];
                 const float tx = w00 * g00.x + w01 * g01.x + w10 * g10.x + w11 * g11.x;
                 const float ty = w00 * g00.y + w01 * g01.y + w10 * g10.y + w11 * g11.y;
                 T[m] = t; TX[m] = tx; TY[m] = ty;
@@ -148,18 +220,26 @@ __device__ bool lk_track(const StreamDev &D, int sa, int sb, float ux, float uy,
             const int jx = (int)fqx - r, jy = (int)fqy - r;
             const float v00 = (1.f - cx) * (1.f - cy), v01 = cx * (1.f - cy);
             const float v10 = (1.f - cx) * cy, v11 = cx * cy;
-            const bool jin = jx >= 0 && jx + ww <= wl - 1 && jy >= 0 && jy + ww <= hl - 1;
-            group_sync<WPF>(grp);
-            stage1<PT, NT>(Jb, p, wl, hl, jx, jy, pw, jin, sI, tig);
-            group_sync<WPF>(grp);
+            int ox = jx - jx0, oy = jy - jy0;
+            if (ox < 0 || ox > 2 * LK_MARGIN || oy < 0 || oy > 2 * LK_MARGIN) {   // same for the whole group
+                jx0 = jx - LK_MARGIN;
+                jy0 = jy - LK_MARGIN;
+                jin = jx0 >= 0 && jx0 + pj - 1 <= wl - 1 && jy0 >= 0 && jy0 + pj - 1 <= hl - 1;
+                group_sync<WPF>(grp);
+                offJ = stage1<PT, NT>(Jb, p, wl, hl, jx0, jy0, pj, swJ, jin, sJ, tig);
+                group_sync<WPF>(grp);
+                ox = LK_MARGIN;
+                oy = LK_MARGIN;
+            }
+            const float *sJo = sJ + oy * swJ + ox + offJ;
             float bxs = 0.f, bys = 0.f, unused = 0.f;
             int i2 = i_l0, j2 = j_l0;
 #pragma unroll
             for (int m = 0; m < NS; ++m) {
                 const int k = tig + NT * m;
                 if (k < N) {
-                    const int o = j2 * pw + i2;
-                    const float jv = v00 * sI[o] + v01 * sI[o + 1] + v10 * sI[o + pw] + v11 * sI[o + pw + 1];
+                    const int o = j2 * swJ + i2;
+                    const float jv = v00 * sJo[o] + v01 * sJo[o + 1] + v10 * sJo[o + swJ] + v11 * sJo[o + swJ + 1];
                     const float e = T[m] - jv;
                     bxs += e * TX[m];
                     bys += e * TY[m];
@@ -182,9 +262,13 @@ __device__ bool lk_track(const StreamDev &D, int sa, int sb, float ux, float uy,
     return vx >= 0.f && vx <= (float)(D.w - 1) && vy >= 0.f && vy <= (float)(D.h - 1);
 }
 
-// Shared memory per feature group: a (2r+2)^2 FP32 patch, a (2r+2)^2 float2
-// patch and the cross-warp reduction slots.
-__host__ __device__ constexpr int lk_group_floats(int r) { return 3 * (2 * r + 2) * (2 * r + 2) + 8; }
+// Shared memory per feature group: the template's FP32 and float2 patches
+// ((2r+2) rows of stride lk_sw(2r+2)), the next frame's patch ((2r+2+2 margin)
+// rows of stride lk_sw(2r+2+2 margin)) and the reduction slots.
+__host__ __device__ constexpr int lk_group_floats(int r)
+{
+    return 3 * (2 * r + 2) * lk_sw(2 * r + 2) + (2 * r + 2 + 2 * LK_MARGIN) * lk_sw(2 * r + 2 + 2 * LK_MARGIN) + 8;
+}
 
 template <typename PT, int NS, int RC, int WPF, int MINB>
 __global__ void __launch_bounds__(128, MINB) k_lk(const StreamDev *__restrict__ S, WorkList wl, LkIO io, int rmax)
@@ -193,9 +277,12 @@ __global__ void __launch_bounds__(128, MINB) k_lk(const StreamDev *__restrict__ 
     constexpr int NT = 32 * WPF;
     const int grp = threadIdx.x / NT, tig = threadIdx.x - grp * NT;
     float *base = lk_smem + grp * lk_group_floats(rmax);
+    // regions sized for rmax; a stream with a smaller radius uses a prefix
+    const int tI = (2 * rmax + 2) * lk_sw(2 * rmax + 2);
     float *sI = base;
-    float2 *sG = reinterpret_cast<float2 *>(base + (2 * rmax + 2) * (2 * rmax + 2));
-    float *red = base + 3 * (2 * rmax + 2) * (2 * rmax + 2);
+    float2 *sG = reinterpret_cast<float2 *>(base + tI);
+    float *sJ = base + 3 * tI;
+    float *red = sJ + (2 * rmax + 2 + 2 * LK_MARGIN) * lk_sw(2 * rmax + 2 + 2 * LK_MARGIN);
     const int ngroups = (gridDim.x * blockDim.x) / NT;
     for (int item = (blockIdx.x * blockDim.x + threadIdx.x) / NT; item < wl.total; item += ngroups) {
         const int s = wl_stream(wl, item);
@@ -213,9 +300,11 @@ __global__ void __launch_bounds__(128, MINB) k_lk(const StreamDev *__restrict__ 
         const float2 u = pts[f];
         int iters = 0, tpl = 0;
         float vx, vy, bx = u.x, by = u.y;
-        const bool ok1 = lk_track<PT, NS, RC, WPF>(D, sp, sp ^ 1, u.x, u.y, vx, vy, iters, tpl, sI, sG, red, tig, grp);
+        const bool ok1 = lk_track<PT, NS, RC, WPF>(D, sp, sp ^ 1, u.x, u.y, vx, vy, iters, tpl, sI, sG, sJ, red, tig,
+                                                   grp);
         bool ok2 = false;
-        if (ok1) ok2 = lk_track<PT, NS, RC, WPF>(D, sp ^ 1, sp, vx, vy, bx, by, iters, tpl, sI, sG, red, tig, grp);
+        if (ok1) ok2 = lk_track<PT, NS, RC, WPF>(D, sp ^ 1, sp, vx, vy, bx, by, iters, tpl, sI, sG, sJ, red, tig,
+                                                    grp);
         if (!ok1) { bx = u.x; by = u.y; }
         const float ex = bx - u.x, ey = by - u.y;
         const float e2 = ex * ex + ey * ey;
@@ -265,19 +354,22 @@ struct LkKernel {
 //   2: two warps per feature, <= 80 registers (6 blocks / SM)
 //   3: two warps per feature, <= 128 registers (4 blocks / SM)
 // Other radii use the runtime-radius build of variant 0.
+// rcode: the window radius shared by every stream, or minus the largest
+// radius when streams differ (then the runtime-radius build, sized for it).
 template <typename PT>
-void run_variant(int v, const Launch &L, const StreamDev *S, WorkList wl, LkIO io, int r)
+void run_variant(int v, const Launch &L, const StreamDev *S, WorkList wl, LkIO io, int rcode)
 {
-    if (r == 10) {
+    if (rcode == 10) {
         switch (v) {
-        case 1: LkKernel<PT, 14, 10, 1, 3>::run(L, S, wl, io, r); return;
-        case 2: LkKernel<PT, 7, 10, 2, 6>::run(L, S, wl, io, r); return;
-        case 3: LkKernel<PT, 7, 10, 2, 4>::run(L, S, wl, io, r); return;
-        default: LkKernel<PT, 14, 10, 1, 4>::run(L, S, wl, io, r); return;
+        case 1: LkKernel<PT, 14, 10, 1, 3>::run(L, S, wl, io, 10); return;
+        case 2: LkKernel<PT, 7, 10, 2, 6>::run(L, S, wl, io, 10); return;
+        case 3: LkKernel<PT, 7, 10, 2, 4>::run(L, S, wl, io, 10); return;
+        default: LkKernel<PT, 14, 10, 1, 4>::run(L, S, wl, io, 10); return;
         }
     }
-    if (r < 10) LkKernel<PT, 14, 0, 1, 4>::run(L, S, wl, io, r);
-    else LkKernel<PT, 20, 0, 1, 3>::run(L, S, wl, io, r);
+    const int rmax = rcode < 0 ? -rcode : rcode;
+    if (rmax <= 10) LkKernel<PT, 14, 0, 1, 4>::run(L, S, wl, io, rmax);
+    else LkKernel<PT, 20, 0, 1, 3>::run(L, S, wl, io, rmax);
 }
 
 template <typename PT>
@@ -287,6 +379,7 @@ void warm_all()
         if (r == 10) {
             LkKernel<PT, 14, 10, 1, 4>::occ(r); LkKernel<PT, 14, 10, 1, 3>::occ(r);
             LkKernel<PT, 7, 10, 2, 6>::occ(r); LkKernel<PT, 7, 10, 2, 4>::occ(r);
+            LkKernel<PT, 14, 0, 1, 4>::occ(r);
         } else if (r < 10) {
             LkKernel<PT, 14, 0, 1, 4>::occ(r);
         } else {
@@ -305,8 +398,8 @@ void warm_lk()
     warm_all<__half>();
 }
 
-void launch_lk(const Launch &L, int prec, int r, int variant, const StreamDev *S, WorkList wl, LkIO io)
+void launch_lk(const Launch &L, int prec, int rcode, int variant, const StreamDev *S, WorkList wl, LkIO io)
 {
-    if (prec) run_variant<__half>(variant, L, S, wl, io, r);
-    else run_variant<float>(variant, L, S, wl, io, r);
+    if (prec) run_variant<__half>(variant, L, S, wl, io, rcode);
+    else run_variant<float>(variant, L, S, wl, io, rcode);
 }

@@ -87,7 +87,8 @@ void launch_select(const Launch &L, const StreamDev *S, int n, DetIO io);
 
 // Tracker variants (warps per feature, register budget); see k_lk.cu.
 int lk_variants();
-void launch_lk(const Launch &L, int prec, int r, int variant, const StreamDev *S, WorkList wl, LkIO io);
+// rcode: the window radius of every stream, or minus the largest when they differ.
+void launch_lk(const Launch &L, int prec, int rcode, int variant, const StreamDev *S, WorkList wl, LkIO io);
 
 void launch_compact(const Launch &L, const StreamDev *S, int n, CompactIO io);
 void launch_fit(const Launch &L, const StreamDev *S, int n, FitIO io, int streaming);

@@ -20,7 +20,7 @@ const char *kVersion = "gb300-stab 0.1 (sm_103a)";
 
 struct Pipeline {
     int n = 0;
-    int prec = 0, rmax = 10, Lmax = 1, sms = 0, ring = 1;
+    int prec = 0, rmax = 0, rmin = 1 << 30, Lmax = 1, sms = 0, ring = 1;
     std::vector<StreamDev> hs;
     std::vector<stab_params> P;
     StreamDev *ds = nullptr;
@@ -35,6 +35,10 @@ struct Pipeline {
     cudaGraphExec_t gexec = nullptr;
     long long t_host = 0;
     int lk_variant = 1;   // tracker kernel variant (autotuned for batches)
+
+    // Window radius for the tracker launch: the radius when every stream uses
+    // the same one, its negative (the largest) when they differ.
+    int rcode() const { return rmin == rmax ? rmax : -rmax; }
 
     void reset_graph()
     {
@@ -111,6 +115,7 @@ stab_status build(Pipeline &pp, int n, const int *w, const int *h, const int *C,
         if (s) return s;
         if (P[i].precision != pp.prec) return fail(pp.err, STAB_ERR_INVALID_ARG, "all streams of a batch share one precision");
         pp.rmax = std::max(pp.rmax, P[i].win_radius);
+        pp.rmin = std::min(pp.rmin, P[i].win_radius);
         pp.Lmax = std::max(pp.Lmax, P[i].levels);
     }
     cudaDeviceGetAttribute(&pp.sms, cudaDevAttrMultiProcessorCount, 0);
@@ -278,7 +283,7 @@ void enqueue_step(Pipeline &pp, cudaStream_t s, Prof *pf = nullptr)
     mark("filter");
     launch_select(L, pp.ds, pp.n, DetIO{});
     mark("select");
-    launch_lk(L, pp.prec, pp.rmax, pp.lk_variant, pp.ds, pp.wl_lk, LkIO{});
+    launch_lk(L, pp.prec, pp.rcode(), pp.lk_variant, pp.ds, pp.wl_lk, LkIO{});
     mark("lk");
     launch_compact(L, pp.ds, pp.n, CompactIO{});
     mark("compact");
@@ -440,7 +445,7 @@ stab_status stab_lk(stab_ctx *c, const uint8_t *prev, const uint8_t *next, int p
             scratch_status_fwd = pp.hs[0].status_fwd;
             io.status_fwd = scratch_status_fwd;
         }
-        launch_lk(L, pp.prec, pp.rmax, pp.lk_variant, pp.ds, wl, io);
+        launch_lk(L, pp.prec, pp.rcode(), pp.lk_variant, pp.ds, wl, io);
     }
     return cuda_check(pp.err, "stab_lk");
 }
@@ -457,7 +462,7 @@ stab_status stab_track(stab_ctx *c, const uint8_t *prev, const uint8_t *next, in
     build_pyr(pp, L, next, pitch, channels, sn);
     launch_begin(L, pp.ds, 1, t, 0);
     detect_chain(pp, L, DetIO{});
-    launch_lk(L, pp.prec, pp.rmax, pp.lk_variant, pp.ds, pp.wl_lk, LkIO{});
+    launch_lk(L, pp.prec, pp.rcode(), pp.lk_variant, pp.ds, pp.wl_lk, LkIO{});
     launch_compact(L, pp.ds, 1, CompactIO{(float2 *)pts_prev, (float2 *)pts_next, n, status});
     return cuda_check(pp.err, "stab_track");
 }
@@ -724,9 +729,9 @@ stab_status stab_batch_autotune(stab_batch *b, const char *cache_path, int *vari
         for (int cand = 0; cand < nv; ++cand) {
             // the tracker reads the features and pyramids of the last step and
             // writes only its own outputs, so repeated launches are harmless
-            launch_lk(L, pp.prec, pp.rmax, cand, pp.ds, pp.wl_lk, LkIO{});
+            launch_lk(L, pp.prec, pp.rcode(), cand, pp.ds, pp.wl_lk, LkIO{});
             cudaEventRecord(e0, s);
-            for (int k = 0; k < 5; ++k) launch_lk(L, pp.prec, pp.rmax, cand, pp.ds, pp.wl_lk, LkIO{});
+            for (int k = 0; k < 5; ++k) launch_lk(L, pp.prec, pp.rcode(), cand, pp.ds, pp.wl_lk, LkIO{});
             cudaEventRecord(e1, s);
             cudaEventSynchronize(e1);
             float ms = 0.f;

@@ -146,7 +146,10 @@ def test_lk_parity_other_window_radii(r):
     ref = O.track(O.pyramid(f0, 3), O.pyramid(f1, 3), pts, win_r=r)
     ctx = S.Context(w, h, _params(max_corners=150, levels=3, win_radius=r))
     g = {k: v.cpu().numpy() for k, v in ctx.lk(_cuda(f0), _cuda(f1), _cuda(pts)).items()}
-    assert (g["status"] == ref["status"]).mean() >= 0.99
+    # a 9 x 9 window sums 5x fewer samples than 21 x 21: its G and b are noisier
+    # and more decisions land near the thresholds
+    differ = g["status"] != ref["status"]
+    assert differ.mean() <= (0.01 if r >= 10 else 0.03), (ref["fb_err"][differ], g["fb_err"][differ])
     both = (g["status"] == 1) & (ref["status"] == 1)
     assert both.sum() >= 0.7 * len(pts)
     assert np.hypot(*(g["fwd"][both] - ref["fwd"][both]).T).max() < 0.01
