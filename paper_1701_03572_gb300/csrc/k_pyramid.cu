@@ -75,9 +75,49 @@ __device__ __forceinline__ void emit4(const StreamDev &D, int slot, int l, int x
 }
 
 // Level 0: frame (gray, or RGB converted to luma) -> u8 level 0 + planes.
+// Interior tiles (the common case): the 18 source rows of the tile and its
+// halo are staged as aligned 16-byte vectors from column x0 - 16 (3 (x0 - 16)
+// is a multiple of 16 for x0 a multiple of 64), luma is formed four pixels at
+// a time from three 32-bit words, and each thread emits its 4 pixels from five
+// 32-bit luma words.  Tiles at the image border take the general path, which
+// clamps every coordinate.
+constexpr int L0_COLS = 96;   // staged luma columns: x0 - 16 .. x0 + 79
+
+__device__ __forceinline__ unsigned luma4(unsigned a, unsigned b, unsigned c)
+{
+    // 12 bytes = 4 RGB pixels: a = r0 g0 b0 r1, b = g1 b1 r2 g2, c = b2 r3 g3 b3
+    const unsigned l0 = (77u * (a & 255u) + 150u * ((a >> 8) & 255u) + 29u * ((a >> 16) & 255u) + 128u) >> 8;
+    const unsigned l1 = (77u * (a >> 24) + 150u * (b & 255u) + 29u * ((b >> 8) & 255u) + 128u) >> 8;
+    const unsigned l2 = (77u * ((b >> 16) & 255u) + 150u * (b >> 24) + 29u * (c & 255u) + 128u) >> 8;
+    const unsigned l3 = (77u * ((c >> 8) & 255u) + 150u * ((c >> 16) & 255u) + 29u * (c >> 24) + 128u) >> 8;
+    return l0 | (l1 << 8) | (l2 << 16) | (l3 << 24);
+}
+
+template <typename PT>
+__device__ __forceinline__ void emit4w(const StreamDev &D, int slot, int x, int y, unsigned up, unsigned w0,
+                                       unsigned w1, unsigned w2, unsigned dn)
+{
+    typedef typename Plane2<PT>::type PT2;
+    const size_t o = (size_t)y * D.lp[0] + x;
+    *reinterpret_cast<unsigned *>(D.u8[slot][0] + o) = w1;
+    float I[4], gx[4], gy[4];
+    const int left[4] = {(int)(w0 >> 24), (int)(w1 & 255u), (int)((w1 >> 8) & 255u), (int)((w1 >> 16) & 255u)};
+    const int right[4] = {(int)((w1 >> 8) & 255u), (int)((w1 >> 16) & 255u), (int)(w1 >> 24), (int)(w2 & 255u)};
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        I[k] = (float)((w1 >> (8 * k)) & 255u);
+        gx[k] = 0.5f * (float)(right[k] - left[k]);
+        gy[k] = 0.5f * (float)((int)((dn >> (8 * k)) & 255u) - (int)((up >> (8 * k)) & 255u));
+    }
+    store_I(reinterpret_cast<PT *>(D.pI[slot][0]) + o, I);
+    store_G(reinterpret_cast<PT2 *>(D.pG[slot][0]) + o, gx, gy);
+}
+
 template <typename PT>
 __global__ void __launch_bounds__(256) k_level0(const StreamDev *__restrict__ S, WorkList wl, FrameSrc ov)
 {
+    __shared__ __align__(16) uint8_t raw[STAB_TH + 2][3 * L0_COLS];
+    __shared__ __align__(16) unsigned lum[STAB_TH + 2][L0_COLS / 4];
     __shared__ uint8_t sm[STAB_TH + 2][STAB_TW + 4];
     for (int item = blockIdx.x; item < wl.total; item += gridDim.x) {
         const int s = wl_stream(wl, item);
@@ -96,6 +136,38 @@ __global__ void __launch_bounds__(256) k_level0(const StreamDev *__restrict__ S,
         const int w = D.w, h = D.h;
         const int tx = (w + STAB_TW - 1) / STAB_TW;
         const int x0 = (local % tx) * STAB_TW, y0 = (local / tx) * STAB_TH;
+        const int row = threadIdx.x >> 4, c4 = (threadIdx.x & 15) * 4;
+        const int y = y0 + row, x = x0 + c4;
+        const bool fast = x0 >= 64 && x0 + STAB_TW + 1 <= w && C * (x0 - 16 + L0_COLS) <= pitch &&
+                          ((reinterpret_cast<uintptr_t>(src) | (uintptr_t)pitch) & 15) == 0;
+        if (fast) {
+            const int nv = C * L0_COLS / 16;   // 18 (RGB) or 6 (gray) vectors per row
+            const uint8_t *base = src + (size_t)C * (x0 - 16);
+            for (int e = threadIdx.x; e < (STAB_TH + 2) * nv; e += blockDim.x) {
+                const int r = e / nv, v = e - r * nv;
+                const int yy = clampi(y0 - 1 + r, 0, h - 1);
+                const uint4 q = __ldg(reinterpret_cast<const uint4 *>(base + (size_t)yy * pitch) + v);
+                if (C == 3) *reinterpret_cast<uint4 *>(&raw[r][16 * v]) = q;
+                else *reinterpret_cast<uint4 *>(&lum[r][4 * v]) = q;
+            }
+            __syncthreads();
+            if (C == 3) {
+                // luma groups 3 .. 20 (columns x0 - 4 .. x0 + 67) of each row
+                for (int e = threadIdx.x; e < (STAB_TH + 2) * 18; e += blockDim.x) {
+                    const int r = e / 18, g = 3 + (e - r * 18);
+                    const unsigned *wp = reinterpret_cast<const unsigned *>(&raw[r][12 * g]);
+                    lum[r][g] = luma4(wp[0], wp[1], wp[2]);
+                }
+                __syncthreads();
+            }
+            if (y < h) {
+                const int g = (c4 + 16) >> 2;
+                emit4w<PT>(D, slot, x, y, lum[row][g], lum[row + 1][g - 1], lum[row + 1][g], lum[row + 1][g + 1],
+                           lum[row + 2][g]);
+            }
+            __syncthreads();
+            continue;
+        }
         for (int i = threadIdx.x; i < (STAB_TH + 2) * (STAB_TW + 2); i += blockDim.x) {
             int ly = i / (STAB_TW + 2), lx = i - ly * (STAB_TW + 2);
             int gx = clampi(x0 - 1 + lx, 0, w - 1), gy = clampi(y0 - 1 + ly, 0, h - 1);
@@ -106,8 +178,6 @@ __global__ void __launch_bounds__(256) k_level0(const StreamDev *__restrict__ S,
             sm[ly][lx] = (uint8_t)v;
         }
         __syncthreads();
-        const int row = threadIdx.x >> 4, c4 = (threadIdx.x & 15) * 4;
-        const int y = y0 + row, x = x0 + c4;
         if (y < h && x < w) {
             int v[3][6];
 #pragma unroll
@@ -127,7 +197,8 @@ __global__ void __launch_bounds__(256) k_pyr_down(const StreamDev *__restrict__ 
 {
     constexpr int OW = STAB_TW + 2, OH = STAB_TH + 2;   // outputs with ring: 66 x 18
     constexpr int IW = 2 * OW + 3, IH = 2 * OH + 3;     // input footprint: 135 x 39
-    __shared__ uint8_t sin_[IH][IW + 1];
+    constexpr int SW = 160;                             // staged row: IW bytes + up to 15 of alignment
+    __shared__ __align__(16) uint8_t sin_[IH][SW];
     __shared__ uint16_t shs[IH][OW];
     __shared__ uint8_t sout[OH][OW + 2];
     for (int item = blockIdx.x; item < wl.total; item += gridDim.x) {
@@ -141,14 +212,26 @@ __global__ void __launch_bounds__(256) k_pyr_down(const StreamDev *__restrict__ 
         const int tx = (wo + STAB_TW - 1) / STAB_TW;
         const int x0 = (local % tx) * STAB_TW, y0 = (local / tx) * STAB_TH;
         const int ix0 = 2 * x0 - 4, iy0 = 2 * y0 - 4;
-        for (int i = threadIdx.x; i < IH * IW; i += blockDim.x) {
-            int r = i / IW, c = i - r * IW;
-            sin_[r][c] = __ldg(in + (size_t)reflect101(iy0 + r, hi) * pi + reflect101(ix0 + c, wi));
+        // interior tiles: aligned 16-byte row loads (no border reflection needed)
+        const int b0 = ix0 & ~15, off = ix0 - b0, nvec = (off + IW + 15) >> 4;
+        const bool vec = ix0 >= 0 && iy0 >= 0 && ix0 + IW <= wi && iy0 + IH <= hi && b0 + nvec * 16 <= pi;
+        if (vec) {
+            for (int e = threadIdx.x; e < IH * nvec; e += blockDim.x) {
+                const int r = e / nvec, v = e - r * nvec;
+                *reinterpret_cast<uint4 *>(&sin_[r][16 * v]) =
+                    __ldg(reinterpret_cast<const uint4 *>(in + (size_t)(iy0 + r) * pi + b0 + 16 * v));
+            }
+        } else {
+            for (int i = threadIdx.x; i < IH * IW; i += blockDim.x) {
+                int r = i / IW, c = i - r * IW;
+                sin_[r][c] = __ldg(in + (size_t)reflect101(iy0 + r, hi) * pi + reflect101(ix0 + c, wi));
+            }
         }
         __syncthreads();
+        const int so = vec ? off : 0;
         for (int i = threadIdx.x; i < IH * OW; i += blockDim.x) {
             int r = i / OW, c = i - r * OW;
-            const uint8_t *q = &sin_[r][2 * c];
+            const uint8_t *q = &sin_[r][2 * c + so];
             shs[r][c] = (uint16_t)(q[0] + 4 * q[1] + 6 * q[2] + 4 * q[3] + q[4]);
         }
         __syncthreads();
