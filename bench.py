@@ -37,6 +37,7 @@ METRIC = "1080p stabilized frames/s on 1 GB300 (batched vs plain); p99 frame lat
 W, H, CH = 1920, 1080, 3
 STREAMS = 16
 PARAMS = dict(max_corners=1000, levels=5, hypotheses=100, smooth_window=30, model=1)
+RING = 2 * (PARAMS["smooth_window"] // 2 + 2)   # >= W/2 + 2 frames, even for the retracing clip
 FP32_PEAK_NOTE = "152 SMs x 128 FP32 lanes x 2 flop x 2.07 GHz max SM clock"
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
 # LK algorithmic work per window sample: template pass = bilinear I, Ix, Iy
@@ -54,7 +55,7 @@ def config_dict(streams):
             "streams": streams, "resolution": "1920x1080", "channels": 3, "corners": 1000, "levels": 5,
             "hypotheses": 100, "smooth_window": 30,
             "l2": "inputs larger than L2: each step reads new frames from a device ring of "
-                  f"{streams} x 18 RGB 1080p frames (1.8 GB)"}
+                  f"{streams} x {RING} RGB 1080p frames ({streams * RING * W * H * CH / 1e9:.1f} GB)"}
 
 
 # ------------------------------------------------------------ distributed --
@@ -160,7 +161,7 @@ def run_ours(args):
 
     B = args.streams
     A = PARAMS["smooth_window"] // 2
-    ring = 2 * (A + 2)                      # >= A + 2 and even for the retracing clip
+    ring = RING
     clips = make_frames(min(args.clips, B), ring, dev)
     p16 = S.default_params(**PARAMS, precision=S.STAB_FP16_STORAGE)
     batch = S.Batch([(W, H, CH, p16) for _ in range(B)], ring=ring)
@@ -440,8 +441,7 @@ def run_reference(args):
     import torch
     from paper_1701_03572_gb300.synth import CONFIG_SPECS, make_clip
     import dataclasses
-    A = PARAMS["smooth_window"] // 2
-    ring = 2 * (A + 2)
+    ring = RING
     spec = dataclasses.replace(CONFIG_SPECS[2], frames=ring, pingpong=True)
     frames = make_clip(spec, 2000, device="cpu", dtype=torch.float32,
                        frames=range(min(ring, args.warmup + args.steps + 1)))["frames"].numpy()
