@@ -1,0 +1,57 @@
+"""Host logic of the multi-GPU benchmark (one process per GPU, independent
+streams per rank, max-over-ranks timing) exercised with world_size-2 gloo
+process groups on the CPU."""
+import os
+import socket
+
+import pytest
+import torch.distributed as dist
+import torch.multiprocessing as mp
+
+import bench
+
+
+def _free_port():
+    s = socket.socket()
+    s.bind(("127.0.0.1", 0))
+    port = s.getsockname()[1]
+    s.close()
+    return port
+
+
+def _worker(rank, world, port, q):
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port), RANK=str(rank), WORLD_SIZE=str(world),
+                      LOCAL_RANK=str(rank))
+    dist.init_process_group("gloo", init_method="env://", rank=rank, world_size=world)
+    try:
+        ws, r, local = bench.dist_env()
+        mine = bench.partition_streams(16, ws, r)
+        t = 10.0 + 5.0 * r                         # per-rank elapsed ms
+        bench.barrier()
+        worst = bench.max_over_ranks(t)
+        q.put((r, ws, local, mine, worst))
+    finally:
+        dist.destroy_process_group()
+
+
+def test_two_rank_partition_and_max_over_ranks():
+    world, port = 2, _free_port()
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    procs = [ctx.Process(target=_worker, args=(r, world, port, q)) for r in range(world)]
+    for p in procs:
+        p.start()
+    res = sorted(q.get(timeout=120) for _ in range(world))
+    for p in procs:
+        p.join(timeout=60)
+        assert p.exitcode == 0
+    (r0, ws0, l0, m0, w0), (r1, ws1, l1, m1, w1) = res
+    assert ws0 == ws1 == 2 and (r0, r1) == (0, 1) and (l0, l1) == (0, 1)
+    # every stream on exactly one rank, no exchange between ranks
+    assert sorted(m0 + m1) == list(range(16)) and not set(m0) & set(m1)
+    assert w0 == w1 == 15.0
+
+
+def test_single_process_helpers():
+    assert bench.partition_streams(5, 1, 0) == [0, 1, 2, 3, 4]
+    assert bench.max_over_ranks(3.5) == 3.5
