@@ -43,6 +43,22 @@ def lib():
     return _lib
 
 
+def use_library(path):
+    """Point this module at another build of the oracle source (the pin tests
+    use it to check that planted mistakes are caught); returns the previous
+    handle so the caller can restore it with restore_library()."""
+    global _lib
+    prev = _lib
+    _lib = C.CDLL(path)
+    _declare(_lib)
+    return prev
+
+
+def restore_library(handle):
+    global _lib
+    _lib = handle
+
+
 _u8p = C.POINTER(C.c_uint8)
 _f32p = C.POINTER(C.c_float)
 _f64p = C.POINTER(C.c_double)

@@ -189,6 +189,32 @@ def test_detect_vs_brute_force(seed, plateau):
     assert [tuple(map(int, p)) for p in pts] == ref
 
 
+def test_detect_tie_rule_on_symmetric_blocks():
+    """2x2 bright blocks give equal scores at adjacent pixels (symmetry): the
+    raster-order tie rule decides which one survives."""
+    img = np.full((48, 64), 30, np.uint8)
+    for k, (x, y) in enumerate([(12, 12), (30, 14), (47, 20), (20, 33), (40, 35)]):
+        img[y:y + 2, x:x + 2] = 120 + 25 * k
+    l32, _ = O.response(img, 5, 5, 59, 43)
+    eq = (l32[:, 1:] == l32[:, :-1]) & (l32[:, 1:] > 0)
+    assert eq.any()                                  # adjacent equal scores exist
+    roi = (6, 6, 58, 42)
+    pts, _, nc = O.detect(img, roi, 40, 0.01)
+    ref, nref = _detect_brute(img, roi, 40, 0.01)
+    assert nc == nref and [tuple(map(int, p)) for p in pts] == ref
+
+
+def test_detect_threshold_is_strict():
+    """Candidates need a score strictly above q * max: q = 1 admits none."""
+    img = np.clip(smooth_texture(40, 48, 4, sigma=1.5), 0, 255).astype(np.uint8)
+    roi = (5, 4, 43, 36)
+    pts, _, nc = O.detect(img, roi, 25, 1.0)
+    assert len(pts) == 0 and nc == 0
+    pts, _, nc = O.detect(img, roi, 25, 0.0)
+    ref, nref = _detect_brute(img, roi, 25, 0.0)
+    assert nc == nref and [tuple(map(int, p)) for p in pts] == ref
+
+
 def test_detect_square_corners():
     img = np.full((40, 40), 20, np.uint8)
     img[12:28, 12:28] = 220
@@ -391,12 +417,13 @@ def test_smoothing_hand_values():
 
 
 def test_smoothing_constant_velocity_and_window_one():
-    T = 40
+    T = 100
     m = np.tile([0.5, -0.25, 0.01, 0.002], (T, 1))
     m[0] = 0
     for W, shift in [(15, 0.0), (30, 0.5)]:
         Cc, S, mp = O.smooth(m, W)
         inner = slice(W, T - W)
+        assert T - 2 * W > 10
         # symmetric window: S = C; window [t-14, t+15]: S = C + v/2
         assert np.allclose(S[inner], Cc[inner] + shift * m[1], atol=1e-12)
     Cc, S, mp = O.smooth(m, 1)
@@ -468,6 +495,17 @@ def test_charbonnier_gradient_vs_finite_differences():
         e = np.zeros(4); e[a] = hstep
         fd = (O.charb(It, Ip, th + e, margin=20)["loss"] - O.charb(It, Ip, th - e, margin=20)["loss"]) / (2 * hstep)
         assert abs(fd - r["dtheta"][a]) <= 1e-2 * abs(fd) + 1e-3, (a, fd, r["dtheta"][a])
+    # dL/dI_t along a random image direction V: L(I_t + d V) is smooth in d
+    # (I_t enters linearly through the bilinear sample), so a central
+    # difference checks the whole gradient image at once
+    # (checked at eps = 0.5, where the Charbonnier curvature, up to 1/eps^2,
+    # leaves the central difference accurate; the identity holds for any eps)
+    V = np.random.default_rng(3).normal(0, 1, It.shape).astype(np.float32)
+    d, e5 = 1e-2, 0.5
+    fd = (O.charb(It + d * V, Ip, th, margin=20, eps=e5)["loss"] -
+          O.charb(It - d * V, Ip, th, margin=20, eps=e5)["loss"]) / (2 * d)
+    an = float((O.charb(It, Ip, th, margin=20, eps=e5, want_dI=True)["dIt"] * V).sum())
+    assert abs(fd - an) <= 1e-3 * abs(an) + 1e-3, (fd, an)
     # dL/dI_t at a few pixels: L is piecewise linear-plus-Charbonnier in I_t
     for (y, x) in [(50, 60), (70, 90), (33, 41)]:
         Ia, Ib = It.copy(), It.copy()
