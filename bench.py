@@ -221,6 +221,9 @@ def run_ours(args):
     # ---- end to end through host buffers
     e2e = run_e2e(S, batch, clips, offs, ring, args.e2e_steps, B) if args.e2e_steps > 0 else None
 
+    mixed = run_mixed(S, dev, args.mixed_steps, args.warmup) if args.mixed_steps > 0 else None
+    gn = run_gn(S, dev, args.gn_pairs) if args.gn_pairs > 0 else None
+
     out = {"metric": METRIC, "value": round(value, 1), "unit": "frames/s", "n_gpus": ws, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": round(total_ms / args.steps, 4), "higher_is_better": True,
            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "storage": "u8 frames, f16 I/Ix/Iy planes",
@@ -228,7 +231,8 @@ def run_ours(args):
            "latency_ms": {"p50": round(p50, 4), "p99": round(p99, 4), "per": "batch step (16 frames)"},
            "plain": plain, "e2e": e2e, "roofline": roof,
            "kernels_ms": {k: round(v, 4) for k, v in kavg.items()},
-           "gpu_launches": n_k * args.steps, "clocks": clk, "wall_s": round(wall, 3), "autotune": tuned}
+           "gpu_launches": n_k * args.steps, "clocks": clk, "wall_s": round(wall, 3), "autotune": tuned,
+           "mixed_64_streams": mixed, "photometric_gn": gn}
     if ws == 1 and rank == 0 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(clips[0].cpu().numpy(), args.cpu_frames)
     if rank == 0:
@@ -387,6 +391,107 @@ def run_e2e(S, batch, clips, offs, ring, steps, B):
             "api": "stab_batch_step_host (pinned host frames in, stabilised frames out)", "steps": steps}
 
 
+# ------------------------------------------- mixed-resolution batch (64) --
+MIXED = [(320, 240, 200, 3), (640, 480, 292, 4), (1280, 720, 538, 5), (1920, 1080, 1000, 5)]
+
+
+def run_mixed(S, dev, steps, warmup):
+    """64 gray streams, 16 each of 320x240, 640x480, 1280x720, 1920x1080, with
+    200-1000 corners in proportion to area; one graph launch per frame step."""
+    import dataclasses
+
+    import torch
+    from paper_1701_03572_gb300.synth import ClipSpec, make_clip
+    W15 = 15
+    ring = 2 * (W15 // 2 + 2)
+    clips = [make_clip(ClipSpec(w, h, ring, pingpong=True), 3000 + k, device=dev, dtype=torch.float32)["frames"]
+             for k, (w, h, _, _) in enumerate(MIXED)]
+    descs, src = [], []
+    for k, (w, h, K, L) in enumerate(MIXED):
+        p = S.default_params(max_corners=K, levels=L, hypotheses=100, smooth_window=W15,
+                             precision=S.STAB_FP16_STORAGE)
+        for i in range(16):
+            descs.append((w, h, 1, p))
+            src.append((k, (3 * i) % ring))
+    b = S.Batch(descs, ring=ring)
+    for i, (k, off) in enumerate(src):
+        for sl in range(ring):
+            b.input_slot(i, sl).copy_(clips[k][(sl + off) % ring])
+    for _ in range(W15 // 2 + 2):
+        b.step(True)
+    v, _ = b.autotune(None)
+    for _ in range(warmup):
+        b.step(True)
+    torch.cuda.synchronize()
+    stream = torch.cuda.current_stream()
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(steps + 1)]
+    ev[0].record(stream)
+    for k in range(steps):
+        b.step(True)
+        ev[k + 1].record(stream)
+    torch.cuda.synchronize()
+    assert b.sync() == 0
+    ms = sorted(ev[k].elapsed_time(ev[k + 1]) for k in range(steps))
+    tot = ev[0].elapsed_time(ev[-1])
+    area = sum(16 * w * h for w, h, _, _ in MIXED)
+    return {"streams": 64, "resolutions": "16 x each of 320x240, 640x480, 1280x720, 1920x1080 (gray)",
+            "corners": [k for _, _, k, _ in MIXED], "value": round(64 * steps / (tot / 1e3), 1), "unit": "frames/s",
+            "equiv_1080p_frames_per_s": round(steps * area / (W * H) / (tot / 1e3), 1),
+            "step_ms_p50": round(ms[len(ms) // 2], 4),
+            "step_ms_p99": round(ms[min(len(ms) - 1, int(math.ceil(0.99 * len(ms))) - 1)], 4),
+            "lk_variant": v, "steps": steps}
+
+
+# ----------------------------------------------- photometric Gauss-Newton --
+def run_gn(S, dev, pairs, steps_gn=10):
+    """Refine the tracker's estimate of `pairs` 640x480 FP32 frame pairs with
+    10 Gauss-Newton steps on the Charbonnier photometric loss."""
+    import numpy as np
+    import torch
+    from paper_1701_03572_gb300.synth import make_pair_f32
+    w, h, M, EPS = 640, 480, 48, 1e-3
+    ps = [make_pair_f32(w, h, 5000 + k, device=dev) for k in range(pairs)]
+    It = torch.stack([p["cur"] for p in ps]).contiguous()
+    Ip = torch.stack([p["prev"] for p in ps]).contiguous()
+    truth = np.stack([p["theta"] for p in ps])
+    p = S.default_params(max_corners=500, levels=4, hypotheses=256)
+    ctx = S.Context(w, h, p)
+    est = torch.zeros((pairs, 4), dtype=torch.float32, device=dev)
+    out = torch.zeros((pairs, 8), dtype=torch.float32, device=dev)
+    q8 = lambda x: torch.clamp(torch.floor(x + 0.5), 0, 255).to(torch.uint8)
+    for k in range(pairs):
+        src, dst, st, n = ctx.track(q8(Ip[k]), q8(It[k]))
+        ctx.fit(src, dst, n, S.STAB_SIMILARITY, 1, out=out[k])
+    est.copy_(out[:, :4])
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    S.charb_gauss_newton(It, Ip, est, steps_gn, M, EPS)      # warm-up
+    torch.cuda.synchronize()
+    e0.record()
+    th = S.charb_gauss_newton(It, Ip, est, steps_gn, M, EPS)
+    e1.record()
+    torch.cuda.synchronize()
+    gn_ms = e0.elapsed_time(e1)
+    e0.record()
+    loss, dth, _ = S.charb_forward(It, Ip, th, M, EPS)
+    dIt, dIp = S.charb_backward_image(It, Ip, th, M, EPS)
+    e1.record()
+    torch.cuda.synchronize()
+    fb_ms = e0.elapsed_time(e1)
+    r = math.hypot(w, h) / 2
+    err = lambda t: np.abs(t - truth)[:, :2].max(1) + r * np.abs(t - truth)[:, 2:].max(1)
+    before, after = err(est.cpu().numpy().astype(np.float64)), err(th.cpu().numpy().astype(np.float64))
+    omega = (w - 2 * M) * (h - 2 * M)
+    return {"pairs": pairs, "gn_steps": steps_gn, "gn_ms": round(gn_ms, 3),
+            "forward_backward_ms": round(fb_ms, 3),
+            "gn_step_GBps": round(pairs * omega * 8 * steps_gn / (gn_ms / 1e3) / 1e9, 1),
+            "err_px_before": {"median": round(float(np.median(before)), 4), "max": round(float(before.max()), 4)},
+            "err_px_after": {"median": round(float(np.median(after)), 5), "max": round(float(after.max()), 5)},
+            "improved_frac": round(float((after <= before).mean()), 4),
+            "err_unit": "px at the image corner (translation + radius x angle / log-scale error)"}
+
+
 # ---------------------------------------------------- oracle (CPU) timing --
 def oracle_stream(frames, n_frames, warm=0):
     """Time the oracle frame by frame on one 1080p RGB stream (the same per-
@@ -469,6 +574,8 @@ def main():
     ap.add_argument("--plain-steps", type=int, default=60)
     ap.add_argument("--e2e-steps", type=int, default=20)
     ap.add_argument("--cpu-frames", type=int, default=8)
+    ap.add_argument("--mixed-steps", type=int, default=30, help="steps of the 64-stream mixed batch (0 = skip)")
+    ap.add_argument("--gn-pairs", type=int, default=256, help="frame pairs of the photometric refinement (0 = skip)")
     ap.add_argument("--clips", type=int, default=4, help="distinct seeded clips shared round-robin by the streams")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-autotune", action="store_true")
