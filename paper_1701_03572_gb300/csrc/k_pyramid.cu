@@ -75,13 +75,14 @@ __device__ __forceinline__ void emit4(const StreamDev &D, int slot, int l, int x
 }
 
 // Level 0: frame (gray, or RGB converted to luma) -> u8 level 0 + planes.
-// Interior tiles (the common case): the 18 source rows of the tile and its
-// halo are staged as aligned 16-byte vectors from column x0 - 16 (3 (x0 - 16)
-// is a multiple of 16 for x0 a multiple of 64), luma is formed four pixels at
-// a time from three 32-bit words, and each thread emits its 4 pixels from five
-// 32-bit luma words.  Tiles at the image border take the general path, which
-// clamps every coordinate.
-constexpr int L0_COLS = 96;   // staged luma columns: x0 - 16 .. x0 + 79
+// Vertical strips, no shared memory and no barriers: a thread owns 4
+// consecutive columns x .. x+3 of a 32-row strip and walks down it with the
+// luma of rows y-1, y, y+1 (columns x-1 .. x+4) in registers; each new row
+// costs five aligned 32-bit loads of RGB (three of gray), each emitted row
+// three vector stores.  Columns and rows outside the image are clamped
+// (replicated border), so the planes match the clamped central differences.
+constexpr int L0_STRIP = 32;   // rows per strip
+constexpr int L0_GROUPS = 128; // 4-column groups per work item (one per thread)
 
 __device__ __forceinline__ unsigned luma4(unsigned a, unsigned b, unsigned c)
 {
@@ -93,20 +94,56 @@ __device__ __forceinline__ unsigned luma4(unsigned a, unsigned b, unsigned c)
     return l0 | (l1 << 8) | (l2 << 16) | (l3 << 24);
 }
 
+__device__ __forceinline__ unsigned luma1(const uint8_t *p, int C)
+{
+    return C == 1 ? (unsigned)__ldg(p) : (77u * __ldg(p) + 150u * __ldg(p + 1) + 29u * __ldg(p + 2) + 128u) >> 8;
+}
+
+// Luma of columns x-1 (byte 0 of lo), x..x+3 (mid), x+4 (byte 0 of hi) of row yy.
+__device__ __forceinline__ void luma_row(const uint8_t *__restrict__ src, int pitch, int C, int w, int x, int yy,
+                                        bool fast, unsigned &lo, unsigned &mid, unsigned &hi)
+{
+    const uint8_t *row = src + (size_t)yy * pitch;
+    if (fast) {
+        if (C == 3) {
+            const unsigned *q = reinterpret_cast<const unsigned *>(row + 3 * x);
+            const unsigned wl = __ldg(q - 1), a = __ldg(q), b = __ldg(q + 1), c = __ldg(q + 2), wr = __ldg(q + 3);
+            mid = luma4(a, b, c);
+            // x-1: bytes 1..3 of the word before; x+4: bytes 0..2 of the word after
+            lo = (77u * ((wl >> 8) & 255u) + 150u * ((wl >> 16) & 255u) + 29u * (wl >> 24) + 128u) >> 8;
+            hi = (77u * (wr & 255u) + 150u * ((wr >> 8) & 255u) + 29u * ((wr >> 16) & 255u) + 128u) >> 8;
+        } else {
+            const unsigned *q = reinterpret_cast<const unsigned *>(row + x);
+            lo = __ldg(q - 1) >> 24;
+            mid = __ldg(q);
+            hi = __ldg(q + 1) & 255u;
+        }
+        return;
+    }
+    unsigned v[6];
+#pragma unroll
+    for (int k = 0; k < 6; ++k) v[k] = luma1(row + (size_t)clampi(x - 1 + k, 0, w - 1) * C, C);
+    lo = v[0];
+    mid = v[1] | (v[2] << 8) | (v[3] << 16) | (v[4] << 24);
+    hi = v[5];
+}
+
 template <typename PT>
-__device__ __forceinline__ void emit4w(const StreamDev &D, int slot, int x, int y, unsigned up, unsigned w0,
-                                       unsigned w1, unsigned w2, unsigned dn)
+__device__ __forceinline__ void emit_row(const StreamDev &D, int slot, int x, int y, int w, unsigned up, unsigned lo,
+                                         unsigned mid, unsigned hi, unsigned dn)
 {
     typedef typename Plane2<PT>::type PT2;
     const size_t o = (size_t)y * D.lp[0] + x;
-    *reinterpret_cast<unsigned *>(D.u8[slot][0] + o) = w1;
+    *reinterpret_cast<unsigned *>(D.u8[slot][0] + o) = mid;
+    const int b[6] = {(int)lo, (int)(mid & 255u), (int)((mid >> 8) & 255u), (int)((mid >> 16) & 255u),
+                      (int)(mid >> 24), (int)hi};
     float I[4], gx[4], gy[4];
-    const int left[4] = {(int)(w0 >> 24), (int)(w1 & 255u), (int)((w1 >> 8) & 255u), (int)((w1 >> 16) & 255u)};
-    const int right[4] = {(int)((w1 >> 8) & 255u), (int)((w1 >> 16) & 255u), (int)(w1 >> 24), (int)(w2 & 255u)};
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
-        I[k] = (float)((w1 >> (8 * k)) & 255u);
-        gx[k] = 0.5f * (float)(right[k] - left[k]);
+        // columns beyond the image edge replicate the last column
+        const int r = (x + k + 1 <= w - 1) ? b[k + 2] : b[k + 1];
+        I[k] = (float)b[k + 1];
+        gx[k] = 0.5f * (float)(r - b[k]);
         gy[k] = 0.5f * (float)((int)((dn >> (8 * k)) & 255u) - (int)((up >> (8 * k)) & 255u));
     }
     store_I(reinterpret_cast<PT *>(D.pI[slot][0]) + o, I);
@@ -114,11 +151,8 @@ __device__ __forceinline__ void emit4w(const StreamDev &D, int slot, int x, int 
 }
 
 template <typename PT>
-__global__ void __launch_bounds__(256) k_level0(const StreamDev *__restrict__ S, WorkList wl, FrameSrc ov)
+__global__ void __launch_bounds__(L0_GROUPS) k_level0(const StreamDev *__restrict__ S, WorkList wl, FrameSrc ov)
 {
-    __shared__ __align__(16) uint8_t raw[STAB_TH + 2][3 * L0_COLS];
-    __shared__ __align__(16) unsigned lum[STAB_TH + 2][L0_COLS / 4];
-    __shared__ uint8_t sm[STAB_TH + 2][STAB_TW + 4];
     for (int item = blockIdx.x; item < wl.total; item += gridDim.x) {
         const int s = wl_stream(wl, item);
         const StreamDev &D = S[s];
@@ -134,59 +168,24 @@ __global__ void __launch_bounds__(256) k_level0(const StreamDev *__restrict__ S,
             pitch = D.in_pitch; C = D.C;
         }
         const int w = D.w, h = D.h;
-        const int tx = (w + STAB_TW - 1) / STAB_TW;
-        const int x0 = (local % tx) * STAB_TW, y0 = (local / tx) * STAB_TH;
-        const int row = threadIdx.x >> 4, c4 = (threadIdx.x & 15) * 4;
-        const int y = y0 + row, x = x0 + c4;
-        const bool fast = x0 >= 64 && x0 + STAB_TW + 1 <= w && C * (x0 - 16 + L0_COLS) <= pitch &&
-                          ((reinterpret_cast<uintptr_t>(src) | (uintptr_t)pitch) & 15) == 0;
-        if (fast) {
-            const int nv = C * L0_COLS / 16;   // 18 (RGB) or 6 (gray) vectors per row
-            const uint8_t *base = src + (size_t)C * (x0 - 16);
-            for (int e = threadIdx.x; e < (STAB_TH + 2) * nv; e += blockDim.x) {
-                const int r = e / nv, v = e - r * nv;
-                const int yy = clampi(y0 - 1 + r, 0, h - 1);
-                const uint4 q = __ldg(reinterpret_cast<const uint4 *>(base + (size_t)yy * pitch) + v);
-                if (C == 3) *reinterpret_cast<uint4 *>(&raw[r][16 * v]) = q;
-                else *reinterpret_cast<uint4 *>(&lum[r][4 * v]) = q;
-            }
-            __syncthreads();
-            if (C == 3) {
-                // luma groups 3 .. 20 (columns x0 - 4 .. x0 + 67) of each row
-                for (int e = threadIdx.x; e < (STAB_TH + 2) * 18; e += blockDim.x) {
-                    const int r = e / 18, g = 3 + (e - r * 18);
-                    const unsigned *wp = reinterpret_cast<const unsigned *>(&raw[r][12 * g]);
-                    lum[r][g] = luma4(wp[0], wp[1], wp[2]);
-                }
-                __syncthreads();
-            }
-            if (y < h) {
-                const int g = (c4 + 16) >> 2;
-                emit4w<PT>(D, slot, x, y, lum[row][g], lum[row + 1][g - 1], lum[row + 1][g], lum[row + 1][g + 1],
-                           lum[row + 2][g]);
-            }
-            __syncthreads();
-            continue;
+        const int ngx = (w + 4 * L0_GROUPS - 1) / (4 * L0_GROUPS);
+        const int x = ((local % ngx) * L0_GROUPS + threadIdx.x) * 4, y0 = (local / ngx) * L0_STRIP;
+        if (x >= w) continue;
+        // word loads need x-1 .. x+4 inside the row and 4-byte aligned rows
+        const bool fast = x >= 4 && x + 8 <= w && ((reinterpret_cast<uintptr_t>(src) | (uintptr_t)pitch) & 3) == 0;
+        const int y1 = min(y0 + L0_STRIP, h);
+        unsigned plo, pmid, phi, clo, cmid, chi;
+        unsigned dummy0, dummy1;
+        luma_row(src, pitch, C, w, x, max(y0 - 1, 0), fast, dummy0, pmid, dummy1);
+        luma_row(src, pitch, C, w, x, y0, fast, clo, cmid, chi);
+        (void)plo; (void)phi;
+        for (int y = y0; y < y1; ++y) {
+            unsigned nlo, nmid, nhi;
+            luma_row(src, pitch, C, w, x, min(y + 1, h - 1), fast, nlo, nmid, nhi);
+            emit_row<PT>(D, slot, x, y, w, pmid, clo, cmid, chi, nmid);
+            pmid = cmid;
+            clo = nlo; cmid = nmid; chi = nhi;
         }
-        for (int i = threadIdx.x; i < (STAB_TH + 2) * (STAB_TW + 2); i += blockDim.x) {
-            int ly = i / (STAB_TW + 2), lx = i - ly * (STAB_TW + 2);
-            int gx = clampi(x0 - 1 + lx, 0, w - 1), gy = clampi(y0 - 1 + ly, 0, h - 1);
-            const uint8_t *p = src + (size_t)gy * pitch + (size_t)gx * C;
-            int v;
-            if (C == 1) v = __ldg(p);
-            else v = (77 * __ldg(p) + 150 * __ldg(p + 1) + 29 * __ldg(p + 2) + 128) >> 8;
-            sm[ly][lx] = (uint8_t)v;
-        }
-        __syncthreads();
-        if (y < h && x < w) {
-            int v[3][6];
-#pragma unroll
-            for (int r = 0; r < 3; ++r)
-#pragma unroll
-                for (int c = 0; c < 6; ++c) v[r][c] = sm[row + r][c4 + c];
-            emit4<PT>(D, slot, 0, x, y, v);
-        }
-        __syncthreads();
     }
 }
 
@@ -279,8 +278,8 @@ __global__ void k_plane_f32(const StreamDev *__restrict__ S, int slot, int l, fl
 void launch_level0(const Launch &L, int prec, const StreamDev *S, WorkList wl, FrameSrc ov)
 {
     int g = grid_for(L, wl.total, prec ? occ_level0_h() : occ_level0_f());
-    if (prec) k_level0<__half><<<g, 256, 0, L.stream>>>(S, wl, ov);
-    else k_level0<float><<<g, 256, 0, L.stream>>>(S, wl, ov);
+    if (prec) k_level0<__half><<<g, L0_GROUPS, 0, L.stream>>>(S, wl, ov);
+    else k_level0<float><<<g, L0_GROUPS, 0, L.stream>>>(S, wl, ov);
 }
 
 void launch_pyr_down(const Launch &L, int prec, const StreamDev *S, WorkList wl, int l, int slot_ov)
@@ -307,7 +306,17 @@ void launch_plane_f32(const Launch &L, int prec, const StreamDev *S, int slot, i
         }                                                                         \
         return v;                                                                 \
     }
-OCC_FN(occ_level0_f, k_level0<float>)
-OCC_FN(occ_level0_h, k_level0<__half>)
+#define OCC_FN128(name, kern)                                                                  \
+    int name()                                                                                 \
+    {                                                                                          \
+        static int v = 0;                                                                      \
+        if (!v) {                                                                              \
+            if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, kern, L0_GROUPS, 0) != cudaSuccess || v < 1) \
+                v = 1;                                                                         \
+        }                                                                                      \
+        return v;                                                                              \
+    }
+OCC_FN128(occ_level0_f, k_level0<float>)
+OCC_FN128(occ_level0_h, k_level0<__half>)
 OCC_FN(occ_pyr_f, k_pyr_down<float>)
 OCC_FN(occ_pyr_h, k_pyr_down<__half>)

@@ -213,7 +213,8 @@ stab_status build(Pipeline &pp, int n, const int *w, const int *h, const int *C,
         wl->total = pre[n];
         lists.push_back({wl, pre});
     };
-    mk(&pp.wl_l0, [](const StreamDev &D) { return tiles(D.w, D.h); });
+    // level 0: strips of 512 columns x 32 rows (one thread per 4 columns)
+    mk(&pp.wl_l0, [](const StreamDev &D) { return ((D.w + 511) / 512) * ((D.h + 31) / 32); });
     for (int l = 1; l < STAB_MAXL; ++l)
         mk(&pp.wl_pyr[l], [l](const StreamDev &D) { return l < D.L ? tiles(D.lw[l], D.lh[l]) : 0; });
     mk(&pp.wl_resp, [](const StreamDev &D) { return tiles(D.roi_x1 - D.roi_x0, D.roi_y1 - D.roi_y0); });
