@@ -90,7 +90,7 @@ def _declare(L):
     L.or_fit.restype = C.c_int
     L.or_ls_similarity.argtypes = [_f64p, _f64p, C.c_int, C.c_int, _f64p]
     L.or_smooth.argtypes = [_f64p, C.c_int, C.c_int, _f64p, _f64p, _f64p]
-    L.or_warp_inverse.argtypes = [_f64p, C.c_int, C.c_int, _f32p]
+    L.or_warp_inverse.argtypes = [_f64p, C.c_int, C.c_int, C.c_double, _f32p]
     L.or_warp.argtypes = [_u8p, C.c_int, C.c_int, C.c_int, C.c_int, _f32p, _u8p, C.c_int]
     L.or_charb.argtypes = [_f32p, _f32p, C.c_int, C.c_int, C.c_int, _f64p, C.c_double, _f64p, _f64p, _f64p,
                            _f64p, _f64p]
@@ -242,10 +242,11 @@ def smooth(m, W: int):
     return Cc, S, mp
 
 
-def warp_inverse(m, w, h) -> np.ndarray:
+def warp_inverse(m, w, h, zoom: float = 1.0) -> np.ndarray:
+    """Inverse warp of motion m composed with the composition crop's zoom."""
     m = _c(m, np.float64)
     out = np.zeros(6, np.float32)
-    lib().or_warp_inverse(_p(m, _f64p), w, h, _p(out, _f32p))
+    lib().or_warp_inverse(_p(m, _f64p), w, h, float(zoom), _p(out, _f32p))
     return out
 
 
@@ -303,6 +304,53 @@ class Params:
     min_fit: int = 10
     smooth_window: int = 15
     rigid: bool = False
+    hybrid: bool = False         # Sec. 4.1 hybrid mechanism (overrides `rigid`)
+    dwell: int = 20              # Sec. 4.1: transitions between hybrid decisions
+    crop_zoom: float = 1.0       # Sec. 5.1 composition crop (1 = none)
+
+
+def hybrid_choice(e_rigid: float, ok_rigid: bool, e_sim: float, ok_sim: bool, cur_rigid: bool) -> bool:
+    """Decision of the hybrid mechanism (Sec. 4.1, Fig. 3): rigid when its RMS
+    distance is lower than the similarity's, else similarity.  Each RMS is
+    taken over the model's own inliers (the refit of its robust fit).  A model
+    whose fit failed cannot be chosen; when both failed the current choice
+    stays.  Returns True for rigid."""
+    if ok_rigid and ok_sim:
+        return e_rigid < e_sim
+    if ok_rigid:
+        return True
+    if ok_sim:
+        return False
+    return cur_rigid
+
+
+def fit_transition(src, dst, w, h, t: int, p: Params, cur_rigid: bool) -> dict:
+    """Motion fit of transition t (frame t-1 -> t) under the model setting of
+    p.  With the hybrid mechanism (Sec. 4.1) transition t is a decision when
+    (t - 1) % dwell == 0: both models are fitted, each RMS taken over its own
+    inliers, hybrid_choice picks one and the motion is that model's fit; on
+    the other transitions the current choice alone is fitted.  Returns the fit,
+    the model used (rigid or not), whether t was a decision, and the RMS of
+    each model fitted here (-1 where none)."""
+    args = (p.hypotheses, p.seed, t, p.inlier_thresh, p.min_fit)
+    e = {True: -1.0, False: -1.0}
+    if p.hybrid and (t - 1) % p.dwell == 0:
+        fr = fit(src, dst, w, h, True, *args)
+        fs = fit(src, dst, w, h, False, *args)
+        if fr["flags"] == 0:
+            e[True] = fr["rms"]
+        if fs["flags"] == 0:
+            e[False] = fs["rms"]
+        rigid = hybrid_choice(fr["rms"], fr["flags"] == 0, fs["rms"], fs["flags"] == 0, cur_rigid)
+        f = fr if rigid else fs
+        decision = True
+    else:
+        rigid = cur_rigid if p.hybrid else p.rigid
+        f = fit(src, dst, w, h, rigid, *args)
+        if f["flags"] == 0:
+            e[rigid] = f["rms"]
+        decision = False
+    return dict(f=f, rigid=rigid, decision=decision, e_rigid=e[True], e_sim=e[False])
 
 
 def run_clip(frames: np.ndarray, p: Params) -> dict:
@@ -316,6 +364,9 @@ def run_clip(frames: np.ndarray, p: Params) -> dict:
     roi = roi_of(w, h, p.win_r)
     incs = np.zeros((T, 4)); flags = np.zeros(T, np.int32)
     n_tracked = np.zeros(T, np.int32); n_inl = np.zeros(T, np.int32); detected = np.zeros(T, bool)
+    rigid_used = np.zeros(T, bool); decision = np.zeros(T, bool)
+    e_rigid = np.full(T, -1.0); e_sim = np.full(T, -1.0)
+    cur_rigid = p.rigid and not p.hybrid     # hybrid: similarity until the first decision
     feats = None
     for t in range(1, T):
         if feats is None or (t - 1) % p.redetect_period == 0 or len(feats) < p.min_tracks:
@@ -326,14 +377,19 @@ def run_clip(frames: np.ndarray, p: Params) -> dict:
         src = feats[keep]
         dst = tr["fwd"][keep].astype(np.float32)
         n_tracked[t] = int(keep.sum())
-        f = fit(src, dst, w, h, p.rigid, p.hypotheses, p.seed, t, p.inlier_thresh, p.min_fit)
+        tr_fit = fit_transition(src, dst, w, h, t, p, cur_rigid)
+        f = tr_fit["f"]
+        cur_rigid = tr_fit["rigid"]
+        decision[t] = tr_fit["decision"]; e_rigid[t] = tr_fit["e_rigid"]; e_sim[t] = tr_fit["e_sim"]
+        rigid_used[t] = cur_rigid
         incs[t] = f["m"]; flags[t] = f["flags"]; n_inl[t] = f["inliers"]
         feats = dst
     Cc, S, mp = smooth(incs, p.smooth_window)
     Minv = np.zeros((T, 6), np.float32)
     out = np.zeros_like(frames)
     for t in range(1, T):
-        Minv[t] = warp_inverse(mp[t], w, h)
+        Minv[t] = warp_inverse(mp[t], w, h, p.crop_zoom)
         out[t - 1] = warp(frames[t - 1], Minv[t])
     return dict(incs=incs, flags=flags, n_tracked=n_tracked, n_inliers=n_inl, detected=detected, C=Cc, S=S,
-                mp=mp, Minv=Minv, out=out)
+                mp=mp, Minv=Minv, out=out, rigid_used=rigid_used, decision=decision, e_rigid=e_rigid,
+                e_sim=e_sim)

@@ -532,15 +532,31 @@ void or_smooth(const double *m, int T, int W, double *C, double *S, double *mp)
 /* Inverse mapping of the compensating warp for parameters m (Sec. 5.1: the
  * frame is warped by the corrected similarity; the output pixel p takes the
  * source at M(m)^-1 p).  In pixel coordinates with c the image centre:
- * q = c + (1/s) R(-theta) (p - c - t).  Minv = [a00 a01 b0 a10 a11 b1] (FP32). */
-void or_warp_inverse(const double m[4], int w, int h, float Minv[6])
+ * q = c + (1/s) R(-theta) (p - c - t).
+ *
+ * Composition crop (Sec. 5.1, last paragraph: the warped frame is cropped and
+ * resized to hide the unfilled border; the paper fixes no amount): a zoom z
+ * about the centre, so output pixel p shows the compensated frame at
+ * c + (p - c) / z.  The two maps are composed here as 3x3 matrices in FP64,
+ * Minv = W Z^-1 with W the warp inverse above and Z^-1 the zoom's inverse;
+ * z = 1 leaves W unchanged.  Minv = [a00 a01 b0 a10 a11 b1] (FP32). */
+void or_warp_inverse(const double m[4], int w, int h, double zoom, float Minv[6])
 {
     double cx = 0.5 * (w - 1), cy = 0.5 * (h - 1);
     double is = exp(-m[3]), c = cos(m[2]), sn = sin(m[2]);
     double a00 = is * c, a01 = is * sn, a10 = -is * sn, a11 = is * c;
     double ux = cx + m[0], uy = cy + m[1];
-    Minv[0] = (float)a00; Minv[1] = (float)a01; Minv[2] = (float)(cx - (a00 * ux + a01 * uy));
-    Minv[3] = (float)a10; Minv[4] = (float)a11; Minv[5] = (float)(cy - (a10 * ux + a11 * uy));
+    double W[3][3] = {{a00, a01, cx - (a00 * ux + a01 * uy)}, {a10, a11, cy - (a10 * ux + a11 * uy)}, {0, 0, 1}};
+    double iz = 1.0 / zoom;
+    double Zi[3][3] = {{iz, 0, cx - iz * cx}, {0, iz, cy - iz * cy}, {0, 0, 1}};
+    double P[3][3];
+    for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j) {
+            P[i][j] = 0.0;
+            for (int k = 0; k < 3; ++k) P[i][j] += W[i][k] * Zi[k][j];
+        }
+    Minv[0] = (float)P[0][0]; Minv[1] = (float)P[0][1]; Minv[2] = (float)P[0][2];
+    Minv[3] = (float)P[1][0]; Minv[4] = (float)P[1][1]; Minv[5] = (float)P[1][2];
 }
 
 /* Compensating bilinear warp (Sec. 5.1, final step).  out(p) = bilinear(src,

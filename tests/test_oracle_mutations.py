@@ -1,12 +1,15 @@
 """The oracle's pins catch plausible mistakes.
 
 Each case plants one mistake (a dropped term, a wrong sign or index, a
-transposed operand, an off-by-one border) in a copy of the oracle's C source,
-builds it, and runs the pins against it: at least one pin must fail.  The
-oracle itself is never modified."""
+transposed operand, an off-by-one border) in a copy of the oracle's C source
+(built into a separate library) or of its Python orchestration (loaded as a
+separate module), and runs the pins against it: at least one pin must fail.
+The oracle itself is never modified."""
 import os
 import subprocess
+import sys
 import tempfile
+import types
 
 import pytest
 
@@ -41,7 +44,21 @@ MUTATIONS = [
     ("warp rounding", "float r = floorf(v + 0.5f);", "float r = floorf(v);"),
     ("inverse warp rotation sign", "double a00 = is * c, a01 = is * sn, a10 = -is * sn, a11 = is * c;", "double a00 = is * c, a01 = -is * sn, a10 = is * sn, a11 = is * c;"),
     ("adjoint rotation term sign", "s * (-ry * gxv + rx * gyv)", "s * (ry * gxv + rx * gyv)"),
+    ("crop zoom inverted", "double iz = 1.0 / zoom;", "double iz = zoom;"),
+    ("crop composed before the compensation", "P[i][j] += W[i][k] * Zi[k][j];", "P[i][j] += Zi[i][k] * W[k][j];"),
+    ("crop zoom about the origin", "double Zi[3][3] = {{iz, 0, cx - iz * cx}, {0, iz, cy - iz * cy}, {0, 0, 1}};",
+     "double Zi[3][3] = {{iz, 0, 0}, {0, iz, 0}, {0, 0, 1}};"),
     ("adjoint image weight", "double wt[4] = {(1 - ax) * (1 - ay), ax * (1 - ay), (1 - ax) * ay, ax * ay};", "double wt[4] = {(1 - ax) * (1 - ay), (1 - ax) * ay, ax * (1 - ay), ax * ay};"),
+]
+
+# Mistakes planted in the oracle's Python orchestration (oracle.py).
+PY_MUTATIONS = [
+    ("hybrid tie goes to rigid", "return e_rigid < e_sim", "return e_rigid <= e_sim"),
+    ("hybrid comparison reversed", "return e_rigid < e_sim", "return e_rigid > e_sim"),
+    ("hybrid may choose a failed fit", "    if ok_rigid:\n        return True", "    if ok_sim:\n        return True"),
+    ("hybrid schedule off by one", "if p.hybrid and (t - 1) % p.dwell == 0:", "if p.hybrid and t % p.dwell == 0:"),
+    ("hybrid motion from the other model", "f = fr if rigid else fs", "f = fs if rigid else fr"),
+    ("hybrid choice not held", "rigid = cur_rigid if p.hybrid else p.rigid", "rigid = False if p.hybrid else p.rigid"),
 ]
 
 PINS = [
@@ -64,6 +81,11 @@ PINS = [
     (P.test_warp_identity_and_integer_shift, {}), (P.test_warp_inverse_of_rotation_is_rot90, {}),
     (P.test_warp_vs_scipy_bilinear, {}), (P.test_warp_inverse_maps_points_back, {}),
     (P.test_charbonnier_gradient_vs_finite_differences, {}),
+    (P.test_hybrid_choice_rule, {}), (P.test_hybrid_prefers_similarity_under_a_scale_change, {}),
+    (P.test_hybrid_prefers_rigid_when_similarity_buys_inliers_with_error, {}),
+    (P.test_crop_zoom_is_a_zoom_about_the_centre, {}), (P.test_crop_zoom_composes_after_the_compensation, {}),
+    (P.test_crop_zoom_of_linear_ramp, {}), (P.test_crop_zoom_hides_the_unfilled_border, {}),
+    (P.test_hybrid_transitions_on_scripted_pairs, {}), (P.test_hybrid_dwell_schedule_and_bookkeeping, {}),
 ]
 
 
@@ -93,4 +115,30 @@ def test_planted_mistake_is_caught(name, orig, bad, tmpdir_mod):
                 break
     finally:
         O.restore_library(prev)
+    assert caught is not None, f"no pin caught the planted mistake '{name}'"
+
+
+def _first_failing_pin():
+    for fn, kw in PINS:
+        try:
+            fn(**kw)
+        except Exception as e:               # a pin failed (assertion or error): mistake caught
+            return f"{fn.__name__}: {type(e).__name__}"
+    return None
+
+
+@pytest.mark.parametrize("name,orig,bad", PY_MUTATIONS, ids=[m[0] for m in PY_MUTATIONS])
+def test_planted_python_mistake_is_caught(name, orig, bad):
+    src = open(O.__file__).read()
+    assert src.count(orig) >= 1, f"mutation site not found: {orig}"
+    mod = types.ModuleType("oracle_mutant")
+    mod.__file__ = O.__file__
+    sys.modules["oracle_mutant"] = mod
+    try:
+        exec(compile(src.replace(orig, bad), O.__file__, "exec"), mod.__dict__)
+        P.O = mod
+        caught = _first_failing_pin()
+    finally:
+        P.O = O
+        del sys.modules["oracle_mutant"]
     assert caught is not None, f"no pin caught the planted mistake '{name}'"

@@ -548,3 +548,176 @@ def test_pipeline_recovers_generator_motion():
     assert (r["flags"][1:] == 0).all()
     assert np.abs(r["incs"][1:, 2:] - gt[1:, 2:]).max() < 1e-3
     assert np.abs(r["incs"][1:, :2] - gt[1:, :2]).max() < 0.1
+
+
+# ------------------------------------------- hybrid mechanism (Sec. 4.1) --
+def _hybrid_pairs(radial: float, scale: float, seed: int = 7):
+    """Point pairs in a 320 x 240 frame (pixel coordinates, FP32): 40 within
+    5 px of the centre and 20 on a circle of radius 110 about it, all scaled
+    about the centre by `scale`, the circle then pushed `radial` px outward,
+    and all moved by the same rigid motion (theta = 0.01, t = (2, -1))."""
+    w, h = 320, 240
+    c = np.array([(w - 1) / 2, (h - 1) / 2])
+    rng = np.random.default_rng(seed)
+    th = 0.01
+    R = np.array([[math.cos(th), -math.sin(th)], [math.sin(th), math.cos(th)]])
+    t = np.array([2.0, -1.0])
+    near = rng.uniform(-5, 5, (40, 2))
+    ang = np.linspace(0, 2 * math.pi, 20, endpoint=False)
+    u = np.stack([np.cos(ang), np.sin(ang)], 1)
+    far = 110 * u
+    src = np.concatenate([near, far])
+    tgt = np.concatenate([near * scale, far * scale + radial * u])
+    dst = tgt @ R.T + t
+    return (src + c).astype(np.float32), (dst + c).astype(np.float32), w, h
+
+
+def test_hybrid_choice_rule():
+    # rigid iff both fits exist and rigid's RMS is strictly lower; a failed
+    # fit cannot be chosen; no fit keeps the current choice
+    cases = [((0.1, True, 0.2, True, False), True), ((0.2, True, 0.1, True, True), False),
+             ((0.1, True, 0.1, True, True), False), ((0.1, False, 0.2, True, True), False),
+             ((0.3, True, 0.2, False, False), True), ((0.1, False, 0.2, False, True), True),
+             ((0.1, False, 0.2, False, False), False)]
+    for args, want in cases:
+        assert O.hybrid_choice(*args) is want, args
+
+
+def test_hybrid_prefers_similarity_under_a_scale_change():
+    # scale 1.02 about the centre: the far pairs move 2.2 px more than any
+    # rotation + translation explains (rigid outliers), the near ones < 0.1 px
+    src, dst, w, h = _hybrid_pairs(0.0, 1.02)
+    fr = O.fit(src, dst, w, h, True, 100, 0, 1)
+    fs = O.fit(src, dst, w, h, False, 100, 0, 1)
+    assert fr["inliers"] == 40 and fr["mask"][:40].all()
+    assert fs["inliers"] == 60 and fs["rms"] < 1e-4           # exact similarity (FP32 inputs)
+    assert abs(fs["m"][3] - math.log(1.02)) < 1e-5
+    assert fr["rms"] > 0.02                                    # rigid cannot absorb 0.02 x (r <= 7 px)
+    assert O.hybrid_choice(fr["rms"], True, fs["rms"], True, True) is False
+
+
+def test_hybrid_prefers_rigid_when_similarity_buys_inliers_with_error():
+    # 3 px radial push on the circle: rigid keeps the 40 exact near pairs
+    # (no translation brings the circle within 1 px without losing the near
+    # pairs); the similarity through two circle points scales by 1 + 3/110 and
+    # keeps all 60, so its least squares leaves the near pairs a residual of
+    # about 0.027 r (E[r^2] = 50/3 over the 10 x 10 square): E_s ~ 0.09 px
+    src, dst, w, h = _hybrid_pairs(3.0, 1.0)
+    fr = O.fit(src, dst, w, h, True, 100, 0, 1)
+    fs = O.fit(src, dst, w, h, False, 100, 0, 1)
+    assert fr["inliers"] == 40 and fr["mask"][:40].all() and fr["rms"] < 1e-4
+    assert fs["inliers"] == 60
+    assert 0.05 < fs["rms"] < 0.15
+    assert abs(fs["m"][3] - math.log(1 + 3 / 110)) < 1e-3
+    assert O.hybrid_choice(fr["rms"], True, fs["rms"], True, False) is True
+
+
+def test_hybrid_transitions_on_scripted_pairs():
+    # dwell 4: transitions 1 and 5 decide, 2-4 and 6 hold.  Each transition
+    # gets pairs that favour the model NOT currently held, so a decision
+    # switches and a held transition must still fit the held model.
+    rig = _hybrid_pairs(3.0, 1.0)       # rigid wins a decision (40 inliers, log-scale 0)
+    sim = _hybrid_pairs(0.0, 1.02)      # similarity wins a decision (60 inliers, log-scale log 1.02)
+    p = O.Params(hybrid=True, dwell=4, hypotheses=100, seed=0)
+    script = [(1, rig, True, True), (2, sim, False, True), (4, sim, False, True),
+              (5, sim, True, False), (6, rig, False, False)]
+    cur = False
+    for t, (src, dst, w, h), decides, want_rigid in script:
+        r = O.fit_transition(src, dst, w, h, t, p, cur)
+        assert r["decision"] is decides and r["rigid"] is want_rigid, t
+        f = r["f"]
+        if want_rigid:
+            assert f["m"][3] == 0.0 and f["inliers"] == 40
+        else:
+            assert f["m"][3] != 0.0
+        if decides:
+            assert r["e_rigid"] >= 0 and r["e_sim"] >= 0
+        else:
+            assert (r["e_rigid"] >= 0) == want_rigid and (r["e_sim"] >= 0) == (not want_rigid)
+        cur = r["rigid"]
+
+
+def test_hybrid_dwell_schedule_and_bookkeeping():
+    # decisions at the first transition and every `dwell` after it; the
+    # choice holds in between; each motion is the chosen model's fit
+    import dataclasses
+    from paper_1701_03572_gb300.synth import make_clip, CONFIG_SPECS
+    spec = dataclasses.replace(CONFIG_SPECS[0], frames=11)
+    clip = make_clip(spec, 9)
+    frames = clip["frames"].numpy()
+    dwell = 4
+    r = O.run_clip(frames, O.Params(hybrid=True, dwell=dwell))
+    T = frames.shape[0]
+    assert list(np.nonzero(r["decision"])[0]) == [1, 5, 9]
+    prev = False
+    for t in range(1, T):
+        if r["decision"][t]:
+            er, es = r["e_rigid"][t], r["e_sim"][t]
+            assert er >= 0 and es >= 0
+            assert r["rigid_used"][t] == (er < es)
+        else:
+            assert r["rigid_used"][t] == prev
+            used = r["e_rigid"][t] if prev else r["e_sim"][t]
+            other = r["e_sim"][t] if prev else r["e_rigid"][t]
+            assert used >= 0 and other == -1.0
+        prev = r["rigid_used"][t]
+    # a rigid motion has zero log-scale; every motion matches the generator
+    assert all((r["incs"][t, 3] == 0.0) == bool(r["rigid_used"][t]) for t in range(1, T))
+    gt = clip["incs"]
+    assert np.abs(r["incs"][1:, 2] - gt[1:, 2]).max() < 1e-3
+    assert np.abs(r["incs"][1:, :2] - gt[1:, :2]).max() < 0.1
+
+
+# ------------------------------------------ composition crop (Sec. 5.1) --
+def test_crop_zoom_is_a_zoom_about_the_centre():
+    w, h, z = 64, 48, 1.25
+    cx, cy = (w - 1) / 2, (h - 1) / 2
+    M = O.warp_inverse([0, 0, 0, 0], w, h, z).astype(np.float64)
+    want = [1 / z, 0, cx - cx / z, 0, 1 / z, cy - cy / z]
+    assert np.abs(M - want).max() < 1e-6
+
+
+def test_crop_zoom_composes_after_the_compensation():
+    # output pixel p shows the compensated frame at c + (p - c) / z
+    w, h = 320, 240
+    c = np.array([(w - 1) / 2, (h - 1) / 2])
+    rng = np.random.default_rng(71)
+    for _ in range(5):
+        m = rng.normal(0, [3, 3, 0.02, 0.02])
+        z = rng.uniform(1.05, 1.5)
+        A1 = O.warp_inverse(m, w, h).astype(np.float64).reshape(2, 3)
+        Az = O.warp_inverse(m, w, h, z).astype(np.float64).reshape(2, 3)
+        p = rng.uniform(0, [w, h], (20, 2))
+        pz = c + (p - c) / z
+        q1 = pz @ A1[:, :2].T + A1[:, 2]
+        qz = p @ Az[:, :2].T + Az[:, 2]
+        assert np.abs(q1 - qz).max() < 1e-3
+
+
+def test_crop_zoom_of_linear_ramp():
+    # bilinear sampling reproduces a linear image exactly: a 2x zoom of
+    # f(x, y) = 2 x + y shows f(c + (p - c) / 2), rounded half up
+    w, h = 64, 48
+    Y, X = np.mgrid[0:h, 0:w].astype(np.float64)
+    img = (2 * X + Y).astype(np.uint8)
+    out = O.warp(img, O.warp_inverse([0, 0, 0, 0], w, h, 2.0)).astype(np.int64)
+    cx, cy = (w - 1) / 2, (h - 1) / 2
+    ref = np.floor(2 * (cx + (X - cx) / 2) + (cy + (Y - cy) / 2) + 0.5).astype(np.int64)
+    d = np.abs(out - ref)
+    assert d.max() <= 1 and (d > 0).mean() < 0.01    # +-1 only where FP32 q rounds across .5
+
+
+def test_crop_zoom_hides_the_unfilled_border():
+    # a constant frame warped by a correction leaves zero-filled pixels at
+    # the border; a zoom large enough that the inverse image of the output
+    # rectangle lies inside the frame leaves none
+    w, h = 320, 240
+    img = np.full((h, w), 200, np.uint8)
+    m = [4.0, -3.0, 0.01, 0.01]
+    assert (O.warp(img, O.warp_inverse(m, w, h)) == 0).any()
+    z = 1.1
+    M = O.warp_inverse(m, w, h, z).astype(np.float64).reshape(2, 3)
+    corners = np.array([[0, 0], [w - 1, 0], [0, h - 1], [w - 1, h - 1]], np.float64)
+    q = corners @ M[:, :2].T + M[:, 2]
+    assert (q >= 0).all() and (q[:, 0] <= w - 1).all() and (q[:, 1] <= h - 1).all()
+    assert (O.warp(img, M.reshape(-1).astype(np.float32)) == 200).all()
