@@ -22,6 +22,7 @@
 #define STAB_SEL_SMEM 12288  // selection keys held in shared memory
 #define STAB_TW 64           // image tile: 64 x 16 pixels, 256 threads x 4 pixels
 #define STAB_TH 16
+#define STAB_WTH 32          // warp output tile: 64 x 32 pixels, 256 threads x 2 rows x 4 pixels
 
 // Per-stream mutable state (device memory).
 struct StreamState {

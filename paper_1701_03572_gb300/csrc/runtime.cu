@@ -220,7 +220,7 @@ stab_status build(Pipeline &pp, int n, const int *w, const int *h, const int *C,
     mk(&pp.wl_resp, [](const StreamDev &D) { return tiles(D.roi_x1 - D.roi_x0, D.roi_y1 - D.roi_y0); });
     mk(&pp.wl_filter, [](const StreamDev &D) { return (D.cand_cap + 2047) / 2048; });
     mk(&pp.wl_lk, [](const StreamDev &D) { return D.K; });
-    mk(&pp.wl_warp, [](const StreamDev &D) { return tiles(D.w, D.h); });
+    mk(&pp.wl_warp, [](const StreamDev &D) { return ((D.w + STAB_TW - 1) / STAB_TW) * ((D.h + STAB_WTH - 1) / STAB_WTH); });
     for (auto &e : lists) all.insert(all.end(), e.second.begin(), e.second.end());
     if (cudaMalloc(&pp.prefix, all.size() * sizeof(int)) != cudaSuccess) return fail(pp.err, STAB_ERR_OOM, "cudaMalloc");
     cudaMemcpy(pp.prefix, all.data(), all.size() * sizeof(int), cudaMemcpyHostToDevice);
