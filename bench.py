@@ -319,7 +319,7 @@ def run_plain(S, clip, ring, steps, dev):
     dst = torch.zeros((K, 2), device=dev)
     status = torch.zeros(K, dtype=torch.uint8, device=dev)
     n = torch.zeros(1, dtype=torch.int32, device=dev)
-    mot = torch.zeros(8, device=dev)
+    mot = torch.zeros(S.MOTION_WORDS, device=dev)
     Minv = torch.zeros(6, device=dev)
     ready = torch.zeros(1, dtype=torch.int32, device=dev)
     out = torch.zeros((H, W, CH), dtype=torch.uint8, device=dev)
@@ -457,7 +457,7 @@ def run_gn(S, dev, pairs, steps_gn=10):
     p = S.default_params(max_corners=500, levels=4, hypotheses=256)
     ctx = S.Context(w, h, p)
     est = torch.zeros((pairs, 4), dtype=torch.float32, device=dev)
-    out = torch.zeros((pairs, 8), dtype=torch.float32, device=dev)
+    out = torch.zeros((pairs, S.MOTION_WORDS), dtype=torch.float32, device=dev)
     q8 = lambda x: torch.clamp(torch.floor(x + 0.5), 0, 255).to(torch.uint8)
     for k in range(pairs):
         src, dst, st, n = ctx.track(q8(Ip[k]), q8(It[k]))

@@ -49,12 +49,17 @@ typedef enum {
     STAB_ERR_CAPACITY = -6        /* a device buffer would have overflowed */
 } stab_status;
 
-typedef enum { STAB_RIGID = 0, STAB_SIMILARITY = 1 } stab_model;        /* Sec. 4: 3 or 4 DOF */
+/* Sec. 4: rigid (3 DOF), similarity (4 DOF), or the hybrid mechanism of
+ * Sec. 4.1 that fits both every `dwell` transitions and keeps the one with the
+ * lower RMS distance for the next `dwell` transitions. */
+typedef enum { STAB_RIGID = 0, STAB_SIMILARITY = 1, STAB_HYBRID = 2 } stab_model;
 typedef enum { STAB_FP32 = 0, STAB_FP16_STORAGE = 1 } stab_precision;  /* storage of I, Ix, Iy planes */
 
 /* Flag bits of stab_motion.flags */
 #define STAB_FLAG_SKIPPED 1       /* fewer than min_fit pairs or no valid hypothesis */
 #define STAB_FLAG_DETECTED 2      /* corners were re-detected on the previous frame */
+#define STAB_FLAG_RIGID 4         /* the motion was fitted with the rigid model */
+#define STAB_FLAG_DECISION 8      /* hybrid mechanism: a decision transition ((t - 1) % dwell == 0) */
 
 typedef struct {
     int max_corners;      /* K: corners kept per detection (Sec. 3.1 fixes a count; <= 2048) */
@@ -76,6 +81,10 @@ typedef struct {
     int smooth_window;    /* averaging window W (Sec. 5.1; 1..63) */
     int model;            /* stab_model */
     int precision;        /* stab_precision */
+    int dwell;            /* hybrid mechanism: transitions between decisions (Sec. 4.1: 20) */
+    float crop_zoom;      /* composition crop (Sec. 5.1): output = centre region of the warped
+                             frame magnified by crop_zoom about the image centre; 1 = no crop,
+                             range [1, 4] */
 } stab_params;
 
 typedef struct {
@@ -84,6 +93,8 @@ typedef struct {
     int n_tracks;                    /* pairs that passed the forward-backward check */
     float rms;                       /* RMS residual of the refit over its inliers (px) */
     int flags;                       /* STAB_FLAG_* */
+    float e_rigid;                   /* RMS of the rigid fit made at this transition (px), -1 if none */
+    float e_similarity;              /* RMS of the similarity fit made at this transition, -1 if none */
 } stab_motion;
 
 typedef struct stab_ctx stab_ctx;
@@ -185,7 +196,12 @@ stab_status stab_track(stab_ctx *ctx, const uint8_t *prev_dev, const uint8_t *ne
  * kept, then the closed-form least-squares similarity (or rotation for
  * rigid) on its inliers.  src/dst: device points, count from *n_dev (device).
  * Fewer than min_fit pairs => identity with STAB_FLAG_SKIPPED.  Writes one
- * stab_motion to out_dev (device). */
+ * stab_motion to out_dev (device).  model STAB_HYBRID (Sec. 4.1): when
+ * (t - 1) % dwell == 0 both models are fitted and the rigid one is chosen iff
+ * both fits succeed and its RMS over its own inliers is strictly lower (only
+ * one fit succeeding chooses that one; none keeps the current choice, which
+ * starts as similarity); the choice is kept in the context and used alone on
+ * the other transitions. */
 stab_status stab_fit(stab_ctx *ctx, const float *src_dev, const float *dst_dev, const int *n_dev, int model,
                      int t, stab_motion *out_dev, void *stream);
 
@@ -193,7 +209,9 @@ stab_status stab_fit(stab_ctx *ctx, const float *src_dev, const float *dst_dev, 
  * motion must be the identity): C_t = sum_{k<=t} m_k, S_t = mean of C over
  * [t - (W-1)/2, t + W/2] clipped to [0, T-1], m'_t = m_t + S_t - C_t.
  * Writes mprime_dev (T x 4 floats) and Minv_dev (T x 6: the inverse warp of
- * m'_t; frame t-1 is composed with Minv_t). */
+ * m'_t composed with the crop zoom z of the context's parameters, i.e. output
+ * pixel p samples the compensated frame at c + (p - c) / z; frame t-1 is
+ * composed with Minv_t). */
 stab_status stab_smooth(stab_ctx *ctx, const stab_motion *motions_dev, int T, int window, float *mprime_dev,
                         float *Minv_dev, void *stream);
 

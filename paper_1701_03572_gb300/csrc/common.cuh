@@ -42,14 +42,15 @@ struct StreamState {
     long long tpl;        // LK template passes (feature x level x direction) of this step
     int n_det;            // corners of the last detection
     int n_above;          // candidates above the quality threshold (before the top-K cut)
+    int hyb_rigid;        // hybrid mechanism: the model held since the last decision (1 rigid)
 };
 
 struct StreamDev {
     int w, h, C, L, K;
     int lw[STAB_MAXL], lh[STAB_MAXL], lp[STAB_MAXL];   // level sizes, pitch (elements)
     // parameters
-    int r, max_iters, period, min_tracks, min_fit, H, rigid, W, prec;
-    float eps2, min_eig, quality, fb2, tau2;
+    int r, max_iters, period, min_tracks, min_fit, H, model, dwell, W, prec;
+    float eps2, min_eig, quality, fb2, tau2, zoom;
     unsigned long long seed;
     int roi_x0, roi_y0, roi_x1, roi_y1;
     // pyramids: two slots (frame parity); u8 levels and I / (Ix, Iy) planes

@@ -8,7 +8,10 @@
 // model and residual use one fixed IEEE FP32 operation sequence (explicit
 // _rn intrinsics, no contraction), so counts and the winning hypothesis are
 // reproducible bit for bit.  The closed-form least-squares refit on the
-// winner's inliers uses fixed-order FP32 block reductions.
+// winner's inliers uses fixed-order FP32 block reductions.  With the hybrid
+// mechanism (Sec. 4.1) a decision transition fits both models in the same CTA
+// and keeps the rigid one iff its RMS over its own inliers is strictly lower;
+// the choice is held in the stream state until the next decision.
 #include "kernels.cuh"
 
 namespace {
@@ -141,14 +144,17 @@ __global__ void __launch_bounds__(1024) k_compact(const StreamDev *__restrict__ 
 // thread per stream).  C_t = C_{t-1} + m_t; when frame u = t - 1 - W/2 >= 0 is
 // ready: S = mean of C over [max(0, u+1 - (W-1)/2), t], m' = m_{u+1} + (S -
 // C_{u+1}), inverse warp of m'.
-__device__ void inverse_warp(float4 mp, int w, int h, float *Minv)
+// Composition crop (Sec. 5.1): a zoom z about the centre applied to the
+// output, q = W(c + (p - c) / z) with W the inverse warp of m', which is the
+// inverse warp of (z tx, z ty, theta, log s + log z).
+__device__ void inverse_warp(float4 mp, int w, int h, float zoom, float *Minv)
 {
     const float cx = 0.5f * (float)(w - 1), cy = 0.5f * (float)(h - 1);
-    const float is = expf(-mp.w);
+    const float is = __fdiv_rn(expf(-mp.w), zoom);
     float sn, c;
     sincosf(mp.z, &sn, &c);
     const float a00 = is * c, a01 = is * sn, a10 = -is * sn, a11 = is * c;
-    const float ux = cx + mp.x, uy = cy + mp.y;
+    const float ux = cx + zoom * mp.x, uy = cy + zoom * mp.y;
     Minv[0] = a00; Minv[1] = a01; Minv[2] = cx - (a00 * ux + a01 * uy);
     Minv[3] = a10; Minv[4] = a11; Minv[5] = cy - (a10 * ux + a11 * uy);
 }
@@ -166,7 +172,8 @@ __device__ __forceinline__ float4 corrected(float4 m, float4 S, float4 C)
 
 __device__ __forceinline__ float4 mot4(const stab_motion &m) { return make_float4(m.tx, m.ty, m.theta, m.log_scale); }
 
-__device__ int smooth_step(stab_motion *mring, float4 *cring, long long t, int W, int w, int h, float *Minv)
+__device__ int smooth_step(stab_motion *mring, float4 *cring, long long t, int W, int w, int h, float zoom,
+                           float *Minv)
 {
     const int CR = STAB_CRING;
     const float4 Cp = t > 0 ? cring[(t - 1) % CR] : make_float4(0.f, 0.f, 0.f, 0.f);
@@ -182,25 +189,116 @@ __device__ int smooth_step(stab_motion *mring, float4 *cring, long long t, int W
     const float cnt = (float)(t - lo + 1);
     const float4 Sm = make_float4(__fdiv_rn(acc.x, cnt), __fdiv_rn(acc.y, cnt), __fdiv_rn(acc.z, cnt),
                                   __fdiv_rn(acc.w, cnt));
-    inverse_warp(corrected(mot4(mring[j % CR]), Sm, cring[j % CR]), w, h, Minv);
+    inverse_warp(corrected(mot4(mring[j % CR]), Sm, cring[j % CR]), w, h, zoom, Minv);
     return (int)u;
+}
+
+struct FitRes {
+    float tx, ty, th, ls, rms;
+    int inliers;
+    bool ok;
+};
+
+struct FitShared {
+    int wbs[16], wbh[16];
+    int best, bh;
+    float red[16][5];
+};
+
+// Robust fit of one model to the n staged centred pairs (every thread of the
+// block): hypotheses scored by inlier count, the first best kept, then the
+// closed-form least-squares refit on its inliers and their RMS residual.
+__device__ FitRes fit_model(const float2 *ss, const float2 *sd, int n, int rigid, const StreamDev &D, long long t,
+                            FitShared &sh)
+{
+    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5, nwarps = blockDim.x >> 5;
+    FitRes r;
+    r.ok = false;
+    r.tx = r.ty = r.th = r.ls = r.rms = 0.f;
+    r.inliers = 0;
+    int best = -1, bh = 0x7fffffff;
+    for (int hh = wid; hh < D.H; hh += nwarps) {
+        int i, j;
+        sample_pair(D.seed, t, hh, n, i, j);
+        float m[4];
+        int cnt = -1;
+        if (two_point(ss[i], ss[j], sd[i], sd[j], rigid, m)) {
+            int c = 0;
+            for (int k = lane; k < n; k += 32) c += is_inlier(m, ss[k], sd[k], D.tau2);
+            cnt = __reduce_add_sync(0xffffffffu, c);
+        }
+        if (cnt > best) { best = cnt; bh = hh; }
+    }
+    if (lane == 0) { sh.wbs[wid] = best; sh.wbh[wid] = bh; }
+    __syncthreads();
+    if (tid == 0) {
+        int b = -1, h = 0x7fffffff;
+        for (int k = 0; k < nwarps; ++k)
+            if (sh.wbs[k] > b || (sh.wbs[k] == b && sh.wbh[k] < h)) { b = sh.wbs[k]; h = sh.wbh[k]; }
+        sh.best = b; sh.bh = h;
+    }
+    __syncthreads();
+    if (sh.best < 2) return r;
+    int i, j;
+    sample_pair(D.seed, t, sh.bh, n, i, j);
+    float m[4];
+    two_point(ss[i], ss[j], sd[i], sd[j], rigid, m);
+    float v[5] = {0.f, 0.f, 0.f, 0.f, 0.f};
+    for (int k = tid; k < n; k += blockDim.x)
+        if (is_inlier(m, ss[k], sd[k], D.tau2)) {
+            v[0] += 1.f; v[1] += ss[k].x; v[2] += ss[k].y; v[3] += sd[k].x; v[4] += sd[k].y;
+        }
+    block_sum<5>(v, sh.red);
+    const float ni = v[0];
+    const float msx = v[1] / ni, msy = v[2] / ni, mdx = v[3] / ni, mdy = v[4] / ni;
+    float u[5] = {0.f, 0.f, 0.f, 0.f, 0.f};
+    for (int k = tid; k < n; k += blockDim.x)
+        if (is_inlier(m, ss[k], sd[k], D.tau2)) {
+            const float x0 = ss[k].x - msx, x1 = ss[k].y - msy;
+            const float y0 = sd[k].x - mdx, y1 = sd[k].y - mdy;
+            u[0] += x0 * y0 + x1 * y1;
+            u[1] += x0 * y1 - x1 * y0;
+            u[2] += x0 * x0 + x1 * x1;
+        }
+    block_sum<5>(u, sh.red);
+    if (!(u[2] > 0.f)) return r;
+    const float th = atan2f(u[1], u[0]);
+    const float sc = rigid ? 1.f : sqrtf(u[0] * u[0] + u[1] * u[1]) / u[2];
+    float sn, c;
+    sincosf(th, &sn, &c);
+    const float tx = mdx - sc * (c * msx - sn * msy);
+    const float ty = mdy - sc * (sn * msx + c * msy);
+    float e[5] = {0.f, 0.f, 0.f, 0.f, 0.f};
+    for (int k = tid; k < n; k += blockDim.x)
+        if (is_inlier(m, ss[k], sd[k], D.tau2)) {
+            const float px = sc * (c * ss[k].x - sn * ss[k].y) + tx;
+            const float py = sc * (sn * ss[k].x + c * ss[k].y) + ty;
+            e[0] += (sd[k].x - px) * (sd[k].x - px) + (sd[k].y - py) * (sd[k].y - py);
+        }
+    block_sum<5>(e, sh.red);
+    r.tx = tx; r.ty = ty; r.th = th; r.ls = logf(sc);
+    r.inliers = (int)ni;
+    r.rms = sqrtf(e[0] / ni);
+    r.ok = true;
+    return r;
 }
 
 __global__ void __launch_bounds__(512) k_fit(const StreamDev *__restrict__ S, FitIO io, int streaming)
 {
     __shared__ float2 ss[STAB_MAXK], sd[STAB_MAXK];
-    __shared__ int wbs[16], wbh[16];
-    __shared__ int s_best, s_bh;
-    __shared__ float sred[16][5];
+    __shared__ FitShared sh;
     const StreamDev &D = S[blockIdx.x];
     StreamState *st = D.st;
-    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5, nwarps = blockDim.x >> 5;
+    const int tid = threadIdx.x;
     const long long t = io.src ? io.t : st->t;
     int n = io.src ? *io.n : (t >= 1 ? st->n_pairs : 0);
     n = min(max(n, 0), D.K);
     const float2 *src = io.src ? io.src : D.pair_src;
     const float2 *dst = io.src ? io.dst : D.pair_dst;
-    const int rigid = io.src ? io.rigid : D.rigid;
+    const int model = io.src ? io.model : D.model;
+    const bool hybrid = model == STAB_HYBRID;
+    const bool decide = hybrid && t >= 1 && (t - 1) % D.dwell == 0;
+    int rigid = hybrid ? st->hyb_rigid : (model == STAB_RIGID);
     const float cx = __fmul_rn(0.5f, (float)(D.w - 1)), cy = __fmul_rn(0.5f, (float)(D.h - 1));
     for (int i = tid; i < n; i += blockDim.x) {
         float2 a = src[i], b = dst[i];
@@ -213,85 +311,39 @@ __global__ void __launch_bounds__(512) k_fit(const StreamDev *__restrict__ S, Fi
     out.inliers = 0;
     out.n_tracks = n;
     out.rms = 0.f;
+    out.e_rigid = out.e_similarity = -1.f;
     out.flags = (!io.src && st->due) ? STAB_FLAG_DETECTED : 0;
-    bool skip = (t < 1) || n < max(2, D.min_fit);
-    if (!skip) {
-        int best = -1, bh = 0x7fffffff;
-        for (int hh = wid; hh < D.H; hh += nwarps) {
-            int i, j;
-            sample_pair(D.seed, t, hh, n, i, j);
-            float m[4];
-            int cnt = -1;
-            if (two_point(ss[i], ss[j], sd[i], sd[j], rigid, m)) {
-                int c = 0;
-                for (int k = lane; k < n; k += 32) c += is_inlier(m, ss[k], sd[k], D.tau2);
-                cnt = __reduce_add_sync(0xffffffffu, c);
-            }
-            if (cnt > best) { best = cnt; bh = hh; }
-        }
-        if (lane == 0) { wbs[wid] = best; wbh[wid] = bh; }
-        __syncthreads();
-        if (tid == 0) {
-            int b = -1, h = 0x7fffffff;
-            for (int k = 0; k < nwarps; ++k)
-                if (wbs[k] > b || (wbs[k] == b && wbh[k] < h)) { b = wbs[k]; h = wbh[k]; }
-            s_best = b; s_bh = h;
-        }
-        __syncthreads();
-        if (s_best < 2) skip = true;
-        if (!skip) {
-            int i, j;
-            sample_pair(D.seed, t, s_bh, n, i, j);
-            float m[4];
-            two_point(ss[i], ss[j], sd[i], sd[j], rigid, m);
-            float v[5] = {0.f, 0.f, 0.f, 0.f, 0.f};
-            for (int k = tid; k < n; k += blockDim.x)
-                if (is_inlier(m, ss[k], sd[k], D.tau2)) {
-                    v[0] += 1.f; v[1] += ss[k].x; v[2] += ss[k].y; v[3] += sd[k].x; v[4] += sd[k].y;
-                }
-            block_sum<5>(v, sred);
-            const float ni = v[0];
-            const float msx = v[1] / ni, msy = v[2] / ni, mdx = v[3] / ni, mdy = v[4] / ni;
-            float u[3] = {0.f, 0.f, 0.f};
-            for (int k = tid; k < n; k += blockDim.x)
-                if (is_inlier(m, ss[k], sd[k], D.tau2)) {
-                    const float x0 = ss[k].x - msx, x1 = ss[k].y - msy;
-                    const float y0 = sd[k].x - mdx, y1 = sd[k].y - mdy;
-                    u[0] += x0 * y0 + x1 * y1;
-                    u[1] += x0 * y1 - x1 * y0;
-                    u[2] += x0 * x0 + x1 * x1;
-                }
-            float u5[5] = {u[0], u[1], u[2], 0.f, 0.f};
-            block_sum<5>(u5, sred);
-            if (!(u5[2] > 0.f)) {
-                skip = true;
-            } else {
-                const float th = atan2f(u5[1], u5[0]);
-                const float sc = rigid ? 1.f : sqrtf(u5[0] * u5[0] + u5[1] * u5[1]) / u5[2];
-                float sn, c;
-                sincosf(th, &sn, &c);
-                const float tx = mdx - sc * (c * msx - sn * msy);
-                const float ty = mdy - sc * (sn * msx + c * msy);
-                float e[5] = {0.f, 0.f, 0.f, 0.f, 0.f};
-                for (int k = tid; k < n; k += blockDim.x)
-                    if (is_inlier(m, ss[k], sd[k], D.tau2)) {
-                        const float px = sc * (c * ss[k].x - sn * ss[k].y) + tx;
-                        const float py = sc * (sn * ss[k].x + c * ss[k].y) + ty;
-                        e[0] += (sd[k].x - px) * (sd[k].x - px) + (sd[k].y - py) * (sd[k].y - py);
-                    }
-                block_sum<5>(e, sred);
-                out.tx = tx; out.ty = ty; out.theta = th; out.log_scale = logf(sc);
-                out.inliers = (int)ni;
-                out.rms = sqrtf(e[0] / ni);
-            }
+    if (decide) out.flags |= STAB_FLAG_DECISION;
+    FitRes res;
+    res.ok = false;
+    if (t >= 1 && n >= max(2, D.min_fit)) {
+        if (decide) {
+            const FitRes fr = fit_model(ss, sd, n, 1, D, t, sh);
+            const FitRes fs = fit_model(ss, sd, n, 0, D, t, sh);
+            if (fr.ok) out.e_rigid = fr.rms;
+            if (fs.ok) out.e_similarity = fs.rms;
+            if (fr.ok && fs.ok) rigid = fr.rms < fs.rms;
+            else if (fr.ok || fs.ok) rigid = fr.ok;
+            res = rigid ? fr : fs;
+        } else {
+            res = fit_model(ss, sd, n, rigid, D, t, sh);
+            if (res.ok) (rigid ? out.e_rigid : out.e_similarity) = res.rms;
         }
     }
-    if (skip && t >= 1) out.flags |= STAB_FLAG_SKIPPED;
+    if (res.ok) {
+        out.tx = res.tx; out.ty = res.ty; out.theta = res.th; out.log_scale = res.ls;
+        out.inliers = res.inliers;
+        out.rms = res.rms;
+    } else if (t >= 1) {
+        out.flags |= STAB_FLAG_SKIPPED;
+    }
+    if (rigid) out.flags |= STAB_FLAG_RIGID;
     if (tid == 0) {
+        if (decide) st->hyb_rigid = rigid;
         if (io.out) *io.out = out;
         if (!io.src) {
             D.mring[t % STAB_CRING] = out;
-            if (streaming) st->out_frame = smooth_step(D.mring, D.cring, t, D.W, D.w, D.h, D.Minv);
+            if (streaming) st->out_frame = smooth_step(D.mring, D.cring, t, D.W, D.w, D.h, D.zoom, D.Minv);
         }
     }
 }
@@ -325,11 +377,11 @@ __global__ void k_smooth_mp(const stab_motion *m, int T, int W, const float *Cbu
     }
 }
 
-__global__ void k_smooth_minv(const float *mprime, int T, int w, int h, float *Minv)
+__global__ void k_smooth_minv(const float *mprime, int T, int w, int h, float zoom, float *Minv)
 {
     for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < T; t += gridDim.x * blockDim.x)
         inverse_warp(make_float4(mprime[4 * t], mprime[4 * t + 1], mprime[4 * t + 2], mprime[4 * t + 3]), w, h,
-                     Minv + 6 * t);
+                     zoom, Minv + 6 * t);
 }
 
 __global__ void k_smooth_push(const StreamDev *__restrict__ S, long long t, const stab_motion *m, float *Minv,
@@ -339,7 +391,7 @@ __global__ void k_smooth_push(const StreamDev *__restrict__ S, long long t, cons
     const StreamDev &D = S[0];
     D.mring[t % STAB_CRING] = *m;
     float M[6];
-    int u = smooth_step(D.mring, D.cring, t, D.W, D.w, D.h, M);
+    int u = smooth_step(D.mring, D.cring, t, D.W, D.w, D.h, D.zoom, M);
     if (u >= 0)
         for (int k = 0; k < 6; ++k) Minv[k] = M[k];
     *ready = u;
@@ -363,12 +415,12 @@ void launch_fit(const Launch &L, const StreamDev *S, int n, FitIO io, int stream
     k_fit<<<n, 512, 0, L.stream>>>(S, io, streaming);
 }
 
-void launch_smooth_offline(const Launch &L, const stab_motion *m, int T, int W, int w, int h, float *mprime,
-                           float *Minv)
+void launch_smooth_offline(const Launch &L, const stab_motion *m, int T, int W, int w, int h, float zoom,
+                           float *mprime, float *Minv)
 {
     k_smooth_c<<<1, 32, 0, L.stream>>>(m, T, Minv);
     k_smooth_mp<<<(T + 255) / 256, 256, 0, L.stream>>>(m, T, W, Minv, mprime);
-    k_smooth_minv<<<(T + 255) / 256, 256, 0, L.stream>>>(mprime, T, w, h, Minv);
+    k_smooth_minv<<<(T + 255) / 256, 256, 0, L.stream>>>(mprime, T, w, h, zoom, Minv);
 }
 
 void launch_smooth_push(const Launch &L, const StreamDev *S, long long t, const stab_motion *m, float *Minv,

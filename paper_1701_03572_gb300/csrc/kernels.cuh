@@ -53,7 +53,7 @@ struct CompactIO {
 struct FitIO {
     const float2 *src, *dst;
     const int *n;
-    int rigid;
+    int model;     // stab_model
     long long t;
     stab_motion *out;
 };
@@ -92,8 +92,8 @@ void launch_lk(const Launch &L, int prec, int rcode, int variant, const StreamDe
 
 void launch_compact(const Launch &L, const StreamDev *S, int n, CompactIO io);
 void launch_fit(const Launch &L, const StreamDev *S, int n, FitIO io, int streaming);
-void launch_smooth_offline(const Launch &L, const stab_motion *m, int T, int W, int w, int h, float *mprime,
-                           float *Minv);
+void launch_smooth_offline(const Launch &L, const stab_motion *m, int T, int W, int w, int h, float zoom,
+                           float *mprime, float *Minv);
 void launch_smooth_push(const Launch &L, const StreamDev *S, long long t, const stab_motion *m, float *Minv,
                         int *ready);
 void launch_advance(const Launch &L, const StreamDev *S, int n);

@@ -91,7 +91,10 @@ stab_status check_params(const stab_params &p, int w, int h, std::string &err)
     if (p.redetect_period < 1) return fail(err, STAB_ERR_INVALID_ARG, "redetect_period < 1");
     if (p.hypotheses < 1 || p.hypotheses > 1 << 20) return fail(err, STAB_ERR_INVALID_ARG, "hypotheses out of range");
     if (p.smooth_window < 1 || p.smooth_window >= STAB_CRING) return fail(err, STAB_ERR_INVALID_ARG, "smooth_window out of [1, 63]");
-    if (p.model != STAB_RIGID && p.model != STAB_SIMILARITY) return fail(err, STAB_ERR_INVALID_ARG, "bad model");
+    if (p.model != STAB_RIGID && p.model != STAB_SIMILARITY && p.model != STAB_HYBRID)
+        return fail(err, STAB_ERR_INVALID_ARG, "bad model");
+    if (p.dwell < 1) return fail(err, STAB_ERR_INVALID_ARG, "dwell < 1");
+    if (!(p.crop_zoom >= 1.f && p.crop_zoom <= 4.f)) return fail(err, STAB_ERR_INVALID_ARG, "crop_zoom out of [1, 4]");
     if (p.precision != STAB_FP32 && p.precision != STAB_FP16_STORAGE) return fail(err, STAB_ERR_INVALID_ARG, "bad precision");
     int lw = w, lh = h;
     for (int l = 1; l < p.levels; ++l) { lw = (lw + 1) / 2; lh = (lh + 1) / 2; }
@@ -141,7 +144,8 @@ stab_status build(Pipeline &pp, int n, const int *w, const int *h, const int *C,
             for (int l = 0; l < D.L; ++l) D.lp[l] = up(D.lw[l], 64);
             D.r = p.win_radius; D.max_iters = p.max_iters; D.period = p.redetect_period;
             D.min_tracks = p.min_tracks; D.min_fit = p.min_fit; D.H = p.hypotheses;
-            D.rigid = p.model == STAB_RIGID; D.W = p.smooth_window; D.prec = p.precision;
+            D.model = p.model; D.dwell = p.dwell; D.zoom = p.crop_zoom;
+            D.W = p.smooth_window; D.prec = p.precision;
             D.eps2 = p.eps * p.eps; D.min_eig = p.min_eig; D.quality = p.quality;
             D.fb2 = p.fb_thresh * p.fb_thresh;
             {
@@ -354,6 +358,8 @@ stab_status stab_default_params(stab_params *o)
     o->smooth_window = 15;
     o->model = STAB_SIMILARITY;
     o->precision = STAB_FP32;
+    o->dwell = 20;
+    o->crop_zoom = 1.0f;
     return STAB_OK;
 }
 
@@ -471,10 +477,10 @@ stab_status stab_track(stab_ctx *c, const uint8_t *prev, const uint8_t *next, in
 stab_status stab_fit(stab_ctx *c, const float *src, const float *dst, const int *n, int model, int t,
                      stab_motion *out, void *stream)
 {
-    if (!c || !src || !dst || !n || !out || (model != STAB_RIGID && model != STAB_SIMILARITY))
+    if (!c || !src || !dst || !n || !out || (model != STAB_RIGID && model != STAB_SIMILARITY && model != STAB_HYBRID))
         return STAB_ERR_INVALID_ARG;
     CTX_LAUNCH(c, stream);
-    launch_fit(L, pp.ds, 1, FitIO{(const float2 *)src, (const float2 *)dst, n, model == STAB_RIGID, t, out}, 0);
+    launch_fit(L, pp.ds, 1, FitIO{(const float2 *)src, (const float2 *)dst, n, model, t, out}, 0);
     return cuda_check(pp.err, "stab_fit");
 }
 
@@ -482,7 +488,7 @@ stab_status stab_smooth(stab_ctx *c, const stab_motion *m, int T, int W, float *
 {
     if (!c || !m || !mprime || !Minv || T < 1 || W < 1) return STAB_ERR_INVALID_ARG;
     CTX_LAUNCH(c, stream);
-    launch_smooth_offline(L, m, T, W, pp.hs[0].w, pp.hs[0].h, mprime, Minv);
+    launch_smooth_offline(L, m, T, W, pp.hs[0].w, pp.hs[0].h, pp.hs[0].zoom, mprime, Minv);
     return cuda_check(pp.err, "stab_smooth");
 }
 

@@ -15,10 +15,11 @@ import torch
 from .build import LIB
 
 STAB_OK, STAB_WARN_SKIPPED = 0, 1
-STAB_RIGID, STAB_SIMILARITY = 0, 1
+STAB_RIGID, STAB_SIMILARITY, STAB_HYBRID = 0, 1, 2
 STAB_FP32, STAB_FP16_STORAGE = 0, 1
 STAB_TRACK_CONTINUE = 1
-STAB_FLAG_SKIPPED, STAB_FLAG_DETECTED = 1, 2
+STAB_FLAG_SKIPPED, STAB_FLAG_DETECTED, STAB_FLAG_RIGID, STAB_FLAG_DECISION = 1, 2, 4, 8
+MOTION_WORDS = 10          # 4-byte words of one stab_motion record
 
 
 class StabParams(C.Structure):
@@ -27,12 +28,13 @@ class StabParams(C.Structure):
                 ("roi_margin_y", C.c_int), ("redetect_period", C.c_int), ("min_tracks", C.c_int),
                 ("fb_thresh", C.c_float), ("inlier_thresh", C.c_float), ("hypotheses", C.c_int),
                 ("seed", C.c_uint64), ("min_fit", C.c_int), ("smooth_window", C.c_int), ("model", C.c_int),
-                ("precision", C.c_int)]
+                ("precision", C.c_int), ("dwell", C.c_int), ("crop_zoom", C.c_float)]
 
 
 class StabMotion(C.Structure):
     _fields_ = [("tx", C.c_float), ("ty", C.c_float), ("theta", C.c_float), ("log_scale", C.c_float),
-                ("inliers", C.c_int), ("n_tracks", C.c_int), ("rms", C.c_float), ("flags", C.c_int)]
+                ("inliers", C.c_int), ("n_tracks", C.c_int), ("rms", C.c_float), ("flags", C.c_int),
+                ("e_rigid", C.c_float), ("e_similarity", C.c_float)]
 
 
 class StreamDesc(C.Structure):
@@ -122,11 +124,11 @@ def default_params(**kw) -> StabParams:
 
 
 def motions_from_raw(raw: torch.Tensor) -> dict:
-    """Decode a (T, 8) float32 tensor of stab_motion records."""
+    """Decode a (T, MOTION_WORDS) float32 tensor of stab_motion records."""
     r = raw.detach().cpu().contiguous()
     iv = r.view(torch.int32)
     return dict(m=r[:, :4].double().numpy(), inliers=iv[:, 4].numpy(), n_tracks=iv[:, 5].numpy(),
-                rms=r[:, 6].numpy(), flags=iv[:, 7].numpy())
+                rms=r[:, 6].numpy(), flags=iv[:, 7].numpy(), e_rigid=r[:, 8].numpy(), e_similarity=r[:, 9].numpy())
 
 
 class StabError(RuntimeError):
@@ -227,7 +229,7 @@ class Context:
 
     def fit(self, src: torch.Tensor, dst: torch.Tensor, n: torch.Tensor, model: int, t: int,
             out: torch.Tensor | None = None):
-        out = out if out is not None else torch.zeros(8, dtype=torch.float32, device=src.device)
+        out = out if out is not None else torch.zeros(MOTION_WORDS, dtype=torch.float32, device=src.device)
         self._chk(lib().stab_fit(self._h, _p(src.contiguous()), _p(dst.contiguous()), _p(n), model, t, _p(out),
                                  _s()), "stab_fit")
         return out
@@ -326,7 +328,7 @@ class Batch:
         arr = (StabMotion * self.n)()
         self._chk(lib().stab_batch_motions(self._h, arr), "stab_batch_motions")
         return [dict(m=(a.tx, a.ty, a.theta, a.log_scale), inliers=a.inliers, n_tracks=a.n_tracks, rms=a.rms,
-                     flags=a.flags) for a in arr]
+                     flags=a.flags, e_rigid=a.e_rigid, e_similarity=a.e_similarity) for a in arr]
 
     def step_profiled(self, stream=None):
         """One step without a graph; returns {kernel name: ms} (synchronous)."""

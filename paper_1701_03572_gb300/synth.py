@@ -244,3 +244,25 @@ def make_pair_f32(w: int, h: int, seed: int, device: str = "cpu", max_rot_deg=3.
     prev = prev + noise_sigma * torch.randn(prev.shape, generator=gen, dtype=torch.float64, device=dev)
     cur = cur + noise_sigma * torch.randn(cur.shape, generator=gen, dtype=torch.float64, device=dev)
     return dict(prev=prev.clamp(0, 255).float(), cur=cur.clamp(0, 255).float(), theta=th)
+
+
+def hybrid_pairs(radial: float, scale: float, seed: int = 7):
+    """Point pairs in a 320 x 240 frame (pixel coordinates, FP32) that decide
+    the rigid / similarity comparison either way: 40 within 5 px of the centre
+    and 20 on a circle of radius 110 about it, all scaled about the centre by
+    `scale`, the circle then pushed `radial` px outward, and all moved by the
+    same rigid motion (theta = 0.01, t = (2, -1)).  Returns src, dst, w, h."""
+    w, h = 320, 240
+    c = np.array([(w - 1) / 2, (h - 1) / 2])
+    rng = np.random.default_rng(seed)
+    th = 0.01
+    R = np.array([[math.cos(th), -math.sin(th)], [math.sin(th), math.cos(th)]])
+    t = np.array([2.0, -1.0])
+    near = rng.uniform(-5, 5, (40, 2))
+    ang = np.linspace(0, 2 * math.pi, 20, endpoint=False)
+    u = np.stack([np.cos(ang), np.sin(ang)], 1)
+    far = 110 * u
+    src = np.concatenate([near, far])
+    tgt = np.concatenate([near * scale, far * scale + radial * u])
+    dst = tgt @ R.T + t
+    return (src + c).astype(np.float32), (dst + c).astype(np.float32), w, h

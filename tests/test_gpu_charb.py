@@ -116,7 +116,7 @@ def test_gauss_newton_refines_the_tracker_estimate():
         ctx = S.Context(W, H, S.default_params(max_corners=500, levels=4, hypotheses=256))
         src, dst, status, n = ctx.track(torch.as_tensor(a).cuda(), torch.as_tensor(b).cuda())
         out = ctx.fit(src, dst, n, S.STAB_SIMILARITY, 1)
-        est[p] = S.motions_from_raw(out.view(1, 8))["m"][0]
+        est[p] = S.motions_from_raw(out.view(1, S.MOTION_WORDS))["m"][0]
     th0 = torch.as_tensor(est).cuda()
     th = S.charb_gauss_newton(It, Ip, th0, 10, M, EPS)
     torch.cuda.synchronize()

@@ -1,0 +1,225 @@
+"""GPU path vs the CPU oracle for the hybrid rigid/similarity mechanism
+(Sec. 4.1) and the composition crop (Sec. 5.1).
+
+Bars:
+  * hybrid decisions on identical pairs: the decision schedule, the chosen
+    model and the inlier counts equal the oracle's wherever the oracle's two
+    RMS values differ by more than 1e-3 px (FP32 vs FP64 refits; nearer ties
+    may go either way); each RMS within 1e-3 px; parameters within 1e-4
+    (angle, log-scale) and 0.02 px (translation), as for the single-model fit;
+  * whole path: the pairs themselves differ by the tracker's 0.01 px, so the
+    margin and the RMS bar are 0.01 px and the parameters take the whole-path
+    bars (2e-4, 0.05 px) without inlier counts;
+  * crop: inverse maps within the smoothing bound; warped bytes bit-exact for
+    a given map; composed frames within the whole-path bars.
+"""
+import dataclasses
+
+import numpy as np
+import pytest
+import torch
+
+from oracle import oracle as O
+from paper_1701_03572_gb300 import stab as S
+from paper_1701_03572_gb300.synth import CONFIG_SPECS, hybrid_pairs, make_clip
+
+pytestmark = pytest.mark.gpu
+
+DEV = "cuda"
+SAME_PAIRS = dict(margin=1e-3, tol_a=1e-4, tol_t=0.02, inliers=True)
+WHOLE_PATH = dict(margin=1e-2, tol_a=2e-4, tol_t=0.05, inliers=False)
+
+
+def _cuda(a):
+    return torch.as_tensor(np.ascontiguousarray(a)).to(DEV)
+
+
+def _near_tie(ref, margin):
+    return ref["decision"] and ref["e_rigid"] >= 0 and ref["e_sim"] >= 0 and \
+        abs(ref["e_rigid"] - ref["e_sim"]) <= margin
+
+
+def _check_fit(m, ref, k=0, margin=1e-3, tol_a=1e-4, tol_t=0.02, inliers=True):
+    """GPU motion record k against an oracle fit_transition result; returns
+    the GPU's model (True = rigid)."""
+    f = ref["f"]
+    assert bool(m["flags"][k] & S.STAB_FLAG_DECISION) == ref["decision"]
+    for key, e in (("e_rigid", ref["e_rigid"]), ("e_similarity", ref["e_sim"])):
+        if e < 0:
+            assert m[key][k] == -1.0
+        else:
+            assert abs(m[key][k] - e) < margin
+    rigid = bool(m["flags"][k] & S.STAB_FLAG_RIGID)
+    if not _near_tie(ref, margin):
+        assert rigid == ref["rigid"]
+    if rigid == ref["rigid"]:
+        if inliers:
+            assert m["inliers"][k] == f["inliers"]
+        g = m["m"][k]
+        assert abs(g[2] - f["m"][2]) < tol_a and abs(g[3] - f["m"][3]) < tol_a
+        assert np.abs(g[:2] - f["m"][:2]).max() < tol_t
+    return rigid
+
+
+def test_hybrid_fit_on_scripted_pairs():
+    # dwell 4: transitions 1 and 5 decide, 2, 4 and 6 hold; each transition's
+    # pairs favour the model not currently held
+    rig = hybrid_pairs(3.0, 1.0)
+    sim = hybrid_pairs(0.0, 1.02)
+    op = O.Params(hybrid=True, dwell=4, hypotheses=100, seed=0)
+    ctx = S.Context(320, 240, S.default_params(model=S.STAB_HYBRID, dwell=4, hypotheses=100, seed=0,
+                                               max_corners=64))
+    cur = False
+    for t, (src, dst, w, h), want in [(1, rig, True), (2, sim, True), (4, sim, True), (5, sim, False),
+                                       (6, rig, False)]:
+        ref = O.fit_transition(src, dst, w, h, t, op, cur)
+        assert ref["rigid"] is want
+        n = torch.tensor([len(src)], dtype=torch.int32, device=DEV)
+        out = ctx.fit(_cuda(src), _cuda(dst), n, S.STAB_HYBRID, t)
+        torch.cuda.synchronize()
+        m = S.motions_from_raw(out.view(1, S.MOTION_WORDS))
+        assert _check_fit(m, ref, **SAME_PAIRS) is want, t
+        cur = ref["rigid"]
+    assert ctx.sync() == 0
+
+
+def test_hybrid_decision_with_too_few_pairs_keeps_the_model():
+    ctx = S.Context(320, 240, S.default_params(model=S.STAB_HYBRID, dwell=2, max_corners=64))
+    src, dst, _, _ = hybrid_pairs(3.0, 1.0)
+    n = torch.tensor([len(src)], dtype=torch.int32, device=DEV)
+    out1 = ctx.fit(_cuda(src), _cuda(dst), n, S.STAB_HYBRID, 1)          # decides: rigid
+    few = torch.tensor([5], dtype=torch.int32, device=DEV)
+    out3 = ctx.fit(_cuda(src), _cuda(dst), few, S.STAB_HYBRID, 3)        # decision due, too few pairs
+    out4 = ctx.fit(_cuda(src), _cuda(dst), n, S.STAB_HYBRID, 4)          # held: rigid
+    torch.cuda.synchronize()
+    m1, m3, m4 = (S.motions_from_raw(o.view(1, S.MOTION_WORDS)) for o in (out1, out3, out4))
+    assert m1["flags"][0] & S.STAB_FLAG_RIGID
+    assert m3["flags"][0] & S.STAB_FLAG_SKIPPED and m3["flags"][0] & S.STAB_FLAG_DECISION
+    assert m3["flags"][0] & S.STAB_FLAG_RIGID and m3["e_rigid"][0] == -1 and m3["e_similarity"][0] == -1
+    assert m4["flags"][0] & S.STAB_FLAG_RIGID and not m4["flags"][0] & S.STAB_FLAG_DECISION
+    assert m4["inliers"][0] == 40 and m4["m"][0][3] == 0.0
+
+
+def _gpu_clip(frames, p, T):
+    h, w = frames.shape[1:3]
+    ctx = S.Context(w, h, p)
+    raw = torch.zeros((T, S.MOTION_WORDS), dtype=torch.float32, device=DEV)
+    fr = _cuda(frames)
+    for t in range(1, T):
+        src, dst, status, n = ctx.track(fr[t - 1], fr[t], cont=t > 1)
+        ctx.fit(src, dst, n, p.model, t, out=raw[t])
+    mp, Minv = ctx.smooth(raw, p.smooth_window)
+    outs = torch.zeros_like(fr)
+    for t in range(1, T):
+        ctx.warp(fr[t - 1], Minv[t], out=outs[t - 1])
+    torch.cuda.synchronize()
+    assert ctx.sync() == 0
+    return raw, Minv, outs
+
+
+@pytest.mark.parametrize("cfg,zoom", [(0, 1.0), (0, 1.1), (1, 1.05)])
+def test_hybrid_and_crop_whole_path_vs_oracle(cfg, zoom):
+    T = 13
+    clip = make_clip(dataclasses.replace(CONFIG_SPECS[cfg], frames=T), 70 + cfg)
+    frames = clip["frames"].numpy()
+    K, L, H, W = (200, 3, 100, 15) if cfg == 0 else (500, 4, 256, 30)
+    op = O.Params(max_corners=K, levels=L, hypotheses=H, smooth_window=W, hybrid=True, dwell=4, crop_zoom=zoom)
+    gp = S.default_params(max_corners=K, levels=L, hypotheses=H, smooth_window=W, model=S.STAB_HYBRID, dwell=4,
+                          crop_zoom=zoom)
+    ref = O.run_clip(frames, op)
+    raw, Minv, outs = _gpu_clip(frames, gp, T)
+    m = S.motions_from_raw(raw)
+    assert [t for t in range(1, T) if m["flags"][t] & S.STAB_FLAG_DECISION] == [1, 5, 9]
+    assert (m["flags"][1:] & S.STAB_FLAG_SKIPPED == 0).all()
+    same_models = agree = True
+    for t in range(1, T):
+        r = dict(f=dict(m=ref["incs"][t], inliers=ref["n_inliers"][t]), decision=bool(ref["decision"][t]),
+                 rigid=bool(ref["rigid_used"][t]), e_rigid=ref["e_rigid"][t], e_sim=ref["e_sim"][t])
+        if r["decision"]:
+            # a near-tie may go the other way; the dwell block then runs the other model
+            agree = _check_fit(m, r, t, **WHOLE_PATH) == r["rigid"]
+            same_models &= agree
+        elif agree:
+            _check_fit(m, r, t, **WHOLE_PATH)
+    if same_models:
+        d = np.abs(outs.cpu().numpy()[:T - 1].astype(int) - ref["out"][:T - 1].astype(int))
+        assert (d > 1).mean() < 0.02 and d.mean() < 0.3
+
+
+@pytest.mark.parametrize("w,h,C,zoom", [(320, 240, 1, 1.1), (1920, 1080, 3, 1.25), (77, 53, 3, 2.0)])
+def test_crop_zoom_warp_bit_exact(w, h, C, zoom):
+    rng = np.random.default_rng(w + C)
+    shape = (h, w) if C == 1 else (h, w, C)
+    img = rng.integers(0, 256, shape, dtype=np.uint8)
+    ctx = S.Context(w, h, S.default_params(crop_zoom=zoom))
+    for m in ([0, 0, 0, 0], [3.7, -2.2, 0.02, 0.01], [-40.0, 25.0, -0.05, -0.03]):
+        Minv = O.warp_inverse(np.array(m, np.float64), w, h, zoom)
+        out = ctx.warp(_cuda(img), _cuda(Minv))
+        torch.cuda.synchronize()
+        assert np.array_equal(out.cpu().numpy(), O.warp(img, Minv)), m
+
+
+@pytest.mark.parametrize("zoom", [1.0, 1.1, 3.0])
+def test_crop_zoom_smoothing_offline_and_streaming(zoom):
+    T, W = 40, 15
+    rng = np.random.default_rng(5)
+    m = np.zeros((T, 4))
+    m[1:] = np.stack([0.5 + rng.normal(0, 2, T - 1), rng.normal(0, 2, T - 1), rng.normal(0, 0.01, T - 1),
+                      rng.normal(0, 0.005, T - 1)], 1)
+    m32 = m.astype(np.float32)
+    raw = np.zeros((T, S.MOTION_WORDS), np.float32)
+    raw[:, :4] = m32
+    ctx = S.Context(640, 480, S.default_params(smooth_window=W, crop_zoom=zoom))
+    mp, Minv = ctx.smooth(_cuda(raw), W)
+    torch.cuda.synchronize()
+    _, _, ref = O.smooth(m32.astype(np.float64), W)
+    tol_t = 4 * T * np.spacing(np.float32(T)) + 1e-4
+    refM = np.stack([O.warp_inverse(ref[t], 640, 480, zoom) for t in range(T)])
+    assert np.abs(Minv.cpu().numpy() - refM).max() < 1e-3 + tol_t
+    # the streaming smoother emits the same maps
+    ctx2 = S.Context(640, 480, S.default_params(smooth_window=W, crop_zoom=zoom))
+    Mo = Minv.cpu().numpy()
+    for t in range(1, T):
+        M, ready = ctx2.smooth_push(_cuda(raw[t]))
+        torch.cuda.synchronize()
+        u = int(ready.item())
+        if u >= 0 and u + 1 + W // 2 <= T - 1:
+            assert np.array_equal(M.cpu().numpy(), Mo[u + 1])
+
+
+def test_batch_hybrid_and_crop_equal_single_stream_path():
+    """The batched graph step with the hybrid mechanism and a crop zoom
+    reproduces the single-stream path bit for bit (the streaming smoother and
+    the offline one emit the same maps; the hybrid choice is kept per stream)."""
+    T = 14
+    clips = [make_clip(dataclasses.replace(CONFIG_SPECS[0], frames=T), s)["frames"].numpy() for s in (80, 81)]
+    params = [S.default_params(max_corners=200, levels=3, smooth_window=9, precision=1, model=S.STAB_HYBRID,
+                               dwell=3, crop_zoom=1.08),
+              S.default_params(max_corners=150, levels=3, smooth_window=9, precision=1, model=S.STAB_HYBRID,
+                               dwell=5, crop_zoom=1.0)]
+    b = S.Batch([(320, 240, 1, p) for p in params])
+    outs = [[] for _ in clips]
+    motions = [[] for _ in clips]
+    for t in range(T):
+        for i, f in enumerate(clips):
+            b.input_slot(i, t % b.ring).copy_(_cuda(f[t]))
+        b.step(use_graph=True)
+        torch.cuda.synchronize()
+        for i in range(len(clips)):
+            motions[i].append(b.motions()[i])
+            if t - 1 - 9 // 2 >= 0:
+                outs[i].append(b.output(i).cpu().numpy().copy())
+    assert b.sync() == 0
+    for i, f in enumerate(clips):
+        p32 = S.default_params(**{k: getattr(params[i], k) for k, _ in S.StabParams._fields_})
+        p32.precision = 0
+        raw, Minv, o = _gpu_clip(f, p32, T)
+        m = S.motions_from_raw(raw)
+        for t in range(1, T):
+            assert np.array_equal(np.array(motions[i][t]["m"], np.float32), m["m"][t].astype(np.float32)), (i, t)
+            keep = ~S.STAB_FLAG_DETECTED          # set by the batched step only
+            assert motions[i][t]["flags"] & keep == m["flags"][t] & keep, (i, t)
+            assert np.float32(motions[i][t]["e_rigid"]) == m["e_rigid"][t]
+        oc = o.cpu().numpy()
+        for k, frame in enumerate(outs[i]):
+            assert np.array_equal(frame, oc[k]), (i, k)

@@ -186,7 +186,7 @@ def test_fit_parity(cfg, rigid, H):
     n = torch.tensor([len(src)], dtype=torch.int32, device=DEV)
     out = ctx.fit(_cuda(src), _cuda(dst), n, 0 if rigid else 1, 1)
     torch.cuda.synchronize()
-    m = S.motions_from_raw(out.view(1, 8))
+    m = S.motions_from_raw(out.view(1, S.MOTION_WORDS))
     assert m["flags"][0] == 0 and ref["flags"] == 0
     assert m["inliers"][0] == ref["inliers"]
     assert m["n_tracks"][0] == len(src)
@@ -207,7 +207,7 @@ def test_fit_skip_and_degenerate():
     out2 = ctx.fit(_cuda(same), _cuda(same), n2, 1, 2)
     torch.cuda.synchronize()
     for o in (out, out2):
-        m = S.motions_from_raw(o.view(1, 8))
+        m = S.motions_from_raw(o.view(1, S.MOTION_WORDS))
         assert m["flags"][0] & S.STAB_FLAG_SKIPPED and np.all(m["m"][0] == 0)
 
 
@@ -219,7 +219,7 @@ def test_smoothing_parity(T, W):
     m[1:] = np.stack([0.5 + rng.normal(0, 2, T - 1), rng.normal(0, 2, T - 1), rng.normal(0, 0.01, T - 1),
                       rng.normal(0, 0.005, T - 1)], 1)
     m32 = m.astype(np.float32)
-    raw = np.zeros((T, 8), np.float32)
+    raw = np.zeros((T, S.MOTION_WORDS), np.float32)
     raw[:, :4] = m32
     ctx = S.Context(640, 480, _params(smooth_window=W))
     mp, Minv = ctx.smooth(_cuda(raw), W)
@@ -261,7 +261,7 @@ def test_warp_bit_exact(w, h, C):
 def _gpu_clip(frames, p, T):
     h, w = frames.shape[1:3]
     ctx = S.Context(w, h, p)
-    raw = torch.zeros((T, 8), dtype=torch.float32, device=DEV)
+    raw = torch.zeros((T, S.MOTION_WORDS), dtype=torch.float32, device=DEV)
     fr = _cuda(frames)
     for t in range(1, T):
         src, dst, status, n = ctx.track(fr[t - 1], fr[t], cont=t > 1)
@@ -363,7 +363,7 @@ def test_autotuner_picks_a_variant_and_caches_it(tmp_path):
     for i, f in enumerate(clips):
         ctx = S.Context(320, 240, p)
         ctx.set_lk_variant(v)
-        raw = torch.zeros((T, 8), dtype=torch.float32, device=DEV)
+        raw = torch.zeros((T, S.MOTION_WORDS), dtype=torch.float32, device=DEV)
         fr = _cuda(f)
         for t in range(1, T):
             src, dst, status, n = ctx.track(fr[t - 1], fr[t], cont=t > 1)

@@ -50,7 +50,7 @@ def test_fp16_vs_fp32_storage_error_table():
         # whole path: motions and composed frames
         ctx2 = S.Context(w, h, p)
         fr = torch.as_tensor(frames).cuda()
-        raw = torch.zeros((T, 8), dtype=torch.float32, device="cuda")
+        raw = torch.zeros((T, S.MOTION_WORDS), dtype=torch.float32, device="cuda")
         for t in range(1, T):
             src, dst, st, n = ctx2.track(fr[t - 1], fr[t], cont=t > 1)
             ctx2.fit(src, dst, n, p.model, t, out=raw[t])

@@ -38,10 +38,14 @@ def test_default_params_and_argument_errors_without_a_device():
     p = S.default_params()
     assert (p.max_corners, p.levels, p.win_radius, p.max_iters, p.redetect_period) == (200, 3, 10, 30, 5)
     assert abs(p.eps - 0.01) < 1e-9 and p.model == S.STAB_SIMILARITY and p.precision == S.STAB_FP32
+    # the last fields line up with the library's layout (hybrid dwell, crop zoom)
+    assert p.dwell == 20 and p.crop_zoom == 1.0
+    assert C.sizeof(S.StabMotion) == 4 * S.MOTION_WORDS
     L = S.lib()
     h = C.c_void_p()
     bad = [dict(max_corners=0), dict(max_corners=4096), dict(levels=0), dict(levels=9), dict(win_radius=13),
-           dict(smooth_window=64), dict(model=7), dict(precision=3), dict(inlier_thresh=0.0), dict(roi_margin_x=1)]
+           dict(smooth_window=64), dict(model=7), dict(precision=3), dict(inlier_thresh=0.0), dict(roi_margin_x=1),
+           dict(model=3), dict(dwell=0), dict(crop_zoom=0.5), dict(crop_zoom=4.5), dict(crop_zoom=float("nan"))]
     for kw in bad:
         q = S.default_params(**kw)
         assert L.stab_create(320, 240, C.byref(q), C.byref(h)) == -1, kw

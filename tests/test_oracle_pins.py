@@ -14,6 +14,7 @@ import pytest
 from scipy import ndimage
 
 from oracle import oracle as O
+from paper_1701_03572_gb300.synth import hybrid_pairs
 
 GOLD = os.path.join(os.path.dirname(__file__), "golden")
 
@@ -551,27 +552,6 @@ def test_pipeline_recovers_generator_motion():
 
 
 # ------------------------------------------- hybrid mechanism (Sec. 4.1) --
-def _hybrid_pairs(radial: float, scale: float, seed: int = 7):
-    """Point pairs in a 320 x 240 frame (pixel coordinates, FP32): 40 within
-    5 px of the centre and 20 on a circle of radius 110 about it, all scaled
-    about the centre by `scale`, the circle then pushed `radial` px outward,
-    and all moved by the same rigid motion (theta = 0.01, t = (2, -1))."""
-    w, h = 320, 240
-    c = np.array([(w - 1) / 2, (h - 1) / 2])
-    rng = np.random.default_rng(seed)
-    th = 0.01
-    R = np.array([[math.cos(th), -math.sin(th)], [math.sin(th), math.cos(th)]])
-    t = np.array([2.0, -1.0])
-    near = rng.uniform(-5, 5, (40, 2))
-    ang = np.linspace(0, 2 * math.pi, 20, endpoint=False)
-    u = np.stack([np.cos(ang), np.sin(ang)], 1)
-    far = 110 * u
-    src = np.concatenate([near, far])
-    tgt = np.concatenate([near * scale, far * scale + radial * u])
-    dst = tgt @ R.T + t
-    return (src + c).astype(np.float32), (dst + c).astype(np.float32), w, h
-
-
 def test_hybrid_choice_rule():
     # rigid iff both fits exist and rigid's RMS is strictly lower; a failed
     # fit cannot be chosen; no fit keeps the current choice
@@ -586,7 +566,7 @@ def test_hybrid_choice_rule():
 def test_hybrid_prefers_similarity_under_a_scale_change():
     # scale 1.02 about the centre: the far pairs move 2.2 px more than any
     # rotation + translation explains (rigid outliers), the near ones < 0.1 px
-    src, dst, w, h = _hybrid_pairs(0.0, 1.02)
+    src, dst, w, h = hybrid_pairs(0.0, 1.02)
     fr = O.fit(src, dst, w, h, True, 100, 0, 1)
     fs = O.fit(src, dst, w, h, False, 100, 0, 1)
     assert fr["inliers"] == 40 and fr["mask"][:40].all()
@@ -602,7 +582,7 @@ def test_hybrid_prefers_rigid_when_similarity_buys_inliers_with_error():
     # pairs); the similarity through two circle points scales by 1 + 3/110 and
     # keeps all 60, so its least squares leaves the near pairs a residual of
     # about 0.027 r (E[r^2] = 50/3 over the 10 x 10 square): E_s ~ 0.09 px
-    src, dst, w, h = _hybrid_pairs(3.0, 1.0)
+    src, dst, w, h = hybrid_pairs(3.0, 1.0)
     fr = O.fit(src, dst, w, h, True, 100, 0, 1)
     fs = O.fit(src, dst, w, h, False, 100, 0, 1)
     assert fr["inliers"] == 40 and fr["mask"][:40].all() and fr["rms"] < 1e-4
@@ -616,8 +596,8 @@ def test_hybrid_transitions_on_scripted_pairs():
     # dwell 4: transitions 1 and 5 decide, 2-4 and 6 hold.  Each transition
     # gets pairs that favour the model NOT currently held, so a decision
     # switches and a held transition must still fit the held model.
-    rig = _hybrid_pairs(3.0, 1.0)       # rigid wins a decision (40 inliers, log-scale 0)
-    sim = _hybrid_pairs(0.0, 1.02)      # similarity wins a decision (60 inliers, log-scale log 1.02)
+    rig = hybrid_pairs(3.0, 1.0)       # rigid wins a decision (40 inliers, log-scale 0)
+    sim = hybrid_pairs(0.0, 1.02)      # similarity wins a decision (60 inliers, log-scale log 1.02)
     p = O.Params(hybrid=True, dwell=4, hypotheses=100, seed=0)
     script = [(1, rig, True, True), (2, sim, False, True), (4, sim, False, True),
               (5, sim, True, False), (6, rig, False, False)]
