@@ -17,7 +17,11 @@
 // it under the exponent pattern 0x4B000000, floor(q) for |q| < 2^22 is
 // (q + 1.5 * 2^23 rounded down) - 1.5 * 2^23, and the final floor(v + 0.5) is
 // read from the low byte of (v + 0.5) + 2^23 rounded down.  Each is exact, so
-// the results equal the plain floorf / conversion forms bit for bit.
+// the results equal the plain floorf / conversion forms bit for bit.  The FP32
+// arithmetic runs on pixel pairs with the packed f32x2 forms of add / sub / fma
+// (each lane the same IEEE operation, so again the same bits).  One warp
+// derives each tile's job (stream, map, source box) two tiles ahead and
+// publishes it in shared memory.
 #include "kernels.cuh"
 
 namespace {
@@ -34,6 +38,7 @@ struct WJob {
     uint8_t *dst;
     int sp, dp, w, h, C, x0, y0;
     int by0, b0, rows, nvec;
+    int vq, vr, vinv;   // 256 / nvec, 256 % nvec, ceil(2^16 / nvec): the staging loop's stride
     int mode;      // 0 nothing to write, 1 staged, 2 direct gather
     bool edge;     // the box leaves the image: per-pixel range test
     float M[6];
@@ -47,12 +52,51 @@ __device__ __forceinline__ void cp_async16(void *smem, const void *gmem, int src
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait1() { asm volatile("cp.async.wait_group 1;\n" ::: "memory"); }
 
-// Exact floor for |q| < 2^22: value and integer.
-__device__ __forceinline__ float floor_exact(float q, int &qi)
+// Packed pair of FP32 values (lane 0 in the low word) and the f32x2 forms.
+typedef unsigned long long f2;
+__device__ __forceinline__ f2 pk(float lo, float hi)
 {
-    const float r = __fadd_rd(q, kFloorMagic);
-    qi = __float_as_int(r) - kFloorBits;
-    return __fsub_rn(r, kFloorMagic);
+    f2 r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(lo), "f"(hi));
+    return r;
+}
+__device__ __forceinline__ void upk(f2 v, float &lo, float &hi) { asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(v)); }
+__device__ __forceinline__ f2 fma2(f2 a, f2 b, f2 c)
+{
+    f2 d;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+    return d;
+}
+__device__ __forceinline__ f2 add2(f2 a, f2 b)
+{
+    f2 d;
+    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+__device__ __forceinline__ f2 add2_rd(f2 a, f2 b)
+{
+    f2 d;
+    asm("add.rm.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+__device__ __forceinline__ f2 sub2(f2 a, f2 b)
+{
+    f2 d;
+    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+
+// Bilinear values of two pixels from biased taps (2^23 + byte), rounded half
+// up; the low byte of each lane's bits is the result.  The lerps are the fma
+// sequence of the plain form (differences of biased taps are exact, and the
+// unbiased corner is tap - 2^23).
+__device__ __forceinline__ f2 lerp2(f2 ax, f2 ay, f2 b00, f2 b01, f2 b10, f2 b11)
+{
+    const f2 t23 = pk(kTwo23, kTwo23), half = pk(0.5f, 0.5f);
+    const f2 top = fma2(ax, sub2(b01, b00), sub2(b00, t23));
+    const f2 bot = fma2(ax, sub2(b11, b10), sub2(b10, t23));
+    const f2 v = fma2(ay, sub2(bot, top), top);
+    return add2_rd(add2(v, half), t23);
 }
 
 // Byte `sel` of word t as the float 2^23 + byte.
@@ -60,18 +104,6 @@ template <int SEL>
 __device__ __forceinline__ float byte_biased(unsigned t)
 {
     return __uint_as_float(__byte_perm(t, 0x4B000000u, 0x7540 | SEL));
-}
-
-// Bilinear value from biased taps (2^23 + byte), rounded half up; returns a
-// word whose low byte is the result.  top / bottom / vertical lerps are the
-// same fma sequence as the unbiased form (differences of biased taps are
-// exact).
-__device__ __forceinline__ unsigned lerp_biased(float ax, float ay, float b00, float b01, float b10, float b11)
-{
-    const float top = __fmaf_rn(ax, __fsub_rn(b01, b00), __fsub_rn(b00, kTwo23));
-    const float bot = __fmaf_rn(ax, __fsub_rn(b11, b10), __fsub_rn(b10, kTwo23));
-    const float v = __fmaf_rn(ay, __fsub_rn(bot, top), top);
-    return __float_as_uint(__fadd_rd(__fadd_rn(v, 0.5f), kTwo23));
 }
 
 // Plain form of the same rounding, for the gather path (v in [0, 255]).
@@ -153,6 +185,7 @@ __device__ __forceinline__ void make_job(const StreamDev *__restrict__ S, const 
     j.b0 = (bx0 * j.C) & ~15;                                  // floor to 16 bytes (bx0 may be negative)
     j.nvec = ((bx1 + 1) * j.C - j.b0 + 15) >> 4;
     j.rows = by1 - by0 + 1;
+    j.vq = 256 / j.nvec; j.vr = 256 - j.vq * j.nvec; j.vinv = (65536 + j.nvec - 1) / j.nvec;
     j.edge = !(bx0 >= 0 && by0 >= 0 && bx1 <= j.w - 1 && by1 <= j.h - 1);
     const bool fits = j.rows <= WS_ROWS && j.nvec * 16 <= WS_BYTES &&
                       ((reinterpret_cast<uintptr_t>(j.src) | (uintptr_t)j.sp) & 15) == 0;
@@ -161,71 +194,109 @@ __device__ __forceinline__ void make_job(const StreamDev *__restrict__ S, const 
 
 // Copy the job's box into sb: 16-byte chunk (r, v) holds row by0 + r, bytes
 // b0 + 16 v .. + 15; bytes outside the image come out 0 (src-size operand).
+// (256 threads; chunk e = threadIdx.x + 256 k, row = e / nvec stepped by the
+// job's precomputed quotient and remainder of 256 / nvec; tid / nvec by the
+// reciprocal, exact for tid < 256 and nvec < 256.)
 __device__ __forceinline__ void stage(const WJob &j, uint8_t *sb)
 {
-    const int n = j.rows * j.nvec, rowbytes = j.w * j.C;
-    for (int e = threadIdx.x; e < n; e += blockDim.x) {
-        const int r = e / j.nvec, v = e - r * j.nvec;
-        const int gy = j.by0 + r, gx = j.b0 + 16 * v;
+    const int nv = j.nvec, n = j.rows * nv, rowbytes = j.w * j.C, h = j.h, by0 = j.by0, b0 = j.b0, sp = j.sp;
+    const int vq = j.vq, vr = j.vr;
+    const uint8_t *src = j.src;
+    int r = (int)((threadIdx.x * (unsigned)j.vinv) >> 16), v = threadIdx.x - r * nv;
+    for (int e = threadIdx.x; e < n; e += 256) {
+        const int gy = by0 + r, gx = b0 + 16 * v;
         int valid = 0;
-        if (gy >= 0 && gy < j.h && gx >= 0) valid = min(16, max(0, rowbytes - gx));
-        const uint8_t *g = valid ? j.src + (size_t)gy * j.sp + gx : j.src;
+        if (gy >= 0 && gy < h && gx >= 0) valid = min(16, max(0, rowbytes - gx));
+        const uint8_t *g = valid ? src + (size_t)gy * sp + gx : src;
         cp_async16(sb + r * WS_BYTES + 16 * v, g, valid);
+        v += vr; r += vq;
+        if (v >= nv) { v -= nv; ++r; }
     }
 }
 
 // Resample a staged tile: thread (ty, tx) writes pixels x0 + 4 tx .. + 3 of
-// rows y0 + ty and y0 + ty + 16.
+// rows y0 + ty and y0 + ty + 16, as the pixel pairs (0, 1) and (2, 3).
 template <int C, bool EDGE>
 __device__ __forceinline__ void warp_staged(const uint8_t *__restrict__ sb, const WJob &j)
 {
-    const int x = j.x0 + (threadIdx.x & 15) * 4;
-    if (x >= j.w) return;
-    const float xf0 = (float)x, fw = (float)j.w, fh = (float)j.h;
+    const int x = j.x0 + (threadIdx.x & 15) * 4, w = j.w, h = j.h;
+    if (x >= w) return;
+    const float xf0 = (float)x, fw = (float)w, fh = (float)h;
     const int base = -j.by0 * WS_BYTES - j.b0;
+    const float m0 = j.M[0], m1 = j.M[1], m2 = j.M[2], m3 = j.M[3], m4 = j.M[4], m5 = j.M[5];
+    const f2 M0 = pk(m0, m0), M3 = pk(m3, m3), MAG = pk(kFloorMagic, kFloorMagic);
+    const f2 X01 = pk(xf0, __fadd_rn(xf0, 1.f)), X23 = pk(__fadd_rn(xf0, 2.f), __fadd_rn(xf0, 3.f));
+    uint8_t *drow = j.dst + (size_t)x * C;
 #pragma unroll 1
     for (int rr = 0; rr < 2; ++rr) {
         const int y = j.y0 + (threadIdx.x >> 4) + 16 * rr;
-        if (y >= j.h) break;
+        if (y >= h) break;
         const float yf = (float)y;
-        const float qx0 = __fmaf_rn(j.M[1], yf, j.M[2]), qy0 = __fmaf_rn(j.M[4], yf, j.M[5]);
+        const float qx0 = __fmaf_rn(m1, yf, m2), qy0 = __fmaf_rn(m4, yf, m5);
+        const f2 QX0 = pk(qx0, qx0), QY0 = pk(qy0, qy0);
         unsigned res[4 * C];
 #pragma unroll
-        for (int k = 0; k < 4; ++k) {
-            const float xf = __fadd_rn(xf0, (float)k);
-            const float qx = __fmaf_rn(j.M[0], xf, qx0), qy = __fmaf_rn(j.M[3], xf, qy0);
-            if (EDGE && !(qx > -1.0f && qx < fw && qy > -1.0f && qy < fh)) {
+        for (int pp = 0; pp < 2; ++pp) {
+            const f2 qx = fma2(M0, pp ? X23 : X01, QX0), qy = fma2(M3, pp ? X23 : X01, QY0);
+            const f2 rx = add2_rd(qx, MAG), ry = add2_rd(qy, MAG);
+            const f2 ax = sub2(qx, sub2(rx, MAG)), ay = sub2(qy, sub2(ry, MAG));
+            float q[2][2], rf[2][2];
+            upk(qx, q[0][0], q[1][0]); upk(qy, q[0][1], q[1][1]);
+            upk(rx, rf[0][0], rf[1][0]); upk(ry, rf[0][1], rf[1][1]);
+            bool ok[2];
+            int o[2];
 #pragma unroll
-                for (int c = 0; c < C; ++c) res[C * k + c] = 0u;
-                continue;
+            for (int e = 0; e < 2; ++e) {
+                ok[e] = !EDGE || (q[e][0] > -1.0f && q[e][0] < fw && q[e][1] > -1.0f && q[e][1] < fh);
+                const int xi = __float_as_int(rf[e][0]) - kFloorBits, yi = __float_as_int(rf[e][1]) - kFloorBits;
+                o[e] = ok[e] ? base + yi * WS_BYTES + xi * C : 0;   // a pixel outside reads nothing it uses
             }
-            int xi, yi;
-            const float fx = floor_exact(qx, xi), fy = floor_exact(qy, yi);
-            const float ax = __fsub_rn(qx, fx), ay = __fsub_rn(qy, fy);
-            const int o = base + yi * WS_BYTES + xi * C;   // byte offset of tap (xi, yi) in sb
             if (C == 3) {
                 // taps (xi, xi + 1) of a row: 6 bytes at o, inside words o/4 .. o/4 + 2
-                const unsigned *w0 = reinterpret_cast<const unsigned *>(sb + (o & ~3));
-                const unsigned *w1 = w0 + WS_BYTES / 4;
-                const unsigned sel = 0x3210u + (unsigned)(o & 3) * 0x1111u;
-                const unsigned a0 = __byte_perm(w0[0], w0[1], sel), a1 = __byte_perm(w0[1], w0[2], sel);
-                const unsigned c0 = __byte_perm(w1[0], w1[1], sel), c1 = __byte_perm(w1[1], w1[2], sel);
-                res[3 * k + 0] = lerp_biased(ax, ay, byte_biased<0>(a0), byte_biased<3>(a0), byte_biased<0>(c0),
-                                             byte_biased<3>(c0));
-                res[3 * k + 1] = lerp_biased(ax, ay, byte_biased<1>(a0), byte_biased<0>(a1), byte_biased<1>(c0),
-                                             byte_biased<0>(c1));
-                res[3 * k + 2] = lerp_biased(ax, ay, byte_biased<2>(a0), byte_biased<1>(a1), byte_biased<2>(c0),
-                                             byte_biased<1>(c1));
+                unsigned a0[2], a1[2], c0[2], c1[2];
+#pragma unroll
+                for (int e = 0; e < 2; ++e) {
+                    const unsigned *w0 = reinterpret_cast<const unsigned *>(sb + (o[e] & ~3));
+                    const unsigned *w1 = w0 + WS_BYTES / 4;
+                    const unsigned sel = 0x3210u + (unsigned)(o[e] & 3) * 0x1111u;
+                    a0[e] = __byte_perm(w0[0], w0[1], sel); a1[e] = __byte_perm(w0[1], w0[2], sel);
+                    c0[e] = __byte_perm(w1[0], w1[1], sel); c1[e] = __byte_perm(w1[1], w1[2], sel);
+                }
+                const f2 r0 = lerp2(ax, ay, pk(byte_biased<0>(a0[0]), byte_biased<0>(a0[1])),
+                                    pk(byte_biased<3>(a0[0]), byte_biased<3>(a0[1])),
+                                    pk(byte_biased<0>(c0[0]), byte_biased<0>(c0[1])),
+                                    pk(byte_biased<3>(c0[0]), byte_biased<3>(c0[1])));
+                const f2 r1 = lerp2(ax, ay, pk(byte_biased<1>(a0[0]), byte_biased<1>(a0[1])),
+                                    pk(byte_biased<0>(a1[0]), byte_biased<0>(a1[1])),
+                                    pk(byte_biased<1>(c0[0]), byte_biased<1>(c0[1])),
+                                    pk(byte_biased<0>(c1[0]), byte_biased<0>(c1[1])));
+                const f2 r2 = lerp2(ax, ay, pk(byte_biased<2>(a0[0]), byte_biased<2>(a0[1])),
+                                    pk(byte_biased<1>(a1[0]), byte_biased<1>(a1[1])),
+                                    pk(byte_biased<2>(c0[0]), byte_biased<2>(c0[1])),
+                                    pk(byte_biased<1>(c1[0]), byte_biased<1>(c1[1])));
+                float v[3][2];
+                upk(r0, v[0][0], v[0][1]); upk(r1, v[1][0], v[1][1]); upk(r2, v[2][0], v[2][1]);
+#pragma unroll
+                for (int e = 0; e < 2; ++e)
+#pragma unroll
+                    for (int c = 0; c < 3; ++c) res[3 * (2 * pp + e) + c] = ok[e] ? __float_as_uint(v[c][e]) : 0u;
             } else {
-                const uint8_t *r0 = sb + o, *r1 = r0 + WS_BYTES;
-                res[k] = lerp_biased(ax, ay, __uint_as_float(0x4B000000u | r0[0]), __uint_as_float(0x4B000000u | r0[1]),
-                                     __uint_as_float(0x4B000000u | r1[0]), __uint_as_float(0x4B000000u | r1[1]));
+                const uint8_t *p0 = sb + o[0], *p1 = sb + o[1];
+                const f2 r0 = lerp2(ax, ay, pk(__uint_as_float(0x4B000000u | p0[0]), __uint_as_float(0x4B000000u | p1[0])),
+                                    pk(__uint_as_float(0x4B000000u | p0[1]), __uint_as_float(0x4B000000u | p1[1])),
+                                    pk(__uint_as_float(0x4B000000u | p0[WS_BYTES]), __uint_as_float(0x4B000000u | p1[WS_BYTES])),
+                                    pk(__uint_as_float(0x4B000000u | p0[WS_BYTES + 1]),
+                                       __uint_as_float(0x4B000000u | p1[WS_BYTES + 1])));
+                float v0, v1;
+                upk(r0, v0, v1);
+                res[2 * pp] = ok[0] ? __float_as_uint(v0) : 0u;
+                res[2 * pp + 1] = ok[1] ? __float_as_uint(v1) : 0u;
             }
         }
         unsigned o[C];
 #pragma unroll
         for (int k = 0; k < C; ++k) o[k] = pack4(res[4 * k], res[4 * k + 1], res[4 * k + 2], res[4 * k + 3]);
-        store_px4<C>(j.dst + (size_t)y * j.dp + (size_t)x * C, o, min(4, j.w - x) * C);
+        store_px4<C>(drow + (size_t)y * j.dp, o, min(4, w - x) * C);
     }
 }
 
@@ -272,37 +343,37 @@ __device__ __forceinline__ void warp_direct(const WJob &j)
     }
 }
 
-__global__ void __launch_bounds__(256) k_warp(const StreamDev *__restrict__ S, WorkList wl, WarpIO io)
+__global__ void __launch_bounds__(256, 4) k_warp(const StreamDev *__restrict__ S, WorkList wl, WarpIO io)
 {
     __shared__ __align__(16) uint8_t sbox[2][WS_BUF];
-    __shared__ WJob sjob[2];   // every thread derives the same job; thread 0 publishes it for the compute
+    __shared__ WJob sjob[3];   // jobs of tiles it, it + 1, it + 2 (slot k % 3), derived by warp 0
+    const int G = gridDim.x;
     int item = blockIdx.x;
-    {
-        WJob j;
-        j.mode = 0;
-        if (item < wl.total) {
-            make_job(S, wl, io, item, j);
-            if (j.mode == 1) stage(j, sbox[0]);
-        }
-        if (threadIdx.x == 0) sjob[0] = j;
-    }
-    cp_async_commit();
-    for (int it = 0; item < wl.total; item += gridDim.x, ++it) {
-        // the next tile's box streams into the other buffer while this one is resampled
-        const int nitem = item + gridDim.x;
-        {
+    if (threadIdx.x < 32) {
+        for (int k = 0; k < 2; ++k) {
             WJob j;
             j.mode = 0;
-            if (nitem < wl.total) {
-                make_job(S, wl, io, nitem, j);
-                if (j.mode == 1) stage(j, sbox[(it + 1) & 1]);
-            }
-            if (threadIdx.x == 0) sjob[(it + 1) & 1] = j;
+            if (item + k * G < wl.total) make_job(S, wl, io, item + k * G, j);
+            if (threadIdx.x == 0) sjob[k] = j;
         }
+    }
+    __syncthreads();
+    if (sjob[0].mode == 1) stage(sjob[0], sbox[0]);
+    cp_async_commit();
+    for (int it = 0; item < wl.total; item += G, ++it) {
+        // the next tile's box streams into the other buffer while this one is resampled
+        const WJob &nxt = sjob[(it + 1) % 3];
+        if (nxt.mode == 1) stage(nxt, sbox[(it + 1) & 1]);
         cp_async_commit();
+        if (threadIdx.x < 32) {
+            WJob j;
+            j.mode = 0;
+            if (item + 2 * G < wl.total) make_job(S, wl, io, item + 2 * G, j);
+            if (threadIdx.x == 0) sjob[(it + 2) % 3] = j;
+        }
         cp_async_wait1();
         __syncthreads();
-        const WJob &cur = sjob[it & 1];
+        const WJob &cur = sjob[it % 3];
         const uint8_t *sb = sbox[it & 1];
         const int mode = cur.mode, C = cur.C;
         if (mode == 1) {
@@ -317,7 +388,7 @@ __global__ void __launch_bounds__(256) k_warp(const StreamDev *__restrict__ S, W
             if (C == 3) warp_direct<3>(cur);
             else warp_direct<1>(cur);
         }
-        __syncthreads();   // this buffer and job slot are refilled by the prefetch two tiles on
+        __syncthreads();   // this buffer and job slot are refilled two tiles on
     }
 }
 

@@ -187,7 +187,8 @@ def test_fit_parity(cfg, rigid, H):
     out = ctx.fit(_cuda(src), _cuda(dst), n, 0 if rigid else 1, 1)
     torch.cuda.synchronize()
     m = S.motions_from_raw(out.view(1, S.MOTION_WORDS))
-    assert m["flags"][0] == 0 and ref["flags"] == 0
+    assert not m["flags"][0] & S.STAB_FLAG_SKIPPED and ref["flags"] == 0
+    assert bool(m["flags"][0] & S.STAB_FLAG_RIGID) == rigid
     assert m["inliers"][0] == ref["inliers"]
     assert m["n_tracks"][0] == len(src)
     g = m["m"][0]
