@@ -4,8 +4,10 @@
 //
 // A group of WPF warps (WPF = 1 or 2, chosen by the autotuner) tracks one
 // feature.  At each level the group stages the (2r+2)^2 patch of I and of
-// (Ix, Iy) under the window into shared memory (coalesced row loads, FP32,
-// border taps replicated, so sampling is branch-free), samples the (2r+1)^2
+// (Ix, Iy) under the window into shared memory (asynchronous 8 / 16-byte
+// cp.async row copies in the planes' own precision, all of a level's copies in
+// flight together; border taps replicated, so sampling is branch-free; FP16
+// values widen exactly to FP32 when read), samples the (2r+1)^2
 // template bilinearly with weights shared by every sample, and keeps T, Tx,
 // Ty in registers (NS samples per thread).  The next frame's patch is staged
 // once per level around the initial guess with a small margin, so iterations
@@ -52,38 +54,37 @@ __device__ __forceinline__ void group_sum3(float &a, float &b, float &c, float *
 // start column (up to 3 extra leading columns, whole 4-element vectors).
 __host__ __device__ constexpr int lk_sw(int pwid) { return ((pwid + 6) / 4) * 4; }
 
-__device__ __forceinline__ float4 ld4(const float *p) { return __ldg(reinterpret_cast<const float4 *>(p)); }
-__device__ __forceinline__ float4 ld4(const __half *p)
+template <int BYTES>
+__device__ __forceinline__ void cpa(void *sdst, const void *gsrc)
 {
-    const uint2 u = __ldg(reinterpret_cast<const uint2 *>(p));
-    const float2 a = __half22float2(*reinterpret_cast<const __half2 *>(&u.x));
-    const float2 b = __half22float2(*reinterpret_cast<const __half2 *>(&u.y));
-    return make_float4(a.x, a.y, b.x, b.y);
+    const unsigned d = (unsigned)__cvta_generic_to_shared(sdst);
+    if (BYTES == 16) asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(d), "l"(gsrc) : "memory");
+    else asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(d), "l"(gsrc) : "memory");
 }
-__device__ __forceinline__ void ld4x2(const float2 *p, float4 &lo, float4 &hi)
-{
-    lo = __ldg(reinterpret_cast<const float4 *>(p));
-    hi = __ldg(reinterpret_cast<const float4 *>(p) + 1);
-}
-__device__ __forceinline__ void ld4x2(const __half2 *p, float4 &lo, float4 &hi)
-{
-    const uint4 u = __ldg(reinterpret_cast<const uint4 *>(p));
-    const float2 a = __half22float2(*reinterpret_cast<const __half2 *>(&u.x));
-    const float2 b = __half22float2(*reinterpret_cast<const __half2 *>(&u.y));
-    const float2 c = __half22float2(*reinterpret_cast<const __half2 *>(&u.z));
-    const float2 d = __half22float2(*reinterpret_cast<const __half2 *>(&u.w));
-    lo = make_float4(a.x, a.y, b.x, b.y);
-    hi = make_float4(c.x, c.y, d.x, d.y);
-}
+__device__ __forceinline__ void cpa_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
 
-// Stage the pwid x pwid patch with top-left (x0, y0) of a plane into shared
-// memory as FP32, row stride sw.  Inside the image, rows are read as aligned
-// 4-element vectors from x0 rounded down to a multiple of 4, and the returned
-// column offset (x0 - that start) locates the patch; near a border every tap
-// is clamped (replicated border) and read singly, offset 0.
-template <typename PT, int NT>
-__device__ __forceinline__ int stage1(const PT *__restrict__ P, int pitch, int wl, int hl, int x0, int y0,
-                                      int pwid, int sw, bool inside, float *dst, int tig)
+// 4 consecutive plane elements (one staged vector) by asynchronous copy.
+__device__ __forceinline__ void cpa_vec4(float *d, const float *g) { cpa<16>(d, g); }
+__device__ __forceinline__ void cpa_vec4(__half *d, const __half *g) { cpa<8>(d, g); }
+__device__ __forceinline__ void cpa_vec4(float2 *d, const float2 *g) { cpa<16>(d, g); cpa<16>(d + 2, g + 2); }
+__device__ __forceinline__ void cpa_vec4(__half2 *d, const __half2 *g) { cpa<16>(d, g); }
+
+// Plane elements read from shared memory, widened to FP32 (exact).
+__device__ __forceinline__ float f1(float v) { return v; }
+__device__ __forceinline__ float f1(__half v) { return __half2float(v); }
+__device__ __forceinline__ float2 f2(float2 v) { return v; }
+__device__ __forceinline__ float2 f2(__half2 v) { return __half22float2(v); }
+
+// Stage the pwid x pwid patch with top-left (x0, y0) of a plane (element
+// type E: the plane's own precision) into shared memory, row stride sw.
+// Inside the image, rows are copied asynchronously as aligned 4-element
+// vectors from x0 rounded down to a multiple of 4, and the returned column
+// offset (x0 - that start) locates the patch; the caller waits for the copies
+// (cpa_wait_all) before the group barrier.  Near a border every tap is
+// clamped (replicated border) and copied singly, offset 0.
+template <typename E, int NT>
+__device__ __forceinline__ int stage(const E *__restrict__ P, int pitch, int wl, int hl, int x0, int y0, int pwid,
+                                     int sw, bool inside, E *dst, int tig)
 {
     const int x0a = x0 & ~3, off = x0 - x0a;
     const int nv = (pwid + off + 3) >> 2;
@@ -91,7 +92,7 @@ __device__ __forceinline__ int stage1(const PT *__restrict__ P, int pitch, int w
         const int n = pwid * nv, q = NT / nv, rr = NT - q * nv;
         int row = tig / nv, v = tig - row * nv;
         for (int e = tig; e < n; e += NT) {
-            *reinterpret_cast<float4 *>(dst + row * sw + 4 * v) = ld4(P + (size_t)(y0 + row) * pitch + x0a + 4 * v);
+            cpa_vec4(dst + row * sw + 4 * v, P + (size_t)(y0 + row) * pitch + x0a + 4 * v);
             v += rr; row += q;
             if (v >= nv) { v -= nv; ++row; }
         }
@@ -101,38 +102,7 @@ __device__ __forceinline__ int stage1(const PT *__restrict__ P, int pitch, int w
     int row = tig / pwid, col = tig - row * pwid;
     for (int e = tig; e < n; e += NT) {
         const int xx = clampi(x0 + col, 0, wl - 1), yy = clampi(y0 + row, 0, hl - 1);
-        dst[row * sw + col] = ld1(P + (size_t)yy * pitch + xx);
-        col += rr; row += q;
-        if (col >= pwid) { col -= pwid; ++row; }
-    }
-    return 0;
-}
-
-template <typename PT2, int NT>
-__device__ __forceinline__ int stage2(const PT2 *__restrict__ P, int pitch, int wl, int hl, int x0, int y0,
-                                      int pwid, int sw, bool inside, float2 *dst, int tig)
-{
-    const int x0a = x0 & ~3, off = x0 - x0a;
-    const int nv = (pwid + off + 3) >> 2;
-    if (inside && x0a + 4 * nv <= pitch) {
-        const int n = pwid * nv, q = NT / nv, rr = NT - q * nv;
-        int row = tig / nv, v = tig - row * nv;
-        for (int e = tig; e < n; e += NT) {
-            float4 lo, hi;
-            ld4x2(P + (size_t)(y0 + row) * pitch + x0a + 4 * v, lo, hi);
-            float4 *d = reinterpret_cast<float4 *>(dst + row * sw + 4 * v);
-            d[0] = lo;
-            d[1] = hi;
-            v += rr; row += q;
-            if (v >= nv) { v -= nv; ++row; }
-        }
-        return off;
-    }
-    const int n = pwid * pwid, q = NT / pwid, rr = NT - q * pwid;
-    int row = tig / pwid, col = tig - row * pwid;
-    for (int e = tig; e < n; e += NT) {
-        const int xx = clampi(x0 + col, 0, wl - 1), yy = clampi(y0 + row, 0, hl - 1);
-        dst[row * sw + col] = ld2(P + (size_t)yy * pitch + xx);
+        dst[row * sw + col] = P[(size_t)yy * pitch + xx];
         col += rr; row += q;
         if (col >= pwid) { col -= pwid; ++row; }
     }
@@ -144,11 +114,11 @@ __device__ __forceinline__ int stage2(const PT2 *__restrict__ P, int pitch, int 
 constexpr int LK_MARGIN = 2;
 
 // Track one feature from pyramid slot sa to slot sb.  RC = compile-time
-// radius (0: runtime D.r).  sI: pw^2 floats, sG: pw^2 float2,
-// sJ: (pw + 2 LK_MARGIN)^2 floats, red: 3 * WPF.
+// radius (0: runtime D.r).  sI: pw rows of I, sG: pw rows of (Ix, Iy), sJ:
+// pw + 2 LK_MARGIN rows of the next frame's I (plane precision), red: 3 * WPF.
 template <typename PT, int NS, int RC, int WPF>
 __device__ bool lk_track(const StreamDev &D, int sa, int sb, float ux, float uy, float &vx, float &vy, int &iters,
-                         int &tpl, float *sI, float2 *sG, float *sJ, float *red, int tig, int grp)
+                         int &tpl, PT *sI, typename Plane2<PT>::type *sG, PT *sJ, float *red, int tig, int grp)
 {
     typedef typename Plane2<PT>::type PT2;
     constexpr int NT = 32 * WPF;
@@ -180,9 +150,10 @@ __device__ bool lk_track(const StreamDev &D, int sa, int sb, float ux, float uy,
         int jy0 = (int)floorf(fminf(fmaxf(py + gy, -64.f), (float)hl + 64.f)) - r - LK_MARGIN;
         bool jin = jx0 >= 0 && jx0 + pj - 1 <= wl - 1 && jy0 >= 0 && jy0 + pj - 1 <= hl - 1;
         group_sync<WPF>(grp);
-        const int offI = stage1<PT, NT>(Ia, p, wl, hl, ix, iy, pw, swI, inside, sI, tig);
-        stage2<PT2, NT>(Ga, p, wl, hl, ix, iy, pw, swI, inside, sG, tig);
-        int offJ = stage1<PT, NT>(Jb, p, wl, hl, jx0, jy0, pj, swJ, jin, sJ, tig);
+        const int offI = stage<PT, NT>(Ia, p, wl, hl, ix, iy, pw, swI, inside, sI, tig);
+        stage<PT2, NT>(Ga, p, wl, hl, ix, iy, pw, swI, inside, sG, tig);
+        int offJ = stage<PT, NT>(Jb, p, wl, hl, jx0, jy0, pj, swJ, jin, sJ, tig);
+        cpa_wait_all();
         group_sync<WPF>(grp);
         float gxx = 0.f, gxy = 0.f, gyy = 0.f;
         int i = i_l0, j = j_l0;
@@ -192,8 +163,9 @@ __device__ bool lk_track(const StreamDev &D, int sa, int sb, float ux, float uy,
             T[m] = 0.f; TX[m] = 0.f; TY[m] = 0.f;
             if (k < N) {
                 const int o = j * swI + i + offI;
-                const float t = w00 * sI[o] + w01 * sI[o + 1] + w10 * sI[o + swI] + w11 * sI[o + swI + 1];
-                const float2 g00 = sG[o], g01 = sG[o + 1], g10 = sG[o + swI], g11 = sG[o + swI + 1];
+                const float t =
+                    w00 * f1(sI[o]) + w01 * f1(sI[o + 1]) + w10 * f1(sI[o + swI]) + w11 * f1(sI[o + swI + 1]);
+                const float2 g00 = f2(sG[o]), g01 = f2(sG[o + 1]), g10 = f2(sG[o + swI]), g11 = f2(sG[o + swI + 1]);
                 const float tx = w00 * g00.x + w01 * g01.x + w10 * g10.x + w11 * g11.x;
                 const float ty = w00 * g00.y + w01 * g01.y + w10 * g10.y + w11 * g11.y;
                 T[m] = t; TX[m] = tx; TY[m] = ty;
@@ -226,12 +198,13 @@ __device__ bool lk_track(const StreamDev &D, int sa, int sb, float ux, float uy,
                 jy0 = jy - LK_MARGIN;
                 jin = jx0 >= 0 && jx0 + pj - 1 <= wl - 1 && jy0 >= 0 && jy0 + pj - 1 <= hl - 1;
                 group_sync<WPF>(grp);
-                offJ = stage1<PT, NT>(Jb, p, wl, hl, jx0, jy0, pj, swJ, jin, sJ, tig);
+                offJ = stage<PT, NT>(Jb, p, wl, hl, jx0, jy0, pj, swJ, jin, sJ, tig);
+                cpa_wait_all();
                 group_sync<WPF>(grp);
                 ox = LK_MARGIN;
                 oy = LK_MARGIN;
             }
-            const float *sJo = sJ + oy * swJ + ox + offJ;
+            const PT *sJo = sJ + oy * swJ + ox + offJ;
             float bxs = 0.f, bys = 0.f, unused = 0.f;
             int i2 = i_l0, j2 = j_l0;
 #pragma unroll
@@ -239,7 +212,8 @@ __device__ bool lk_track(const StreamDev &D, int sa, int sb, float ux, float uy,
                 const int k = tig + NT * m;
                 if (k < N) {
                     const int o = j2 * swJ + i2;
-                    const float jv = v00 * sJo[o] + v01 * sJo[o + 1] + v10 * sJo[o + swJ] + v11 * sJo[o + swJ + 1];
+                    const float jv = v00 * f1(sJo[o]) + v01 * f1(sJo[o + 1]) + v10 * f1(sJo[o + swJ]) +
+                                     v11 * f1(sJo[o + swJ + 1]);
                     const float e = T[m] - jv;
                     bxs += e * TX[m];
                     bys += e * TY[m];
@@ -262,27 +236,32 @@ __device__ bool lk_track(const StreamDev &D, int sa, int sb, float ux, float uy,
     return vx >= 0.f && vx <= (float)(D.w - 1) && vy >= 0.f && vy <= (float)(D.h - 1);
 }
 
-// Shared memory per feature group: the template's FP32 and float2 patches
-// ((2r+2) rows of stride lk_sw(2r+2)), the next frame's patch ((2r+2+2 margin)
-// rows of stride lk_sw(2r+2+2 margin)) and the reduction slots.
-__host__ __device__ constexpr int lk_group_floats(int r)
+// Shared memory per feature group, in bytes, for plane element size es
+// (4: FP32, 2: FP16): the template's I and (Ix, Iy) patches ((2r+2) rows of
+// stride lk_sw(2r+2)), the next frame's patch ((2r+2+2 margin) rows of stride
+// lk_sw(2r+2+2 margin)) and 8 reduction floats; each region 16-byte aligned.
+__host__ __device__ constexpr int lk_al16(int b) { return (b + 15) & ~15; }
+__host__ __device__ constexpr int lk_bytes_I(int r, int es) { return lk_al16((2 * r + 2) * lk_sw(2 * r + 2) * es); }
+__host__ __device__ constexpr int lk_bytes_J(int r, int es)
 {
-    return 3 * (2 * r + 2) * lk_sw(2 * r + 2) + (2 * r + 2 + 2 * LK_MARGIN) * lk_sw(2 * r + 2 + 2 * LK_MARGIN) + 8;
+    return lk_al16((2 * r + 2 + 2 * LK_MARGIN) * lk_sw(2 * r + 2 + 2 * LK_MARGIN) * es);
 }
+__host__ __device__ constexpr int lk_group_bytes(int r, int es) { return 3 * lk_bytes_I(r, es) + lk_bytes_J(r, es) + 32; }
 
 template <typename PT, int NS, int RC, int WPF, int MINB>
 __global__ void __launch_bounds__(128, MINB) k_lk(const StreamDev *__restrict__ S, WorkList wl, LkIO io, int rmax)
 {
-    extern __shared__ float lk_smem[];
-    constexpr int NT = 32 * WPF;
+    typedef typename Plane2<PT>::type PT2;
+    extern __shared__ __align__(16) unsigned char lk_smem[];
+    constexpr int NT = 32 * WPF, ES = (int)sizeof(PT);
     const int grp = threadIdx.x / NT, tig = threadIdx.x - grp * NT;
-    float *base = lk_smem + grp * lk_group_floats(rmax);
+    unsigned char *base = lk_smem + grp * lk_group_bytes(rmax, ES);
     // regions sized for rmax; a stream with a smaller radius uses a prefix
-    const int tI = (2 * rmax + 2) * lk_sw(2 * rmax + 2);
-    float *sI = base;
-    float2 *sG = reinterpret_cast<float2 *>(base + tI);
-    float *sJ = base + 3 * tI;
-    float *red = sJ + (2 * rmax + 2 + 2 * LK_MARGIN) * lk_sw(2 * rmax + 2 + 2 * LK_MARGIN);
+    const int bI = lk_bytes_I(rmax, ES);
+    PT *sI = reinterpret_cast<PT *>(base);
+    PT2 *sG = reinterpret_cast<PT2 *>(base + bI);
+    PT *sJ = reinterpret_cast<PT *>(base + 3 * bI);
+    float *red = reinterpret_cast<float *>(base + 3 * bI + lk_bytes_J(rmax, ES));
     const int ngroups = (gridDim.x * blockDim.x) / NT;
     for (int item = (blockIdx.x * blockDim.x + threadIdx.x) / NT; item < wl.total; item += ngroups) {
         const int s = wl_stream(wl, item);
@@ -327,7 +306,7 @@ __global__ void __launch_bounds__(128, MINB) k_lk(const StreamDev *__restrict__ 
 
 template <typename PT, int NS, int RC, int WPF, int MINB>
 struct LkKernel {
-    static int smem(int rmax) { return (128 / (32 * WPF)) * lk_group_floats(rmax) * 4; }
+    static int smem(int rmax) { return (128 / (32 * WPF)) * lk_group_bytes(rmax, (int)sizeof(PT)); }
     static int occ(int rmax)
     {
         static int v[STAB_MAXR + 1] = {0};
