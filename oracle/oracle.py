@@ -90,6 +90,10 @@ def _declare(L):
     L.or_fit.restype = C.c_int
     L.or_ls_similarity.argtypes = [_f64p, _f64p, C.c_int, C.c_int, _f64p]
     L.or_smooth.argtypes = [_f64p, C.c_int, C.c_int, _f64p, _f64p, _f64p]
+    L.or_sample_triple.argtypes = [C.c_uint64, C.c_int, C.c_int, C.c_int, _i32p, _i32p, _i32p]
+    L.or_fit_affine.argtypes = [_f32p, _f32p, C.c_int, C.c_int, C.c_int, C.c_int, C.c_uint64, C.c_int, C.c_float,
+                                C.c_int, _f64p, _i32p, _f64p, _u8p, _i32p]
+    L.or_fit_affine.restype = C.c_int
     L.or_warp_inverse.argtypes = [_f64p, C.c_int, C.c_int, C.c_double, _f32p]
     L.or_warp.argtypes = [_u8p, C.c_int, C.c_int, C.c_int, C.c_int, _f32p, _u8p, C.c_int]
     L.or_charb.argtypes = [_f32p, _f32p, C.c_int, C.c_int, C.c_int, _f64p, C.c_double, _f64p, _f64p, _f64p,
@@ -221,6 +225,26 @@ def fit(src, dst, w, h, rigid: bool, H: int, seed: int, t: int, tau: float = 1.0
     mask = np.zeros(max(n, 1), np.uint8)
     ni = lib().or_fit(_p(src, _f32p), _p(dst, _f32p), n, w, h, int(rigid), H, C.c_uint64(seed), t, tau,
                       min_pts, _p(out, _f64p), _p(bh, _i32p), _p(rms, _f64p), _p(mask, _u8p), _p(fl, _i32p))
+    return dict(m=out, inliers=int(ni), best_h=int(bh[0]), rms=float(rms[0]), mask=mask[:n].astype(bool),
+                flags=int(fl[0]))
+
+
+def sample_triple(seed: int, t: int, h: int, n: int):
+    i = np.zeros(1, np.int32); j = np.zeros(1, np.int32); k = np.zeros(1, np.int32)
+    lib().or_sample_triple(C.c_uint64(seed), t, h, n, _p(i, _i32p), _p(j, _i32p), _p(k, _i32p))
+    return int(i[0]), int(j[0]), int(k[0])
+
+
+def fit_affine(src, dst, w, h, H: int, seed: int, t: int, tau: float = 1.0, min_pts: int = 10) -> dict:
+    """Robust 6-DOF affine fit (Eq. 7-8); A = m[:4] row-major, t = m[4:],
+    centred coordinates."""
+    src = _c(src, np.float32).reshape(-1, 2)
+    dst = _c(dst, np.float32).reshape(-1, 2)
+    n = src.shape[0]
+    out = np.zeros(6); bh = np.zeros(1, np.int32); rms = np.zeros(1); fl = np.zeros(1, np.int32)
+    mask = np.zeros(max(n, 1), np.uint8)
+    ni = lib().or_fit_affine(_p(src, _f32p), _p(dst, _f32p), n, w, h, H, C.c_uint64(seed), t, tau, min_pts,
+                             _p(out, _f64p), _p(bh, _i32p), _p(rms, _f64p), _p(mask, _u8p), _p(fl, _i32p))
     return dict(m=out, inliers=int(ni), best_h=int(bh[0]), rms=float(rms[0]), mask=mask[:n].astype(bool),
                 flags=int(fl[0]))
 

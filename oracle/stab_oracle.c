@@ -477,6 +477,137 @@ int or_fit(const float *src, const float *dst, int n, int w, int h, int rigid, i
     return ni;
 }
 
+/* ------------------------------------------------------------------------ */
+/* Full 6-degree-of-freedom affine model of Eq. 7-8: d = A s + t with a 2x2
+ * matrix A, fitted like the 3/4-DOF models (hypotheses from minimal samples,
+ * inlier count, closed-form least squares on the winner's inliers).  Eq. 8
+ * needs three non-degenerate pairs for the six unknowns.
+ *
+ * Sample triple of hypothesis h: i and j as for the pair, k = r2 mod (n-2)
+ * stepped past the smaller and then the larger of i, j (uniform over the
+ * remaining points). */
+void or_sample_triple(uint64_t seed, int t, int h, int n, int *i, int *j, int *k)
+{
+    uint64_t base = seed ^ ((uint64_t)(uint32_t)t << 32) ^ ((uint64_t)(uint32_t)h << 8);
+    uint64_t r2 = or_splitmix64(base ^ 2ULL);
+    or_sample_pair(seed, t, h, n, i, j);
+    int lo = *i < *j ? *i : *j, hi = *i < *j ? *j : *i;
+    int c = (int)(r2 % (uint64_t)(n - 2));
+    if (c >= lo) c += 1;
+    if (c >= hi) c += 1;
+    *k = c;
+}
+
+/* Exact affine map through three pairs (centred coordinates) in the FP32
+ * operation order both sides use: with u1 = sj - si, u2 = sk - si,
+ * v1 = dj - di, v2 = dk - di, A [u1 u2] = [v1 v2], so A = [v1 v2] adj / det
+ * (det = u1 x u2) and t = di - A si.  Degenerate when |det| < 1 px^2 (twice the
+ * triangle's area).  m = (a00, a01, a10, a11, tx, ty). */
+static int three_point(const float *si, const float *sj, const float *sk, const float *di, const float *dj,
+                       const float *dk, float m[6])
+{
+    float u1x = sj[0] - si[0], u1y = sj[1] - si[1], u2x = sk[0] - si[0], u2y = sk[1] - si[1];
+    float v1x = dj[0] - di[0], v1y = dj[1] - di[1], v2x = dk[0] - di[0], v2y = dk[1] - di[1];
+    float det = fmaf(u1x, u2y, -(u1y * u2x));
+    if (!(fabsf(det) >= 1.0f)) return 0;
+    m[0] = fmaf(v1x, u2y, -(v2x * u1y)) / det;
+    m[1] = fmaf(v2x, u1x, -(v1x * u2x)) / det;
+    m[2] = fmaf(v1y, u2y, -(v2y * u1y)) / det;
+    m[3] = fmaf(v2y, u1x, -(v1y * u2x)) / det;
+    m[4] = di[0] - fmaf(m[0], si[0], m[1] * si[1]);
+    m[5] = di[1] - fmaf(m[2], si[0], m[3] * si[1]);
+    return 1;
+}
+
+static int is_inlier_affine(const float m[6], const float *s, const float *d, float tau2)
+{
+    float px = fmaf(m[0], s[0], fmaf(m[1], s[1], m[4]));
+    float py = fmaf(m[2], s[0], fmaf(m[3], s[1], m[5]));
+    float ex = d[0] - px, ey = d[1] - py;
+    return fmaf(ex, ex, ey * ey) < tau2;
+}
+
+/* Robust affine fit.  Arguments as or_fit; out = (a00, a01, a10, a11, tx, ty)
+ * in centred coordinates.  Least squares of Eq. 7 on the inliers (FP64): with
+ * centred x = s - mean(s), y = d - mean(d), Sxx = sum x x^T, Syx = sum y x^T,
+ * A = Syx Sxx^-1 and t = mean(d) - A mean(s); skipped when Sxx is singular. */
+int or_fit_affine(const float *src, const float *dst, int n, int w, int h, int H, uint64_t seed, int t, float tau,
+                  int min_pts, double out[6], int *best_h, double *rms, uint8_t *inlier_mask, int *flags)
+{
+    float cx = 0.5f * (float)(w - 1), cy = 0.5f * (float)(h - 1);
+    for (int k = 0; k < 6; ++k) out[k] = 0.0;
+    out[0] = out[3] = 1.0;
+    *best_h = -1; *rms = 0.0; *flags = 0;
+    if (inlier_mask) memset(inlier_mask, 0, (size_t)(n > 0 ? n : 0));
+    int need = min_pts > 3 ? min_pts : 3;
+    if (n < need) { *flags = 1; return 0; }
+    float *s = (float *)malloc(sizeof(float) * 4 * (size_t)n), *d = s + 2 * n;
+    for (int k = 0; k < n; ++k) {
+        s[2 * k] = src[2 * k] - cx; s[2 * k + 1] = src[2 * k + 1] - cy;
+        d[2 * k] = dst[2 * k] - cx; d[2 * k + 1] = dst[2 * k + 1] - cy;
+    }
+    float tau2 = tau * tau;
+    int best = -1, best_score = -1;
+    float bm[6] = {0, 0, 0, 0, 0, 0};
+    for (int hh = 0; hh < H; ++hh) {
+        int i, j, kk;
+        float m[6];
+        or_sample_triple(seed, t, hh, n, &i, &j, &kk);
+        if (!three_point(&s[2 * i], &s[2 * j], &s[2 * kk], &d[2 * i], &d[2 * j], &d[2 * kk], m)) continue;
+        int score = 0;
+        for (int k = 0; k < n; ++k) score += is_inlier_affine(m, &s[2 * k], &d[2 * k], tau2);
+        if (score > best_score) { best_score = score; best = hh; memcpy(bm, m, sizeof(bm)); }
+    }
+    if (best < 0 || best_score < 3) { free(s); *flags = 1; return 0; }
+    *best_h = best;
+    double mus[2] = {0, 0}, mud[2] = {0, 0};
+    int ni = 0;
+    for (int k = 0; k < n; ++k)
+        if (is_inlier_affine(bm, &s[2 * k], &d[2 * k], tau2)) {
+            if (inlier_mask) inlier_mask[k] = 1;
+            mus[0] += s[2 * k]; mus[1] += s[2 * k + 1];
+            mud[0] += d[2 * k]; mud[1] += d[2 * k + 1];
+            ++ni;
+        }
+    mus[0] /= ni; mus[1] /= ni; mud[0] /= ni; mud[1] /= ni;
+    double Sxx[2][2] = {{0, 0}, {0, 0}}, Syx[2][2] = {{0, 0}, {0, 0}};
+    for (int k = 0; k < n; ++k)
+        if (is_inlier_affine(bm, &s[2 * k], &d[2 * k], tau2)) {
+            double x[2] = {s[2 * k] - mus[0], s[2 * k + 1] - mus[1]};
+            double y[2] = {d[2 * k] - mud[0], d[2 * k + 1] - mud[1]};
+            for (int r = 0; r < 2; ++r)
+                for (int c = 0; c < 2; ++c) {
+                    Sxx[r][c] += x[r] * x[c];
+                    Syx[r][c] += y[r] * x[c];
+                }
+        }
+    double D = Sxx[0][0] * Sxx[1][1] - Sxx[0][1] * Sxx[1][0];
+    if (!(D > 0.0)) {
+        free(s); *flags = 1; *best_h = -1;
+        if (inlier_mask) memset(inlier_mask, 0, (size_t)n);
+        for (int k = 0; k < 6; ++k) out[k] = 0.0;
+        out[0] = out[3] = 1.0;
+        return 0;
+    }
+    double inv[2][2] = {{Sxx[1][1] / D, -Sxx[0][1] / D}, {-Sxx[1][0] / D, Sxx[0][0] / D}};
+    double A[2][2];
+    for (int r = 0; r < 2; ++r)
+        for (int c = 0; c < 2; ++c) A[r][c] = Syx[r][0] * inv[0][c] + Syx[r][1] * inv[1][c];
+    double tx = mud[0] - (A[0][0] * mus[0] + A[0][1] * mus[1]);
+    double ty = mud[1] - (A[1][0] * mus[0] + A[1][1] * mus[1]);
+    double e2 = 0;
+    for (int k = 0; k < n; ++k)
+        if (is_inlier_affine(bm, &s[2 * k], &d[2 * k], tau2)) {
+            double px = A[0][0] * s[2 * k] + A[0][1] * s[2 * k + 1] + tx;
+            double py = A[1][0] * s[2 * k] + A[1][1] * s[2 * k + 1] + ty;
+            e2 += (d[2 * k] - px) * (d[2 * k] - px) + (d[2 * k + 1] - py) * (d[2 * k + 1] - py);
+        }
+    *rms = sqrt(e2 / ni);
+    out[0] = A[0][0]; out[1] = A[0][1]; out[2] = A[1][0]; out[3] = A[1][1]; out[4] = tx; out[5] = ty;
+    free(s);
+    return ni;
+}
+
 /* Closed-form least squares of Eq. 7 restricted to a similarity or rigid
  * model, on all n given pairs (centred coordinates; FP64).  Used for pins. */
 void or_ls_similarity(const double *src, const double *dst, int n, int rigid, double out[4])

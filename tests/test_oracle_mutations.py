@@ -48,6 +48,12 @@ MUTATIONS = [
     ("crop composed before the compensation", "P[i][j] += W[i][k] * Zi[k][j];", "P[i][j] += Zi[i][k] * W[k][j];"),
     ("crop zoom about the origin", "double Zi[3][3] = {{iz, 0, cx - iz * cx}, {0, iz, cy - iz * cy}, {0, 0, 1}};",
      "double Zi[3][3] = {{iz, 0, 0}, {0, iz, 0}, {0, 0, 1}};"),
+    ("affine determinant sign", "float det = fmaf(u1x, u2y, -(u1y * u2x));", "float det = fmaf(u1x, u2y, (u1y * u2x));"),
+    ("affine minimal solve column swap", "m[1] = fmaf(v2x, u1x, -(v1x * u2x)) / det;", "m[1] = fmaf(v1x, u1x, -(v2x * u2x)) / det;"),
+    ("affine third index skip order", "    if (c >= lo) c += 1;\n    if (c >= hi) c += 1;", "    if (c >= hi) c += 1;\n    if (c >= lo) c += 1;"),
+    ("affine normal equations transposed", "Syx[r][c] += y[r] * x[c];", "Syx[r][c] += y[c] * x[r];"),
+    ("affine translation from the source mean", "double ty = mud[1] - (A[1][0] * mus[0] + A[1][1] * mus[1]);",
+     "double ty = mud[1] - (A[1][0] * mus[0] + A[1][1] * mud[1]);"),
     ("adjoint image weight", "double wt[4] = {(1 - ax) * (1 - ay), ax * (1 - ay), (1 - ax) * ay, ax * ay};", "double wt[4] = {(1 - ax) * (1 - ay), (1 - ax) * ay, ax * (1 - ay), ax * ay};"),
 ]
 
@@ -85,6 +91,9 @@ PINS = [
     (P.test_hybrid_prefers_rigid_when_similarity_buys_inliers_with_error, {}),
     (P.test_crop_zoom_is_a_zoom_about_the_centre, {}), (P.test_crop_zoom_composes_after_the_compensation, {}),
     (P.test_crop_zoom_of_linear_ramp, {}), (P.test_crop_zoom_hides_the_unfilled_border, {}),
+    (P.test_sample_triples_distinct_and_uniform, {}), (P.test_affine_exact_pairs_recovered, {}),
+    (P.test_affine_refit_is_least_squares_on_inliers, {}), (P.test_affine_of_a_similarity_is_the_similarity, {}),
+    (P.test_affine_collinear_points_are_skipped, {}),
     (P.test_hybrid_transitions_on_scripted_pairs, {}), (P.test_hybrid_dwell_schedule_and_bookkeeping, {}),
 ]
 

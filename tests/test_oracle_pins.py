@@ -701,3 +701,75 @@ def test_crop_zoom_hides_the_unfilled_border():
     q = corners @ M[:, :2].T + M[:, 2]
     assert (q >= 0).all() and (q[:, 0] <= w - 1).all() and (q[:, 1] <= h - 1).all()
     assert (O.warp(img, M.reshape(-1).astype(np.float32)) == 200).all()
+
+
+# --------------------------------------------- 6-DOF affine fit (Eq. 7-8) --
+def _affine_pairs(seed, n=60, noise=0.0, outliers=0):
+    rng = np.random.default_rng(seed)
+    w, h = 320, 240
+    c = np.array([(w - 1) / 2, (h - 1) / 2])
+    A = np.array([[1.02, 0.03], [-0.01, 0.97]]) + rng.normal(0, 0.01, (2, 2))
+    t = rng.normal(0, 3, 2)
+    src = rng.uniform([10, 10], [w - 10, h - 10], (n, 2))
+    dst = (src - c) @ A.T + t + c + rng.normal(0, noise, (n, 2))
+    bad = rng.choice(n, outliers, replace=False)
+    dst[bad] += rng.uniform(5, 20, (outliers, 2)) * rng.choice([-1, 1], (outliers, 2))
+    return src.astype(np.float32), dst.astype(np.float32), A, t, bad, w, h
+
+
+def test_sample_triples_distinct_and_uniform():
+    n = 5
+    seen = {}
+    for h in range(6000):
+        i, j, k = O.sample_triple(11, 3, h, n)
+        assert len({i, j, k}) == 3 and max(i, j, k) < n and min(i, j, k) >= 0
+        assert (i, j) == O.sample_pair(11, 3, h, n)          # the first two are the pair sample
+        seen[(i, j, k)] = seen.get((i, j, k), 0) + 1
+    assert len(seen) == n * (n - 1) * (n - 2)               # every ordered triple occurs
+    counts = np.array(list(seen.values()))
+    assert counts.min() > 0.6 * counts.mean() and counts.max() < 1.4 * counts.mean()
+
+
+def test_affine_exact_pairs_recovered():
+    src, dst, A, t, _, w, h = _affine_pairs(81)
+    f = O.fit_affine(src, dst, w, h, 50, 0, 1)
+    assert f["flags"] == 0 and f["inliers"] == len(src) and f["rms"] < 1e-4
+    assert np.abs(f["m"][:4] - A.reshape(-1)).max() < 1e-5     # FP32 inputs
+    assert np.abs(f["m"][4:] - t).max() < 1e-3
+
+
+def test_affine_refit_is_least_squares_on_inliers():
+    src, dst, A, t, bad, w, h = _affine_pairs(82, n=80, noise=0.2, outliers=16)
+    f = O.fit_affine(src, dst, w, h, 200, 3, 1)
+    mask = f["mask"]
+    assert not mask[bad].any() and mask.sum() >= 80 - 16 - 2  # outliers out; a 1 px gate may drop a tail sample
+    c = np.array([(w - 1) / 2, (h - 1) / 2], np.float32)     # the fit centres its FP32 inputs in FP32
+    X = np.c_[(src[mask] - c).astype(np.float64), np.ones(mask.sum())]
+    Y = (dst[mask] - c).astype(np.float64)
+    sol, *_ = np.linalg.lstsq(X, Y, rcond=None)               # rows: [A^T; t]
+    assert np.abs(f["m"][:4] - sol[:2].T.reshape(-1)).max() < 1e-9
+    assert np.abs(f["m"][4:] - sol[2]).max() < 1e-7
+    resid = Y - X @ sol
+    assert abs(f["rms"] - math.sqrt((resid ** 2).sum(1).mean())) < 1e-9
+
+
+def test_affine_of_a_similarity_is_the_similarity():
+    rng = np.random.default_rng(83)
+    w, h = 320, 240
+    c = np.array([(w - 1) / 2, (h - 1) / 2])
+    th, s, t = 0.03, 1.015, np.array([2.5, -1.5])
+    R = s * np.array([[math.cos(th), -math.sin(th)], [math.sin(th), math.cos(th)]])
+    src = rng.uniform(10, 230, (50, 2)).astype(np.float32)
+    dst = ((src - c) @ R.T + t + c).astype(np.float32)
+    fa = O.fit_affine(src, dst, w, h, 50, 0, 1)
+    fs = O.fit(src, dst, w, h, False, 50, 0, 1)
+    a, b = math.exp(fs["m"][3]) * math.cos(fs["m"][2]), math.exp(fs["m"][3]) * math.sin(fs["m"][2])
+    assert np.abs(fa["m"][:4] - [a, -b, b, a]).max() < 1e-6
+    assert np.abs(fa["m"][4:] - fs["m"][:2]).max() < 1e-4
+
+
+def test_affine_collinear_points_are_skipped():
+    x = np.linspace(20, 300, 40)
+    src = np.stack([x, 0.5 * x + 10], 1).astype(np.float32)
+    f = O.fit_affine(src, src + 1, 320, 240, 100, 0, 1)
+    assert f["flags"] == 1 and np.array_equal(f["m"], [1, 0, 0, 1, 0, 0])
