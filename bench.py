@@ -223,6 +223,7 @@ def run_ours(args):
 
     mixed = run_mixed(S, dev, args.mixed_steps, args.warmup) if args.mixed_steps > 0 else None
     gn = run_gn(S, dev, args.gn_pairs) if args.gn_pairs > 0 else None
+    fits = run_fits(S, dev, args.fit_reps) if args.fit_reps > 0 else None
 
     out = {"metric": METRIC, "value": round(value, 1), "unit": "frames/s", "n_gpus": ws, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": round(total_ms / args.steps, 4), "higher_is_better": True,
@@ -232,7 +233,7 @@ def run_ours(args):
            "plain": plain, "e2e": e2e, "roofline": roof,
            "kernels_ms": {k: round(v, 4) for k, v in kavg.items()},
            "gpu_launches": n_k * args.steps, "clocks": clk, "wall_s": round(wall, 3), "autotune": tuned,
-           "mixed_64_streams": mixed, "photometric_gn": gn}
+           "mixed_64_streams": mixed, "photometric_gn": gn, "fits": fits}
     if ws == 1 and rank == 0 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(clips[0].cpu().numpy(), args.cpu_frames)
     if rank == 0:
@@ -492,6 +493,46 @@ def run_gn(S, dev, pairs, steps_gn=10):
             "err_unit": "px at the image corner (translation + radius x angle / log-scale error)"}
 
 
+def run_fits(S, dev, reps):
+    """Latency of one robust fit call on 1000 pairs of a 1920x1080 frame (0.3 px
+    jitter, 5 % outliers, 100 hypotheses): similarity, a hybrid decision
+    transition (both models fitted and compared), and the 6-DOF affine fit."""
+    import numpy as np
+    import torch
+    w, h, n = 1920, 1080, 1000
+    rng = np.random.default_rng(77)
+    c = np.array([(w - 1) / 2, (h - 1) / 2])
+    th, sc = 0.004, 1.002
+    R = sc * np.array([[math.cos(th), -math.sin(th)], [math.sin(th), math.cos(th)]])
+    src = rng.uniform([40, 40], [w - 40, h - 40], (n, 2))
+    dst = (src - c) @ R.T + np.array([1.7, -0.9]) + c + rng.normal(0, 0.3, (n, 2))
+    bad = rng.choice(n, n // 20, replace=False)
+    dst[bad] += rng.uniform(5, 30, (len(bad), 2))
+    srcd = torch.as_tensor(src.astype(np.float32), device=dev)
+    dstd = torch.as_tensor(dst.astype(np.float32), device=dev)
+    nd = torch.tensor([n], dtype=torch.int32, device=dev)
+    ctx = S.Context(w, h, S.default_params(max_corners=n, hypotheses=100, model=S.STAB_HYBRID))
+    out = torch.zeros(max(S.MOTION_WORDS, S.AFFINE_WORDS), dtype=torch.float32, device=dev)
+    calls = {"similarity_us": lambda: ctx.fit(srcd, dstd, nd, S.STAB_SIMILARITY, 1, out=out),
+             "hybrid_decision_us": lambda: ctx.fit(srcd, dstd, nd, S.STAB_HYBRID, 1, out=out),
+             "affine_us": lambda: ctx.fit_affine(srcd, dstd, nd, 1, out=out)}
+    res = {"pairs": n, "hypotheses": 100, "outliers": len(bad), "calls": reps}
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    for name, fn in calls.items():
+        for _ in range(5):
+            fn()
+        torch.cuda.synchronize()
+        e0.record()
+        for _ in range(reps):
+            fn()
+        e1.record()
+        torch.cuda.synchronize()
+        res[name] = round(e0.elapsed_time(e1) * 1e3 / reps, 2)
+    assert ctx.sync() == 0
+    return res
+
+
 # ---------------------------------------------------- oracle (CPU) timing --
 def oracle_stream(frames, n_frames, warm=0):
     """Time the oracle frame by frame on one 1080p RGB stream (the same per-
@@ -576,6 +617,7 @@ def main():
     ap.add_argument("--cpu-frames", type=int, default=8)
     ap.add_argument("--mixed-steps", type=int, default=30, help="steps of the 64-stream mixed batch (0 = skip)")
     ap.add_argument("--gn-pairs", type=int, default=256, help="frame pairs of the photometric refinement (0 = skip)")
+    ap.add_argument("--fit-reps", type=int, default=200, help="timed calls per fit model (0 = skip)")
     ap.add_argument("--clips", type=int, default=4, help="distinct seeded clips shared round-robin by the streams")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-autotune", action="store_true")

@@ -97,6 +97,16 @@ typedef struct {
     float e_similarity;              /* RMS of the similarity fit made at this transition, -1 if none */
 } stab_motion;
 
+/* Result of the 6-DOF affine fit (Eq. 7-8): dst = A src + t in centred
+ * coordinates (pixel minus ((w-1)/2, (h-1)/2)), A = [a00 a01; a10 a11]. */
+typedef struct {
+    float a00, a01, a10, a11, tx, ty;
+    int inliers;                     /* inliers of the refit */
+    int n_tracks;                    /* pairs given */
+    float rms;                       /* RMS residual of the refit over its inliers (px) */
+    int flags;                       /* STAB_FLAG_SKIPPED when no fit: identity */
+} stab_affine;
+
 typedef struct stab_ctx stab_ctx;
 typedef struct stab_batch stab_batch;
 
@@ -204,6 +214,20 @@ stab_status stab_track(stab_ctx *ctx, const uint8_t *prev_dev, const uint8_t *ne
  * the other transitions. */
 stab_status stab_fit(stab_ctx *ctx, const float *src_dev, const float *dst_dev, const int *n_dev, int model,
                      int t, stab_motion *out_dev, void *stream);
+
+/* Robust 6-DOF affine fit (Eq. 7-8: [A|t] minimising the squared distances
+ * of the inliers; three non-degenerate pairs determine it): `hypotheses`
+ * three-point samples (hypothesis h: the pair sample of h plus a third index
+ * k = r2 mod (n-2) stepped past the two, r2 the SplitMix64 value of
+ * (seed ^ t << 32 ^ h << 8) ^ 2), each solved exactly in a fixed FP32 order
+ * (degenerate when twice the triangle area is below 1 px^2) and scored by
+ * inlier count (residual < inlier_thresh); the first best is refitted by the
+ * closed-form least squares of Eq. 7 on its inliers.  src/dst: device points,
+ * count from *n_dev (device); fewer than max(3, min_fit) pairs, no valid
+ * sample or collinear inliers => identity with STAB_FLAG_SKIPPED.  Writes one
+ * stab_affine to out_dev (device). */
+stab_status stab_fit_affine(stab_ctx *ctx, const float *src_dev, const float *dst_dev, const int *n_dev, int t,
+                            stab_affine *out_dev, void *stream);
 
 /* Offline averaging-window smoothing (Sec. 5.1) of T motions (frame 0's
  * motion must be the identity): C_t = sum_{k<=t} m_k, S_t = mean of C over

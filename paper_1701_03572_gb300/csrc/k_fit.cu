@@ -348,6 +348,133 @@ __global__ void __launch_bounds__(512) k_fit(const StreamDev *__restrict__ S, Fi
     }
 }
 
+// ---------------------------------------------------------------------------
+// 6-DOF affine fit (Eq. 7-8): three-point hypotheses, the same scoring, and
+// the least squares of Eq. 7 on the winner's inliers.
+__device__ __forceinline__ void sample_triple(unsigned long long seed, long long t, int h, int n, int &i, int &j,
+                                              int &k)
+{
+    unsigned long long base = seed ^ ((unsigned long long)(unsigned)t << 32) ^ ((unsigned long long)(unsigned)h << 8);
+    sample_pair(seed, t, h, n, i, j);
+    const int lo = min(i, j), hi = max(i, j);
+    int c = (int)(splitmix64(base ^ 2ull) % (unsigned long long)(n - 2));
+    if (c >= lo) ++c;
+    if (c >= hi) ++c;
+    k = c;
+}
+
+// A [u1 u2] = [v1 v2] through three pairs; m = (a00, a01, a10, a11, tx, ty).
+__device__ __forceinline__ bool three_point(float2 si, float2 sj, float2 sk, float2 di, float2 dj, float2 dk, float m[6])
+{
+    const float u1x = __fsub_rn(sj.x, si.x), u1y = __fsub_rn(sj.y, si.y);
+    const float u2x = __fsub_rn(sk.x, si.x), u2y = __fsub_rn(sk.y, si.y);
+    const float v1x = __fsub_rn(dj.x, di.x), v1y = __fsub_rn(dj.y, di.y);
+    const float v2x = __fsub_rn(dk.x, di.x), v2y = __fsub_rn(dk.y, di.y);
+    const float det = __fmaf_rn(u1x, u2y, -__fmul_rn(u1y, u2x));
+    if (!(fabsf(det) >= 1.0f)) return false;
+    m[0] = __fdiv_rn(__fmaf_rn(v1x, u2y, -__fmul_rn(v2x, u1y)), det);
+    m[1] = __fdiv_rn(__fmaf_rn(v2x, u1x, -__fmul_rn(v1x, u2x)), det);
+    m[2] = __fdiv_rn(__fmaf_rn(v1y, u2y, -__fmul_rn(v2y, u1y)), det);
+    m[3] = __fdiv_rn(__fmaf_rn(v2y, u1x, -__fmul_rn(v1y, u2x)), det);
+    m[4] = __fsub_rn(di.x, __fmaf_rn(m[0], si.x, __fmul_rn(m[1], si.y)));
+    m[5] = __fsub_rn(di.y, __fmaf_rn(m[2], si.x, __fmul_rn(m[3], si.y)));
+    return true;
+}
+
+__device__ __forceinline__ bool is_inlier_affine(const float m[6], float2 s, float2 d, float tau2)
+{
+    const float px = __fmaf_rn(m[0], s.x, __fmaf_rn(m[1], s.y, m[4]));
+    const float py = __fmaf_rn(m[2], s.x, __fmaf_rn(m[3], s.y, m[5]));
+    const float ex = __fsub_rn(d.x, px), ey = __fsub_rn(d.y, py);
+    return __fmaf_rn(ex, ex, __fmul_rn(ey, ey)) < tau2;
+}
+
+__global__ void __launch_bounds__(512) k_fit_affine(const StreamDev *__restrict__ S, AffineIO io)
+{
+    __shared__ float2 ss[STAB_MAXK], sd[STAB_MAXK];
+    __shared__ int wbs[16], wbh[16], s_best, s_bh;
+    __shared__ float red[16][8];
+    const StreamDev &D = S[0];
+    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5, nwarps = blockDim.x >> 5;
+    const long long t = io.t;
+    const int n = min(max(*io.n, 0), D.K);
+    const float cx = __fmul_rn(0.5f, (float)(D.w - 1)), cy = __fmul_rn(0.5f, (float)(D.h - 1));
+    for (int i = tid; i < n; i += blockDim.x) {
+        const float2 a = io.src[i], b = io.dst[i];
+        ss[i] = make_float2(__fsub_rn(a.x, cx), __fsub_rn(a.y, cy));
+        sd[i] = make_float2(__fsub_rn(b.x, cx), __fsub_rn(b.y, cy));
+    }
+    __syncthreads();
+    stab_affine out;
+    out.a00 = 1.f; out.a01 = 0.f; out.a10 = 0.f; out.a11 = 1.f; out.tx = 0.f; out.ty = 0.f;
+    out.inliers = 0; out.n_tracks = n; out.rms = 0.f; out.flags = STAB_FLAG_SKIPPED;
+    if (n >= max(3, D.min_fit)) {
+        int best = -1, bh = 0x7fffffff;
+        for (int hh = wid; hh < D.H; hh += nwarps) {
+            int i, j, k;
+            sample_triple(D.seed, t, hh, n, i, j, k);
+            float m[6];
+            int cnt = -1;
+            if (three_point(ss[i], ss[j], ss[k], sd[i], sd[j], sd[k], m)) {
+                int c = 0;
+                for (int q = lane; q < n; q += 32) c += is_inlier_affine(m, ss[q], sd[q], D.tau2);
+                cnt = __reduce_add_sync(0xffffffffu, c);
+            }
+            if (cnt > best) { best = cnt; bh = hh; }
+        }
+        if (lane == 0) { wbs[wid] = best; wbh[wid] = bh; }
+        __syncthreads();
+        if (tid == 0) {
+            int b = -1, h = 0x7fffffff;
+            for (int q = 0; q < nwarps; ++q)
+                if (wbs[q] > b || (wbs[q] == b && wbh[q] < h)) { b = wbs[q]; h = wbh[q]; }
+            s_best = b; s_bh = h;
+        }
+        __syncthreads();
+        if (s_best >= 3) {
+            int i, j, k;
+            sample_triple(D.seed, t, s_bh, n, i, j, k);
+            float m[6];
+            three_point(ss[i], ss[j], ss[k], sd[i], sd[j], sd[k], m);
+            float v[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+            for (int q = tid; q < n; q += blockDim.x)
+                if (is_inlier_affine(m, ss[q], sd[q], D.tau2)) {
+                    v[0] += 1.f; v[1] += ss[q].x; v[2] += ss[q].y; v[3] += sd[q].x; v[4] += sd[q].y;
+                }
+            block_sum<8>(v, red);
+            const float ni = v[0];
+            const float msx = v[1] / ni, msy = v[2] / ni, mdx = v[3] / ni, mdy = v[4] / ni;
+            float u[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};   // Sxx00, Sxx01, Sxx11, Syx00, Syx01, Syx10, Syx11
+            for (int q = tid; q < n; q += blockDim.x)
+                if (is_inlier_affine(m, ss[q], sd[q], D.tau2)) {
+                    const float x0 = ss[q].x - msx, x1 = ss[q].y - msy, y0 = sd[q].x - mdx, y1 = sd[q].y - mdy;
+                    u[0] += x0 * x0; u[1] += x0 * x1; u[2] += x1 * x1;
+                    u[3] += y0 * x0; u[4] += y0 * x1; u[5] += y1 * x0; u[6] += y1 * x1;
+                }
+            block_sum<8>(u, red);
+            const float det = u[0] * u[2] - u[1] * u[1];
+            if (det > 0.f) {
+                const float i00 = u[2] / det, i01 = -u[1] / det, i11 = u[0] / det;
+                const float a00 = u[3] * i00 + u[4] * i01, a01 = u[3] * i01 + u[4] * i11;
+                const float a10 = u[5] * i00 + u[6] * i01, a11 = u[5] * i01 + u[6] * i11;
+                const float tx = mdx - (a00 * msx + a01 * msy), ty = mdy - (a10 * msx + a11 * msy);
+                float e[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+                for (int q = tid; q < n; q += blockDim.x)
+                    if (is_inlier_affine(m, ss[q], sd[q], D.tau2)) {
+                        const float px = a00 * ss[q].x + a01 * ss[q].y + tx, py = a10 * ss[q].x + a11 * ss[q].y + ty;
+                        e[0] += (sd[q].x - px) * (sd[q].x - px) + (sd[q].y - py) * (sd[q].y - py);
+                    }
+                block_sum<8>(e, red);
+                out.a00 = a00; out.a01 = a01; out.a10 = a10; out.a11 = a11; out.tx = tx; out.ty = ty;
+                out.inliers = (int)ni;
+                out.rms = sqrtf(e[0] / ni);
+                out.flags = 0;
+            }
+        }
+    }
+    if (tid == 0) *io.out = out;
+}
+
 // Offline smoothing in three launches (no scratch beyond the outputs):
 // (1) trajectory C into the Minv buffer, (2) m' from C, (3) Minv from m'.
 __global__ void k_smooth_c(const stab_motion *m, int T, float *Cbuf)
@@ -413,6 +540,11 @@ void launch_compact(const Launch &L, const StreamDev *S, int n, CompactIO io)
 void launch_fit(const Launch &L, const StreamDev *S, int n, FitIO io, int streaming)
 {
     k_fit<<<n, 512, 0, L.stream>>>(S, io, streaming);
+}
+
+void launch_fit_affine(const Launch &L, const StreamDev *S, AffineIO io)
+{
+    k_fit_affine<<<1, 512, 0, L.stream>>>(S, io);
 }
 
 void launch_smooth_offline(const Launch &L, const stab_motion *m, int T, int W, int w, int h, float zoom,

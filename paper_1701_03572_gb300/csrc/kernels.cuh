@@ -58,6 +58,13 @@ struct FitIO {
     stab_motion *out;
 };
 
+struct AffineIO {
+    const float2 *src, *dst;
+    const int *n;
+    long long t;
+    stab_affine *out;
+};
+
 struct WarpIO {
     const uint8_t *src;
     int sp;
@@ -92,6 +99,7 @@ void launch_lk(const Launch &L, int prec, int rcode, int variant, const StreamDe
 
 void launch_compact(const Launch &L, const StreamDev *S, int n, CompactIO io);
 void launch_fit(const Launch &L, const StreamDev *S, int n, FitIO io, int streaming);
+void launch_fit_affine(const Launch &L, const StreamDev *S, AffineIO io);
 void launch_smooth_offline(const Launch &L, const stab_motion *m, int T, int W, int w, int h, float zoom,
                            float *mprime, float *Minv);
 void launch_smooth_push(const Launch &L, const StreamDev *S, long long t, const stab_motion *m, float *Minv,

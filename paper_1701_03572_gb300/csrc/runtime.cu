@@ -484,6 +484,15 @@ stab_status stab_fit(stab_ctx *c, const float *src, const float *dst, const int 
     return cuda_check(pp.err, "stab_fit");
 }
 
+stab_status stab_fit_affine(stab_ctx *c, const float *src, const float *dst, const int *n, int t, stab_affine *out,
+                            void *stream)
+{
+    if (!c || !src || !dst || !n || !out) return STAB_ERR_INVALID_ARG;
+    CTX_LAUNCH(c, stream);
+    launch_fit_affine(L, pp.ds, AffineIO{(const float2 *)src, (const float2 *)dst, n, t, out});
+    return cuda_check(pp.err, "stab_fit_affine");
+}
+
 stab_status stab_smooth(stab_ctx *c, const stab_motion *m, int T, int W, float *mprime, float *Minv, void *stream)
 {
     if (!c || !m || !mprime || !Minv || T < 1 || W < 1) return STAB_ERR_INVALID_ARG;

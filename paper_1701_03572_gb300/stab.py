@@ -37,6 +37,22 @@ class StabMotion(C.Structure):
                 ("e_rigid", C.c_float), ("e_similarity", C.c_float)]
 
 
+class StabAffine(C.Structure):
+    _fields_ = [("a00", C.c_float), ("a01", C.c_float), ("a10", C.c_float), ("a11", C.c_float), ("tx", C.c_float),
+                ("ty", C.c_float), ("inliers", C.c_int), ("n_tracks", C.c_int), ("rms", C.c_float), ("flags", C.c_int)]
+
+
+AFFINE_WORDS = 10          # 4-byte words of one stab_affine record
+
+
+def affine_from_raw(raw: torch.Tensor) -> dict:
+    """Decode a (N, AFFINE_WORDS) float32 tensor of stab_affine records."""
+    r = raw.detach().cpu().contiguous().view(-1, AFFINE_WORDS)
+    iv = r.view(torch.int32)
+    return dict(m=r[:, :6].double().numpy(), inliers=iv[:, 6].numpy(), n_tracks=iv[:, 7].numpy(), rms=r[:, 8].numpy(),
+                flags=iv[:, 9].numpy())
+
+
 class StreamDesc(C.Structure):
     _fields_ = [("w", C.c_int), ("h", C.c_int), ("channels", C.c_int), ("params", StabParams)]
 
@@ -66,6 +82,7 @@ def lib():
             "stab_lk": ([_vp, _vp, _vp, _i, _vp, _i, _vp, _vp, _vp, _vp, _vp, _vp], _i),
             "stab_track": ([_vp, _vp, _vp, _i, _i, _i, _vp, _vp, _vp, _vp, _vp], _i),
             "stab_fit": ([_vp, _vp, _vp, _vp, _i, _i, _vp, _vp], _i),
+            "stab_fit_affine": ([_vp, _vp, _vp, _vp, _i, _vp, _vp], _i),
             "stab_smooth": ([_vp, _vp, _i, _i, _vp, _vp, _vp], _i),
             "stab_smooth_push": ([_vp, _vp, _vp, _vp, _vp], _i),
             "stab_warp": ([_vp, _vp, _i, _vp, _i, _i, _vp, _vp], _i),
@@ -232,6 +249,13 @@ class Context:
         out = out if out is not None else torch.zeros(MOTION_WORDS, dtype=torch.float32, device=src.device)
         self._chk(lib().stab_fit(self._h, _p(src.contiguous()), _p(dst.contiguous()), _p(n), model, t, _p(out),
                                  _s()), "stab_fit")
+        return out
+
+    def fit_affine(self, src: torch.Tensor, dst: torch.Tensor, n: torch.Tensor, t: int,
+                   out: torch.Tensor | None = None):
+        out = out if out is not None else torch.zeros(AFFINE_WORDS, dtype=torch.float32, device=src.device)
+        self._chk(lib().stab_fit_affine(self._h, _p(src.contiguous()), _p(dst.contiguous()), _p(n), t, _p(out), _s()),
+                  "stab_fit_affine")
         return out
 
     def smooth(self, motions: torch.Tensor, window: int):

@@ -266,3 +266,20 @@ def hybrid_pairs(radial: float, scale: float, seed: int = 7):
     tgt = np.concatenate([near * scale, far * scale + radial * u])
     dst = tgt @ R.T + t
     return (src + c).astype(np.float32), (dst + c).astype(np.float32), w, h
+
+
+def affine_pairs(seed: int, n: int = 60, noise: float = 0.0, outliers: int = 0):
+    """Point pairs in a 320 x 240 frame under a seeded affine map (A near
+    [[1.02, 0.03], [-0.01, 0.97]], t ~ N(0, 3 px), centred coordinates), with
+    N(0, noise) jitter and `outliers` pairs moved by 5-20 px per axis.
+    Returns src, dst (FP32 pixel coordinates), A, t, outlier indices, w, h."""
+    rng = np.random.default_rng(seed)
+    w, h = 320, 240
+    c = np.array([(w - 1) / 2, (h - 1) / 2])
+    A = np.array([[1.02, 0.03], [-0.01, 0.97]]) + rng.normal(0, 0.01, (2, 2))
+    t = rng.normal(0, 3, 2)
+    src = rng.uniform([10, 10], [w - 10, h - 10], (n, 2))
+    dst = (src - c) @ A.T + t + c + rng.normal(0, noise, (n, 2))
+    bad = rng.choice(n, outliers, replace=False)
+    dst[bad] += rng.uniform(5, 20, (outliers, 2)) * rng.choice([-1, 1], (outliers, 2))
+    return src.astype(np.float32), dst.astype(np.float32), A, t, bad, w, h

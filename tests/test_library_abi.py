@@ -40,7 +40,7 @@ def test_default_params_and_argument_errors_without_a_device():
     assert abs(p.eps - 0.01) < 1e-9 and p.model == S.STAB_SIMILARITY and p.precision == S.STAB_FP32
     # the last fields line up with the library's layout (hybrid dwell, crop zoom)
     assert p.dwell == 20 and p.crop_zoom == 1.0
-    assert C.sizeof(S.StabMotion) == 4 * S.MOTION_WORDS
+    assert C.sizeof(S.StabMotion) == 4 * S.MOTION_WORDS and C.sizeof(S.StabAffine) == 4 * S.AFFINE_WORDS
     L = S.lib()
     h = C.c_void_p()
     bad = [dict(max_corners=0), dict(max_corners=4096), dict(levels=0), dict(levels=9), dict(win_radius=13),

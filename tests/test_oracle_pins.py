@@ -14,7 +14,7 @@ import pytest
 from scipy import ndimage
 
 from oracle import oracle as O
-from paper_1701_03572_gb300.synth import hybrid_pairs
+from paper_1701_03572_gb300.synth import affine_pairs, hybrid_pairs
 
 GOLD = os.path.join(os.path.dirname(__file__), "golden")
 
@@ -704,19 +704,6 @@ def test_crop_zoom_hides_the_unfilled_border():
 
 
 # --------------------------------------------- 6-DOF affine fit (Eq. 7-8) --
-def _affine_pairs(seed, n=60, noise=0.0, outliers=0):
-    rng = np.random.default_rng(seed)
-    w, h = 320, 240
-    c = np.array([(w - 1) / 2, (h - 1) / 2])
-    A = np.array([[1.02, 0.03], [-0.01, 0.97]]) + rng.normal(0, 0.01, (2, 2))
-    t = rng.normal(0, 3, 2)
-    src = rng.uniform([10, 10], [w - 10, h - 10], (n, 2))
-    dst = (src - c) @ A.T + t + c + rng.normal(0, noise, (n, 2))
-    bad = rng.choice(n, outliers, replace=False)
-    dst[bad] += rng.uniform(5, 20, (outliers, 2)) * rng.choice([-1, 1], (outliers, 2))
-    return src.astype(np.float32), dst.astype(np.float32), A, t, bad, w, h
-
-
 def test_sample_triples_distinct_and_uniform():
     n = 5
     seen = {}
@@ -731,7 +718,7 @@ def test_sample_triples_distinct_and_uniform():
 
 
 def test_affine_exact_pairs_recovered():
-    src, dst, A, t, _, w, h = _affine_pairs(81)
+    src, dst, A, t, _, w, h = affine_pairs(81)
     f = O.fit_affine(src, dst, w, h, 50, 0, 1)
     assert f["flags"] == 0 and f["inliers"] == len(src) and f["rms"] < 1e-4
     assert np.abs(f["m"][:4] - A.reshape(-1)).max() < 1e-5     # FP32 inputs
@@ -739,7 +726,7 @@ def test_affine_exact_pairs_recovered():
 
 
 def test_affine_refit_is_least_squares_on_inliers():
-    src, dst, A, t, bad, w, h = _affine_pairs(82, n=80, noise=0.2, outliers=16)
+    src, dst, A, t, bad, w, h = affine_pairs(82, n=80, noise=0.2, outliers=16)
     f = O.fit_affine(src, dst, w, h, 200, 3, 1)
     mask = f["mask"]
     assert not mask[bad].any() and mask.sum() >= 80 - 16 - 2  # outliers out; a 1 px gate may drop a tail sample
