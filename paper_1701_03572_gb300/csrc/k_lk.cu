@@ -113,6 +113,17 @@ __device__ __forceinline__ int stage(const E *__restrict__ P, int pitch, int wl,
 // within it sample shared memory only; a larger move re-stages the patch.
 constexpr int LK_MARGIN = 2;
 
+// Samples per column segment for NS samples per thread (segments of 7 rows
+// for the 21 x 21 window and smaller, of 5 rows for radius 11 and 12).
+__host__ __device__ constexpr int lk_seg(int ns) { return ns % 7 == 0 ? 7 : 5; }
+
+// Bilinear sampling shared by the template and the iterations: a thread walks
+// column segments of the window (segment s: column s % ww, rows
+// SEG (s / ww) .. + SEG - 1), forming the horizontal lerp of each patch row
+// once and one vertical lerp per sample, so a segment of SEG samples reads
+// SEG + 1 rows of two taps.
+__device__ __forceinline__ float lerpf(float a, float b, float f) { return fmaf(f, b - a, a); }
+
 // Track one feature from pyramid slot sa to slot sb.  RC = compile-time
 // radius (0: runtime D.r).  sI: pw rows of I, sG: pw rows of (Ix, Iy), sJ:
 // pw + 2 LK_MARGIN rows of the next frame's I (plane precision), red: 3 * WPF.
@@ -126,8 +137,15 @@ __device__ bool lk_track(const StreamDev &D, int sa, int sb, float ux, float uy,
     const int r = RC ? RC : D.r, ww = 2 * r + 1, pw = ww + 1, N = ww * ww;
     const int pj = pw + 2 * LK_MARGIN;
     const int swI = lk_sw(pw), swJ = lk_sw(pj);
-    const int qn = NT / ww, rn = NT - qn * ww;
-    const int i_l0 = tig % ww, j_l0 = tig / ww;
+    constexpr int SEG = lk_seg(NS), Q = NS / SEG;
+    const int nseg = (ww + SEG - 1) / SEG;
+    int scol[Q], srow[Q];   // this thread's segments (first row ww: none)
+#pragma unroll
+    for (int q = 0; q < Q; ++q) {
+        const int sgi = tig + NT * q;
+        scol[q] = sgi % ww;
+        srow[q] = sgi < ww * nseg ? (sgi / ww) * SEG : ww;
+    }
     float gx = 0.f, gy = 0.f, dx = 0.f, dy = 0.f;
     float T[NS], TX[NS], TY[NS];
     for (int l = D.L - 1; l >= 0; --l) {
@@ -142,8 +160,6 @@ __device__ bool lk_track(const StreamDev &D, int sa, int sb, float ux, float uy,
         const float fx = floorf(bx), fy = floorf(by);
         const float ax = bx - fx, ay = by - fy;
         const int ix = (int)fx - r, iy = (int)fy - r;
-        const float w00 = (1.f - ax) * (1.f - ay), w01 = ax * (1.f - ay);
-        const float w10 = (1.f - ax) * ay, w11 = ax * ay;
         const bool inside = ix >= 0 && ix + ww <= wl - 1 && iy >= 0 && iy + ww <= hl - 1;
         // next frame's patch around the level's initial guess, with a margin
         int jx0 = (int)floorf(fminf(fmaxf(px + gx, -64.f), (float)wl + 64.f)) - r - LK_MARGIN;
@@ -156,23 +172,27 @@ __device__ bool lk_track(const StreamDev &D, int sa, int sb, float ux, float uy,
         cpa_wait_all();
         group_sync<WPF>(grp);
         float gxx = 0.f, gxy = 0.f, gyy = 0.f;
-        int i = i_l0, j = j_l0;
 #pragma unroll
-        for (int m = 0; m < NS; ++m) {
-            const int k = tig + NT * m;
-            T[m] = 0.f; TX[m] = 0.f; TY[m] = 0.f;
-            if (k < N) {
-                const int o = j * swI + i + offI;
-                const float t =
-                    w00 * f1(sI[o]) + w01 * f1(sI[o + 1]) + w10 * f1(sI[o + swI]) + w11 * f1(sI[o + swI + 1]);
-                const float2 g00 = f2(sG[o]), g01 = f2(sG[o + 1]), g10 = f2(sG[o + swI]), g11 = f2(sG[o + swI + 1]);
-                const float tx = w00 * g00.x + w01 * g01.x + w10 * g10.x + w11 * g11.x;
-                const float ty = w00 * g00.y + w01 * g01.y + w10 * g10.y + w11 * g11.y;
-                T[m] = t; TX[m] = tx; TY[m] = ty;
-                gxx += tx * tx; gxy += tx * ty; gyy += ty * ty;
+        for (int q = 0; q < Q; ++q) {
+            const PT *pI = sI + offI + scol[q];
+            const PT2 *pG = sG + offI + scol[q];
+            int o = min(srow[q], pw - 1) * swI;
+            float hI = lerpf(f1(pI[o]), f1(pI[o + 1]), ax);
+            float2 g0 = f2(pG[o]), g1 = f2(pG[o + 1]);
+            float hX = lerpf(g0.x, g1.x, ax), hY = lerpf(g0.y, g1.y, ax);
+#pragma unroll
+            for (int e = 0; e < SEG; ++e) {
+                const int m = q * SEG + e, rr = srow[q] + e;
+                o = min(rr + 1, pw - 1) * swI;
+                const float hI1 = lerpf(f1(pI[o]), f1(pI[o + 1]), ax);
+                g0 = f2(pG[o]); g1 = f2(pG[o + 1]);
+                const float hX1 = lerpf(g0.x, g1.x, ax), hY1 = lerpf(g0.y, g1.y, ax);
+                const bool ok = rr < ww;
+                const float t = lerpf(hI, hI1, ay), tx = lerpf(hX, hX1, ay), ty = lerpf(hY, hY1, ay);
+                T[m] = ok ? t : 0.f; TX[m] = ok ? tx : 0.f; TY[m] = ok ? ty : 0.f;
+                gxx += TX[m] * TX[m]; gxy += TX[m] * TY[m]; gyy += TY[m] * TY[m];
+                hI = hI1; hX = hX1; hY = hY1;
             }
-            i += rn; j += qn;
-            if (i >= ww) { i -= ww; ++j; }
         }
         group_sum3<WPF>(gxx, gxy, gyy, red, wig, grp);
         ++tpl;
@@ -190,8 +210,6 @@ __device__ bool lk_track(const StreamDev &D, int sa, int sb, float ux, float uy,
             const float fqx = floorf(qx), fqy = floorf(qy);
             const float cx = qx - fqx, cy = qy - fqy;
             const int jx = (int)fqx - r, jy = (int)fqy - r;
-            const float v00 = (1.f - cx) * (1.f - cy), v01 = cx * (1.f - cy);
-            const float v10 = (1.f - cx) * cy, v11 = cx * cy;
             int ox = jx - jx0, oy = jy - jy0;
             if (ox < 0 || ox > 2 * LK_MARGIN || oy < 0 || oy > 2 * LK_MARGIN) {   // same for the whole group
                 jx0 = jx - LK_MARGIN;
@@ -205,22 +223,24 @@ __device__ bool lk_track(const StreamDev &D, int sa, int sb, float ux, float uy,
                 oy = LK_MARGIN;
             }
             const PT *sJo = sJ + oy * swJ + ox + offJ;
-            float bxs = 0.f, bys = 0.f, unused = 0.f;
-            int i2 = i_l0, j2 = j_l0;
+            float bxs = 0.f, bys = 0.f, unused = 0.f, bxs1 = 0.f, bys1 = 0.f;   // two chains: even / odd samples
 #pragma unroll
-            for (int m = 0; m < NS; ++m) {
-                const int k = tig + NT * m;
-                if (k < N) {
-                    const int o = j2 * swJ + i2;
-                    const float jv = v00 * f1(sJo[o]) + v01 * f1(sJo[o + 1]) + v10 * f1(sJo[o + swJ]) +
-                                     v11 * f1(sJo[o + swJ + 1]);
-                    const float e = T[m] - jv;
-                    bxs += e * TX[m];
-                    bys += e * TY[m];
+            for (int q = 0; q < Q; ++q) {
+                const PT *pJ = sJo + scol[q];
+                int o = min(srow[q], pw - 1) * swJ;
+                float h = lerpf(f1(pJ[o]), f1(pJ[o + 1]), cx);
+#pragma unroll
+                for (int e = 0; e < SEG; ++e) {
+                    const int m = q * SEG + e;
+                    o = min(srow[q] + e + 1, pw - 1) * swJ;
+                    const float h1 = lerpf(f1(pJ[o]), f1(pJ[o + 1]), cx);
+                    const float err = T[m] - lerpf(h, h1, cy);       // samples outside the window have TX = TY = 0
+                    if (m & 1) { bxs1 += err * TX[m]; bys1 += err * TY[m]; }
+                    else { bxs += err * TX[m]; bys += err * TY[m]; }
+                    h = h1;
                 }
-                i2 += rn; j2 += qn;
-                if (i2 >= ww) { i2 -= ww; ++j2; }
             }
+            bxs += bxs1; bys += bys1;
             if (WPF == 1) { bxs = wsum(bxs); bys = wsum(bys); }
             else group_sum3<WPF>(bxs, bys, unused, red, wig, grp);
             const float ex = (gyy * bxs - gxy * bys) * idet;
