@@ -22,6 +22,13 @@
 #define STAB_SEL_SMEM 12288  // selection keys held in shared memory
 #define STAB_TW 64           // image tile: 64 x 16 pixels, 256 threads x 4 pixels
 #define STAB_TH 16
+// Corner response work: strips of 128 threads x 4 columns x 32 rows of the ROI.
+#define STAB_RS_THREADS 128
+#define STAB_RS_ROWS 32
+__host__ __device__ inline int stab_resp_items(int rw, int rh)
+{
+    return ((rw + 4 * STAB_RS_THREADS - 1) / (4 * STAB_RS_THREADS)) * ((rh + STAB_RS_ROWS - 1) / STAB_RS_ROWS);
+}
 #define STAB_WTH 32          // warp output tile: 64 x 32 pixels, 256 threads x 2 rows x 4 pixels
 
 // Per-stream mutable state (device memory).

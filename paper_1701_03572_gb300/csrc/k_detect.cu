@@ -54,15 +54,35 @@ __global__ void k_begin(const StreamDev *__restrict__ S, int n, long long t_ov, 
     st->tpl = 0;
 }
 
-__global__ void __launch_bounds__(256) k_response(const StreamDev *__restrict__ S, WorkList wl, DetIO io)
+// One pixel row's bytes at columns x-3 .. x+6 (clamped into the frame; three
+// aligned words when the run lies inside the row).
+__device__ __forceinline__ void rs_pixels(const uint8_t *__restrict__ g, int pitch, int w, int h, int x, int yy,
+                                          bool fast, int (&p)[10])
 {
-    constexpr int TW = STAB_TW, TH = STAB_TH;
-    constexpr int PW = TW + 6, PH = TH + 6;   // pixels
-    constexpr int GW = TW + 4, GH = TH + 4;   // Sobel
-    constexpr int LW = TW + 2, LH = TH + 2;   // scores (tile + NMS ring)
-    __shared__ uint8_t spx[PH][PW + 2];
-    __shared__ short sgx[GH][GW], sgy[GH][GW];
-    __shared__ float slam[LH][LW];
+    const uint8_t *row = g + (size_t)clampi(yy, 0, h - 1) * pitch;
+    if (fast) {
+        const unsigned *q = reinterpret_cast<const unsigned *>(row + x - 4);
+        const unsigned w0 = __ldg(q), w1 = __ldg(q + 1), w2 = __ldg(q + 2);
+        p[0] = (w0 >> 8) & 255u; p[1] = (w0 >> 16) & 255u; p[2] = w0 >> 24;
+        p[3] = w1 & 255u; p[4] = (w1 >> 8) & 255u; p[5] = (w1 >> 16) & 255u; p[6] = w1 >> 24;
+        p[7] = w2 & 255u; p[8] = (w2 >> 8) & 255u; p[9] = (w2 >> 16) & 255u;
+    } else {
+#pragma unroll
+        for (int k = 0; k < 10; ++k) p[k] = __ldg(row + clampi(x - 3 + k, 0, w - 1));
+    }
+}
+
+// Corner response (Eq. 2), NMS and candidate list as barrier-free vertical
+// strips: a thread owns ROI columns x .. x+3 of a 32-row strip and walks its
+// pixel rows once.  Per pixel row it forms the separable Sobel parts
+// (horizontal difference and [1 2 1] smoothing) of columns x-2 .. x+5 and
+// keeps two rows of them; three rows give gx, gy of the previous row, whose
+// products summed over 3 columns (x-1 .. x+4) are kept for two rows more; three
+// such rows give the 3x3 structure tensor and the score two rows back, and
+// three score rows give the NMS of the row before.  Integer sums are exact;
+// the score is lambda32 of them, as in the tile form.
+__global__ void __launch_bounds__(STAB_RS_THREADS) k_response(const StreamDev *__restrict__ S, WorkList wl, DetIO io)
+{
     __shared__ unsigned smax;
     __shared__ int s_last;
     __shared__ unsigned s_cnt[256];
@@ -80,87 +100,98 @@ __global__ void __launch_bounds__(256) k_response(const StreamDev *__restrict__ 
         else { g = D.u8[(int)((st->t - 1) & 1)][0]; pitch = D.lp[0]; }
         const int w = D.w, h = D.h;
         const int rx1 = D.roi_x1, ry1 = D.roi_y1;
-        const int tiles_x = (rx1 - D.roi_x0 + TW - 1) / TW;
-        const int x0 = D.roi_x0 + (local % tiles_x) * TW, y0 = D.roi_y0 + (local / tiles_x) * TH;
-        for (int i = tid; i < PH * PW; i += blockDim.x) {
-            int r = i / PW, c = i - r * PW;
-            spx[r][c] = __ldg(g + (size_t)clampi(y0 - 3 + r, 0, h - 1) * pitch + clampi(x0 - 3 + c, 0, w - 1));
-        }
+        const int ngx = (rx1 - D.roi_x0 + 4 * STAB_RS_THREADS - 1) / (4 * STAB_RS_THREADS);
+        const int x = D.roi_x0 + ((local % ngx) * STAB_RS_THREADS + tid) * 4;
+        const int y0 = D.roi_y0 + (local / ngx) * STAB_RS_ROWS;
+        const int nrows = min(STAB_RS_ROWS, ry1 - y0);
+        const bool fast = x >= 4 && x + 8 <= w && ((x | pitch) & 3) == 0 && (reinterpret_cast<uintptr_t>(g) & 3) == 0;
         if (tid == 0) smax = 0;
         __syncthreads();
-        for (int i = tid; i < GH * GW; i += blockDim.x) {
-            int r = i / GW, c = i - r * GW;
-            int gx = (spx[r][c + 2] + 2 * spx[r + 1][c + 2] + spx[r + 2][c + 2]) -
-                     (spx[r][c] + 2 * spx[r + 1][c] + spx[r + 2][c]);
-            int gy = (spx[r + 2][c] + 2 * spx[r + 2][c + 1] + spx[r + 2][c + 2]) -
-                     (spx[r][c] + 2 * spx[r][c + 1] + spx[r][c + 2]);
-            sgx[r][c] = (short)gx;
-            sgy[r][c] = (short)gy;
-        }
-        __syncthreads();
-        for (int i = tid; i < LH * LW; i += blockDim.x) {
-            int r = i / LW, c = i - r * LW;
-            int a = 0, b = 0, cc = 0;
-#pragma unroll
-            for (int dy = 0; dy < 3; ++dy)
-#pragma unroll
-                for (int dx = 0; dx < 3; ++dx) {
-                    int gx = sgx[r + dy][c + dx], gy = sgy[r + dy][c + dx];
-                    a += gx * gx;
-                    b += gx * gy;
-                    cc += gy * gy;
-                }
-            slam[r][c] = lambda32(a, b, cc);
-        }
-        __syncthreads();
-        // NMS on 4 consecutive pixels of one row
-        const int row = tid >> 4, c4 = (tid & 15) * 4;
-        const int y = y0 + row;
-        unsigned long long keys[2];
-        int nk = 0;
+        int d1[8] = {0}, d2[8] = {0}, s1[8] = {0}, s2[8] = {0};      // Sobel parts of pixel rows py-1, py-2
+        int ha1[6] = {0}, hb1[6] = {0}, hc1[6] = {0};                // tensor row sums of row py-2
+        int ha2[6] = {0}, hb2[6] = {0}, hc2[6] = {0};                // ... of row py-3
+        float l1[6] = {0.f}, l2[6] = {0.f};                          // scores of rows py-3, py-4
         unsigned lmax = 0;
+        for (int k = 0; k < nrows + 6; ++k) {
+            const int py = y0 - 3 + k;
+            int p[10];
+            rs_pixels(g, pitch, w, h, x, py, fast, p);
+            int d0[8], s0[8];
 #pragma unroll
-        for (int k = 0; k < 4; ++k) {
-            int x = x0 + c4 + k;
-            if (x < rx1 && y < ry1) {
-                int r = row + 1, c = c4 + k + 1;
-                float v = slam[r][c];
-                lmax = max(lmax, __float_as_uint(v));
-                bool keep = v > 0.0f;
+            for (int j = 0; j < 8; ++j) {
+                d0[j] = p[j + 2] - p[j];
+                s0[j] = p[j] + 2 * p[j + 1] + p[j + 2];
+            }
+            // gx, gy of row py-1 at columns x-2 .. x+5; products summed over 3 columns
+            int A[8], B[8], C[8];
 #pragma unroll
-                for (int dy = -1; dy <= 1; ++dy)
+            for (int j = 0; j < 8; ++j) {
+                const int gx = d2[j] + 2 * d1[j] + d0[j], gy = s0[j] - s2[j];
+                A[j] = gx * gx; B[j] = gx * gy; C[j] = gy * gy;
+            }
+            int ha0[6], hb0[6], hc0[6];
 #pragma unroll
-                    for (int dx = -1; dx <= 1; ++dx) {
-                        if (dx == 0 && dy == 0) continue;
-                        float u = slam[r + dy][c + dx];
-                        bool after = (dy > 0) || (dy == 0 && dx > 0);   // neighbour later in raster order
-                        keep = keep && (v > u || (v == u && after));
+            for (int i = 0; i < 6; ++i) {
+                ha0[i] = A[i] + A[i + 1] + A[i + 2];
+                hb0[i] = B[i] + B[i + 1] + B[i + 2];
+                hc0[i] = C[i] + C[i + 1] + C[i + 2];
+            }
+            // score of row py-2 at columns x-1 .. x+4
+            float l0[6];
+#pragma unroll
+            for (int i = 0; i < 6; ++i)
+                l0[i] = lambda32(ha2[i] + ha1[i] + ha0[i], hb2[i] + hb1[i] + hb0[i], hc2[i] + hc1[i] + hc0[i]);
+            // NMS of row py-3 (scores l2 = row py-4, l1 = py-3, l0 = py-2)
+            unsigned long long keys[2];
+            int nk = 0;
+            const int y = py - 3;
+            if (k >= 6) {
+#pragma unroll
+                for (int c = 0; c < 4; ++c) {
+                    if (x + c < rx1) {
+                        const float v = l1[c + 1];
+                        lmax = max(lmax, __float_as_uint(v));
+                        // strict maximum over the 3x3 neighbourhood; a tie goes to the lower raster index
+                        bool keep = v > 0.0f && v > l2[c] && v > l2[c + 1] && v > l2[c + 2] && v > l1[c];
+                        keep = keep && v >= l1[c + 2] && v >= l0[c] && v >= l0[c + 1] && v >= l0[c + 2];
+                        if (keep && nk < 2) {
+                            const unsigned idx = (unsigned)(y * w + x + c);
+                            keys[nk++] = ((unsigned long long)__float_as_uint(v) << 32) |
+                                         (unsigned long long)(0xFFFFFFFFu - idx);
+                        }
                     }
-                if (keep && nk < 2) {
-                    unsigned idx = (unsigned)(y * w + x);
-                    keys[nk++] = ((unsigned long long)__float_as_uint(v) << 32) | (unsigned long long)(0xFFFFFFFFu - idx);
                 }
+            }
+            // warp-aggregated append of this row's candidates
+            if (__any_sync(0xffffffffu, nk > 0)) {
+                int incl = nk;
+                for (int o = 1; o < 32; o <<= 1) {
+                    const int v = __shfl_up_sync(0xffffffffu, incl, o);
+                    if (lane >= o) incl += v;
+                }
+                const int tot = __shfl_sync(0xffffffffu, incl, 31);
+                int base = 0;
+                if (lane == 31) base = atomicAdd(&st->n_cand, tot);
+                base = __shfl_sync(0xffffffffu, base, 31);
+                const int pos = base + incl - nk;
+                for (int q = 0; q < nk; ++q) {
+                    if (pos + q < D.cand_cap) D.cand[pos + q] = keys[q];
+                    else set_err(st, STAB_ERR_CAPACITY);
+                    atomicAdd(&D.hist[(unsigned)(keys[q] >> (32 + STAB_HSHIFT))], 1u);
+                }
+            }
+            // shift the row windows
+#pragma unroll
+            for (int j = 0; j < 8; ++j) { d2[j] = d1[j]; d1[j] = d0[j]; s2[j] = s1[j]; s1[j] = s0[j]; }
+#pragma unroll
+            for (int i = 0; i < 6; ++i) {
+                ha2[i] = ha1[i]; ha1[i] = ha0[i]; hb2[i] = hb1[i]; hb1[i] = hb0[i]; hc2[i] = hc1[i]; hc1[i] = hc0[i];
+                l2[i] = l1[i]; l1[i] = l0[i];
             }
         }
         // block max of the score
         for (int o = 16; o; o >>= 1) lmax = max(lmax, __shfl_xor_sync(0xffffffffu, lmax, o));
         if (lane == 0) atomicMax(&smax, lmax);
-        // warp-aggregated append
-        int incl = nk;
-        for (int o = 1; o < 32; o <<= 1) {
-            int v = __shfl_up_sync(0xffffffffu, incl, o);
-            if (lane >= o) incl += v;
-        }
-        int tot = __shfl_sync(0xffffffffu, incl, 31);
-        int base = 0;
-        if (lane == 31 && tot) base = atomicAdd(&st->n_cand, tot);
-        base = __shfl_sync(0xffffffffu, base, 31);
-        int pos = base + incl - nk;
-        for (int k = 0; k < nk; ++k) {
-            if (pos + k < D.cand_cap) D.cand[pos + k] = keys[k];
-            else set_err(st, STAB_ERR_CAPACITY);
-            atomicAdd(&D.hist[(unsigned)(keys[k] >> (32 + STAB_HSHIFT))], 1u);
-        }
         __syncthreads();
         if (tid == 0) {
             atomicMax(&st->lam_max, smax);
@@ -177,20 +208,20 @@ __global__ void __launch_bounds__(256) k_response(const StreamDev *__restrict__ 
             float thr = __fmul_rn(D.quality, __uint_as_float(lm));
             unsigned thr_bits = __float_as_uint(thr);
             unsigned tbin = thr_bits >> STAB_HSHIFT;
-            // thread i owns bins [4095 - 16 i - 15, 4095 - 16 i], highest first
+            // thread i owns bins [4095 - 32 i - 31, 4095 - 32 i], highest first
             unsigned cnt = 0;
-            for (int j = 0; j < 16; ++j) {
-                unsigned b = STAB_HBINS - 1 - 16 * tid - j;
+            for (int j = 0; j < 32; ++j) {
+                unsigned b = STAB_HBINS - 1 - 32 * tid - j;
                 if (b >= tbin) cnt += __ldcg(&D.hist[b]);
             }
             s_cnt[tid] = cnt;
             __syncthreads();
             if (tid == 0) {
                 unsigned K = (unsigned)D.K, cum = 0, bin = tbin;
-                for (int i = 0; i < 256; ++i) {
+                for (int i = 0; i < STAB_RS_THREADS; ++i) {
                     if (cum + s_cnt[i] >= K) {
-                        for (int j = 0; j < 16; ++j) {
-                            unsigned b = STAB_HBINS - 1 - 16 * i - j;
+                        for (int j = 0; j < 32; ++j) {
+                            unsigned b = STAB_HBINS - 1 - 32 * i - j;
                             if (b < tbin) break;
                             cum += __ldcg(&D.hist[b]);
                             if (cum >= K) { bin = b; break; }
@@ -352,7 +383,8 @@ void launch_begin(const Launch &L, const StreamDev *S, int n, long long t_ov, in
 static int occ_response()
 {
     static int occ = 0;
-    if (!occ && (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_response, 256, 0) != cudaSuccess || occ < 1))
+    if (!occ && (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_response, STAB_RS_THREADS, 0) != cudaSuccess ||
+                 occ < 1))
         occ = 1;
     return occ;
 }
@@ -374,7 +406,7 @@ void warm_detect()
 
 void launch_response(const Launch &L, const StreamDev *S, WorkList wl, DetIO io)
 {
-    k_response<<<grid_for(L, wl.total, occ_response()), 256, 0, L.stream>>>(S, wl, io);
+    k_response<<<grid_for(L, wl.total, occ_response()), STAB_RS_THREADS, 0, L.stream>>>(S, wl, io);
 }
 
 void launch_filter(const Launch &L, const StreamDev *S, WorkList wl)

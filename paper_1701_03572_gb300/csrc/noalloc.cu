@@ -121,7 +121,7 @@ extern "C" stab_status stab_detect_noalloc(const uint8_t *gray, int w, int h, in
     d.feat = reinterpret_cast<float2 *>(base + kOffFeat);
     d.det_lam = reinterpret_cast<float *>(base + kOffLam);
     d.st = reinterpret_cast<StreamState *>(base + kOffState);
-    const int tiles = ((rw + STAB_TW - 1) / STAB_TW) * ((rh + STAB_TH - 1) / STAB_TH);
+    const int tiles = stab_resp_items(rw, rh);
     const int chunks = (d.cand_cap + kChunk - 1) / kChunk;
     cudaStream_t s = (cudaStream_t)stream;
     k_noalloc_setup<<<1, 256, 0, s>>>(d, tiles, chunks);

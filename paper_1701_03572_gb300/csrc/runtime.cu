@@ -221,7 +221,7 @@ stab_status build(Pipeline &pp, int n, const int *w, const int *h, const int *C,
     mk(&pp.wl_l0, [](const StreamDev &D) { return ((D.w + 511) / 512) * ((D.h + 31) / 32); });
     for (int l = 1; l < STAB_MAXL; ++l)
         mk(&pp.wl_pyr[l], [l](const StreamDev &D) { return l < D.L ? tiles(D.lw[l], D.lh[l]) : 0; });
-    mk(&pp.wl_resp, [](const StreamDev &D) { return tiles(D.roi_x1 - D.roi_x0, D.roi_y1 - D.roi_y0); });
+    mk(&pp.wl_resp, [](const StreamDev &D) { return stab_resp_items(D.roi_x1 - D.roi_x0, D.roi_y1 - D.roi_y0); });
     mk(&pp.wl_filter, [](const StreamDev &D) { return (D.cand_cap + 2047) / 2048; });
     mk(&pp.wl_lk, [](const StreamDev &D) { return D.K; });
     mk(&pp.wl_warp, [](const StreamDev &D) { return ((D.w + STAB_TW - 1) / STAB_TW) * ((D.h + STAB_WTH - 1) / STAB_WTH); });
