@@ -127,8 +127,10 @@ __device__ __forceinline__ float lerpf(float a, float b, float f) { return fmaf(
 // Track one feature from pyramid slot sa to slot sb.  RC = compile-time
 // radius (0: runtime D.r).  sI: pw rows of I, sG: pw rows of (Ix, Iy), sJ:
 // pw + 2 LK_MARGIN rows of the next frame's I (plane precision), red: 3 * WPF.
+// Not inlined: the kernel calls it for the forward and the backward track, and
+// one copy of its unrolled body keeps the instruction working set small.
 template <typename PT, int NS, int RC, int WPF>
-__device__ bool lk_track(const StreamDev &D, int sa, int sb, float ux, float uy, float &vx, float &vy, int &iters,
+__device__ __noinline__ bool lk_track(const StreamDev &D, int sa, int sb, float ux, float uy, float &vx, float &vy, int &iters,
                          int &tpl, PT *sI, typename Plane2<PT>::type *sG, PT *sJ, float *red, int tig, int grp)
 {
     typedef typename Plane2<PT>::type PT2;
@@ -223,7 +225,7 @@ __device__ bool lk_track(const StreamDev &D, int sa, int sb, float ux, float uy,
                 oy = LK_MARGIN;
             }
             const PT *sJo = sJ + oy * swJ + ox + offJ;
-            float bxs = 0.f, bys = 0.f, unused = 0.f, bxs1 = 0.f, bys1 = 0.f;   // two chains: even / odd samples
+            float bxs = 0.f, bys = 0.f, unused = 0.f;
 #pragma unroll
             for (int q = 0; q < Q; ++q) {
                 const PT *pJ = sJo + scol[q];
@@ -235,12 +237,11 @@ __device__ bool lk_track(const StreamDev &D, int sa, int sb, float ux, float uy,
                     o = min(srow[q] + e + 1, pw - 1) * swJ;
                     const float h1 = lerpf(f1(pJ[o]), f1(pJ[o + 1]), cx);
                     const float err = T[m] - lerpf(h, h1, cy);       // samples outside the window have TX = TY = 0
-                    if (m & 1) { bxs1 += err * TX[m]; bys1 += err * TY[m]; }
-                    else { bxs += err * TX[m]; bys += err * TY[m]; }
+                    bxs += err * TX[m];
+                    bys += err * TY[m];
                     h = h1;
                 }
             }
-            bxs += bxs1; bys += bys1;
             if (WPF == 1) { bxs = wsum(bxs); bys = wsum(bys); }
             else group_sum3<WPF>(bxs, bys, unused, red, wig, grp);
             const float ex = (gyy * bxs - gxy * bys) * idet;
