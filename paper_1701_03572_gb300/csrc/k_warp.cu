@@ -172,7 +172,9 @@ __device__ __forceinline__ void make_job(const StreamDev *__restrict__ S, const 
         const int u = D.st->out_frame;
         if (u < 0) return;
         j.src = D.ring + (long long)(u % D.ring_len) * D.slot_bytes;
-        j.sp = D.in_pitch; j.dst = D.out; j.dp = D.out_pitch; j.C = D.C; Mp = D.Minv;
+        // two output buffers by step parity: the host copy of one overlaps the next step
+        j.sp = D.in_pitch; j.dst = D.out + (long long)(D.st->t & 1) * D.slot_bytes; j.dp = D.out_pitch; j.C = D.C;
+        Mp = D.Minv;
     }
 #pragma unroll
     for (int k = 0; k < 6; ++k) j.M[k] = Mp[k];

@@ -35,6 +35,12 @@ struct Pipeline {
     cudaGraphExec_t gexec = nullptr;
     long long t_host = 0;
     int lk_variant = 1;   // tracker kernel variant (autotuned for batches)
+    // host-buffer steps: input copies, the step and output copies on three
+    // streams chained by events, so copies of neighbouring steps overlap the step
+    cudaStream_t hs_in = nullptr, hs_comp = nullptr, hs_out = nullptr;
+    cudaEvent_t ev_in[2] = {}, ev_comp[4] = {}, ev_out[4] = {}, ev_join = nullptr;
+    bool host_mode = false;   // the last step was a host-buffer step
+    int wmax = 1;             // largest smoothing window of the batch
 
     // Window radius for the tracker launch: the radius when every stream uses
     // the same one, its negative (the largest) when they differ.
@@ -53,6 +59,11 @@ struct Pipeline {
         if (gexec) cudaGraphExecDestroy(gexec);
         if (graph) cudaGraphDestroy(graph);
         if (cap) cudaStreamDestroy(cap);
+        for (cudaStream_t x : {hs_in, hs_comp, hs_out})
+            if (x) cudaStreamDestroy(x);
+        for (cudaEvent_t e : {ev_in[0], ev_in[1], ev_comp[0], ev_comp[1], ev_comp[2], ev_comp[3], ev_out[0], ev_out[1],
+                              ev_out[2], ev_out[3], ev_join})
+            if (e) cudaEventDestroy(e);
         if (prefix) cudaFree(prefix);
         if (ds) cudaFree(ds);
         if (arena) cudaFree(arena);
@@ -187,7 +198,7 @@ stab_status build(Pipeline &pp, int n, const int *w, const int *h, const int *C,
             D.out_pitch = D.in_pitch;
             if (C[i]) {
                 D.ring = (uint8_t *)take((size_t)D.slot_bytes * pp.ring);
-                D.out = (uint8_t *)take((size_t)D.slot_bytes);
+                D.out = (uint8_t *)take((size_t)D.slot_bytes * 2);   // two buffers by step parity
             } else {
                 D.ring = nullptr;
                 D.out = nullptr;
@@ -537,6 +548,7 @@ stab_status stab_batch_create(int n, const stab_stream_desc *d, int ring, stab_b
     stab_batch *b = new stab_batch();
     b->C = C;
     stab_status s = build(b->pp, n, w.data(), h.data(), C.data(), P.data(), ring);
+    for (int i = 0; i < n; ++i) b->pp.wmax = std::max(b->pp.wmax, P[i].smooth_window);
     if (s == STAB_OK && cudaStreamCreateWithFlags(&b->pp.cap, cudaStreamNonBlocking) != cudaSuccess)
         s = cuda_check(b->pp.err, "stream create");
     if (s != STAB_OK) {
@@ -563,8 +575,9 @@ uint8_t *stab_batch_input(stab_batch *b, int i, int slot)
 
 uint8_t *stab_batch_output(stab_batch *b, int i)
 {
-    if (!b || i < 0 || i >= b->pp.n) return nullptr;
-    return b->pp.hs[i].out;
+    if (!b || i < 0 || i >= b->pp.n || !b->pp.hs[i].out) return nullptr;
+    const StreamDev &D = b->pp.hs[i];
+    return D.out + (size_t)((b->pp.t_host - 1) & 1) * D.slot_bytes;   // the buffer the last step wrote
 }
 
 int stab_batch_pitch(const stab_batch *b, int i) { return (b && i >= 0 && i < b->pp.n) ? b->pp.hs[i].in_pitch : 0; }
@@ -578,6 +591,7 @@ stab_status stab_batch_step(stab_batch *b, int use_graph, void *stream)
     Pipeline &pp = b->pp;
     cudaStream_t s = (cudaStream_t)stream;
     pp.last = s;
+    pp.host_mode = false;
     if (use_graph) {
         if (!pp.gexec) {
             if (cudaStreamBeginCapture(pp.cap, cudaStreamCaptureModeThreadLocal) != cudaSuccess)
@@ -601,6 +615,7 @@ stab_status stab_batch_step_profiled(stab_batch *b, void *stream, float *ms, int
     Prof pf;
     pf.s = (cudaStream_t)stream;
     pp.last = pf.s;
+    pp.host_mode = false;
     enqueue_step(pp, pf.s, &pf);
     ++pp.t_host;
     stab_status st = cuda_check(pp.err, "stab_batch_step_profiled");
@@ -766,27 +781,67 @@ stab_status stab_batch_autotune(stab_batch *b, const char *cache_path, int *vari
     return stab_batch_set_lk_variant(b, v);
 }
 
+static stab_status host_streams(Pipeline &pp)
+{
+    if (pp.hs_in) return STAB_OK;
+    bool ok = cudaStreamCreateWithFlags(&pp.hs_in, cudaStreamNonBlocking) == cudaSuccess &&
+              cudaStreamCreateWithFlags(&pp.hs_comp, cudaStreamNonBlocking) == cudaSuccess &&
+              cudaStreamCreateWithFlags(&pp.hs_out, cudaStreamNonBlocking) == cudaSuccess &&
+              cudaEventCreateWithFlags(&pp.ev_join, cudaEventDisableTiming) == cudaSuccess;
+    for (int k = 0; ok && k < 4; ++k)
+        ok = cudaEventCreateWithFlags(&pp.ev_comp[k], cudaEventDisableTiming) == cudaSuccess &&
+             cudaEventCreateWithFlags(&pp.ev_out[k], cudaEventDisableTiming) == cudaSuccess &&
+             (k >= 2 || cudaEventCreateWithFlags(&pp.ev_in[k], cudaEventDisableTiming) == cudaSuccess);
+    return ok ? STAB_OK : cuda_check(pp.err, "host-step streams");
+}
+
+// Host-buffer step t: copies of frame t into ring slot t % ring on hs_in, the
+// step on hs_comp, copies of the composed frames on hs_out, chained by events.
+// Slot t % ring is last read by the warp of step t - ring + 1 + W/2, done once
+// step t - 2 is done when ring >= W/2 + 3 (else the copies wait for step t - 1);
+// the output buffer of step t (parity t) was last read by the output copies
+// of step t - 2.  The caller's stream waits for this step's output copies.
 stab_status stab_batch_step_host(stab_batch *b, const uint8_t *const *frames, uint8_t *const *outs, void *stream)
 {
     if (!b || !frames) return STAB_ERR_INVALID_ARG;
+    for (int i = 0; i < b->pp.n; ++i)
+        if (!frames[i]) return STAB_ERR_INVALID_ARG;
     Pipeline &pp = b->pp;
+    stab_status st = host_streams(pp);
+    if (st != STAB_OK) return st;
     cudaStream_t s = (cudaStream_t)stream;
     const long long t = pp.t_host;
+    if (!pp.host_mode) {   // order after whatever the caller submitted before
+        cudaEventRecord(pp.ev_join, s);
+        cudaStreamWaitEvent(pp.hs_in, pp.ev_join, 0);
+        cudaStreamWaitEvent(pp.hs_comp, pp.ev_join, 0);
+        cudaStreamWaitEvent(pp.hs_out, pp.ev_join, 0);
+    }
+    const long long back = pp.ring >= pp.wmax / 2 + 3 ? 2 : 1;
+    if (pp.host_mode && t >= back) cudaStreamWaitEvent(pp.hs_in, pp.ev_comp[(t - back) & 3], 0);
     for (int i = 0; i < pp.n; ++i) {
         const StreamDev &D = pp.hs[i];
-        if (!frames[i]) return STAB_ERR_INVALID_ARG;
         cudaMemcpy2DAsync(D.ring + (size_t)(t % pp.ring) * D.slot_bytes, D.in_pitch, frames[i], (size_t)D.w * D.C,
-                          (size_t)D.w * D.C, D.h, cudaMemcpyHostToDevice, s);
+                          (size_t)D.w * D.C, D.h, cudaMemcpyHostToDevice, pp.hs_in);
     }
-    stab_status st = stab_batch_step(b, 1, stream);
+    cudaEventRecord(pp.ev_in[t & 1], pp.hs_in);
+    cudaStreamWaitEvent(pp.hs_comp, pp.ev_in[t & 1], 0);
+    if (pp.host_mode && t >= 2) cudaStreamWaitEvent(pp.hs_comp, pp.ev_out[(t - 2) & 3], 0);
+    st = stab_batch_step(b, 1, pp.hs_comp);
     if (st != STAB_OK) return st;
+    cudaEventRecord(pp.ev_comp[t & 3], pp.hs_comp);
+    cudaStreamWaitEvent(pp.hs_out, pp.ev_comp[t & 3], 0);
     if (outs)
         for (int i = 0; i < pp.n; ++i) {
             const StreamDev &D = pp.hs[i];
             if (outs[i] && t - 1 - pp.P[i].smooth_window / 2 >= 0)
-                cudaMemcpy2DAsync(outs[i], (size_t)D.w * D.C, D.out, D.out_pitch, (size_t)D.w * D.C, D.h,
-                                  cudaMemcpyDeviceToHost, s);
+                cudaMemcpy2DAsync(outs[i], (size_t)D.w * D.C, D.out + (size_t)(t & 1) * D.slot_bytes, D.out_pitch,
+                                  (size_t)D.w * D.C, D.h, cudaMemcpyDeviceToHost, pp.hs_out);
         }
+    cudaEventRecord(pp.ev_out[t & 3], pp.hs_out);
+    cudaStreamWaitEvent(s, pp.ev_out[t & 3], 0);
+    pp.last = s;
+    pp.host_mode = true;
     return cuda_check(pp.err, "stab_batch_step_host");
 }
 

@@ -377,3 +377,36 @@ def test_autotuner_picks_a_variant_and_caches_it(tmp_path):
             assert np.array_equal(np.array(mot[i]["m"], np.float32), m["m"][T - 1].astype(np.float32))
         else:
             assert np.abs(np.array(mot[i]["m"]) - m["m"][T - 1]).max() < 1e-3
+
+
+def test_batch_host_buffers_pipelined_equal_device_path():
+    """stab_batch_step_host overlaps the copies of neighbouring steps with the
+    step (three streams, double-buffered output): calls made back to back with
+    distinct host output buffers and one synchronisation at the end give the
+    same frames as the device-input path, bit for bit."""
+    T, W = 16, 7
+    clips = [_clip(0, T, s)["frames"].numpy() for s in (91, 92)]
+    params = [_params(max_corners=200, levels=3, smooth_window=W, precision=1),
+              _params(max_corners=150, levels=3, smooth_window=W, precision=1, crop_zoom=1.05)]
+    ring = W // 2 + 3
+    bd = S.Batch([(320, 240, 1, p) for p in params], ring=ring)
+    ref = [[None] * T for _ in clips]
+    for t in range(T):
+        for i, f in enumerate(clips):
+            bd.input_slot(i, t % bd.ring).copy_(_cuda(f[t]))
+        bd.step(use_graph=True)
+        torch.cuda.synchronize()
+        if t - 1 - W // 2 >= 0:
+            for i in range(len(clips)):
+                ref[i][t] = bd.output(i).cpu().numpy().copy()
+    assert bd.sync() == 0
+    bh = S.Batch([(320, 240, 1, p) for p in params], ring=ring)
+    host = [[torch.as_tensor(f[t]).pin_memory() for t in range(T)] for f in clips]
+    outs = [[torch.zeros((240, 320), dtype=torch.uint8).pin_memory() for _ in clips] for _ in range(T)]
+    for t in range(T):
+        bh.step_host([host[i][t] for i in range(len(clips))], outs[t])
+    assert bh.sync() == 0
+    for t in range(T):
+        for i in range(len(clips)):
+            if ref[i][t] is not None:
+                assert np.array_equal(outs[t][i].numpy(), ref[i][t]), (t, i)
