@@ -114,6 +114,41 @@ __device__ __forceinline__ void set_err(StreamState *st, int code)
 
 __device__ __forceinline__ int clampi(int v, int lo, int hi) { return v < lo ? lo : (v > hi ? hi : v); }
 
+// Packed pair of FP32 values (lane 0 in the low word) and the sm_100+ f32x2
+// forms of add / sub / fma: each lane is the IEEE operation of its scalar form.
+typedef unsigned long long fx2;
+__device__ __forceinline__ fx2 pk(float lo, float hi)
+{
+    fx2 r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(lo), "f"(hi));
+    return r;
+}
+__device__ __forceinline__ void upk(fx2 v, float &lo, float &hi) { asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(v)); }
+__device__ __forceinline__ fx2 fma2(fx2 a, fx2 b, fx2 c)
+{
+    fx2 d;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+    return d;
+}
+__device__ __forceinline__ fx2 add2(fx2 a, fx2 b)
+{
+    fx2 d;
+    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+__device__ __forceinline__ fx2 add2_rd(fx2 a, fx2 b)
+{
+    fx2 d;
+    asm("add.rm.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+__device__ __forceinline__ fx2 sub2(fx2 a, fx2 b)
+{
+    fx2 d;
+    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+
 // Plane element access for the two storage precisions.
 __device__ __forceinline__ float ld1(const float *p) { return __ldg(p); }
 __device__ __forceinline__ float ld1(const __half *p) { return __half2float(__ldg(p)); }

@@ -149,7 +149,12 @@ __device__ __noinline__ bool lk_track(const StreamDev &D, int sa, int sb, float 
         srow[q] = sgi < ww * nseg ? (sgi / ww) * SEG : ww;
     }
     float gx = 0.f, gy = 0.f, dx = 0.f, dy = 0.f;
-    float T[NS], TX[NS], TY[NS];
+    // An even number of segments per thread runs as pairs (segments 2p, 2p+1
+    // in the two lanes of packed f32x2 arithmetic); T, Tx, Ty are kept as pairs.
+    constexpr bool PAIR = Q % 2 == 0;
+    constexpr int NP = PAIR ? NS / 2 : 1;
+    float T[PAIR ? 1 : NS], TX[PAIR ? 1 : NS], TY[PAIR ? 1 : NS];
+    fx2 TT[NP], TTX[NP], TTY[NP];
     for (int l = D.L - 1; l >= 0; --l) {
         const PT *Ia = reinterpret_cast<const PT *>(D.pI[sa][l]);
         const PT2 *Ga = reinterpret_cast<const PT2 *>(D.pG[sa][l]);
@@ -174,26 +179,69 @@ __device__ __noinline__ bool lk_track(const StreamDev &D, int sa, int sb, float 
         cpa_wait_all();
         group_sync<WPF>(grp);
         float gxx = 0.f, gxy = 0.f, gyy = 0.f;
+        if constexpr (PAIR) {
+            const fx2 AX = pk(ax, ax), AY = pk(ay, ay);
+            fx2 sxx = pk(0.f, 0.f), sxy = sxx, syy = sxx;
 #pragma unroll
-        for (int q = 0; q < Q; ++q) {
-            const PT *pI = sI + offI + scol[q];
-            const PT2 *pG = sG + offI + scol[q];
-            int o = min(srow[q], pw - 1) * swI;
-            float hI = lerpf(f1(pI[o]), f1(pI[o + 1]), ax);
-            float2 g0 = f2(pG[o]), g1 = f2(pG[o + 1]);
-            float hX = lerpf(g0.x, g1.x, ax), hY = lerpf(g0.y, g1.y, ax);
+            for (int pp = 0; pp < Q / 2; ++pp) {
+                const int qa = 2 * pp, qb = 2 * pp + 1;
+                const PT *pIa = sI + offI + scol[qa], *pIb = sI + offI + scol[qb];
+                const PT2 *pGa = sG + offI + scol[qa], *pGb = sG + offI + scol[qb];
+                int oa = min(srow[qa], pw - 1) * swI, ob = min(srow[qb], pw - 1) * swI;
+                float2 ga0 = f2(pGa[oa]), ga1 = f2(pGa[oa + 1]), gb0 = f2(pGb[ob]), gb1 = f2(pGb[ob + 1]);
+                fx2 a0 = pk(f1(pIa[oa]), f1(pIb[ob])), a1 = pk(f1(pIa[oa + 1]), f1(pIb[ob + 1]));
+                fx2 hI = fma2(AX, sub2(a1, a0), a0);
+                a0 = pk(ga0.x, gb0.x); a1 = pk(ga1.x, gb1.x);
+                fx2 hX = fma2(AX, sub2(a1, a0), a0);
+                a0 = pk(ga0.y, gb0.y); a1 = pk(ga1.y, gb1.y);
+                fx2 hY = fma2(AX, sub2(a1, a0), a0);
 #pragma unroll
-            for (int e = 0; e < SEG; ++e) {
-                const int m = q * SEG + e, rr = srow[q] + e;
-                o = min(rr + 1, pw - 1) * swI;
-                const float hI1 = lerpf(f1(pI[o]), f1(pI[o + 1]), ax);
-                g0 = f2(pG[o]); g1 = f2(pG[o + 1]);
-                const float hX1 = lerpf(g0.x, g1.x, ax), hY1 = lerpf(g0.y, g1.y, ax);
-                const bool ok = rr < ww;
-                const float t = lerpf(hI, hI1, ay), tx = lerpf(hX, hX1, ay), ty = lerpf(hY, hY1, ay);
-                T[m] = ok ? t : 0.f; TX[m] = ok ? tx : 0.f; TY[m] = ok ? ty : 0.f;
-                gxx += TX[m] * TX[m]; gxy += TX[m] * TY[m]; gyy += TY[m] * TY[m];
-                hI = hI1; hX = hX1; hY = hY1;
+                for (int e = 0; e < SEG; ++e) {
+                    const int ra = srow[qa] + e, rb = srow[qb] + e;
+                    oa = min(ra + 1, pw - 1) * swI; ob = min(rb + 1, pw - 1) * swI;
+                    ga0 = f2(pGa[oa]); ga1 = f2(pGa[oa + 1]); gb0 = f2(pGb[ob]); gb1 = f2(pGb[ob + 1]);
+                    a0 = pk(f1(pIa[oa]), f1(pIb[ob])); a1 = pk(f1(pIa[oa + 1]), f1(pIb[ob + 1]));
+                    const fx2 hI1 = fma2(AX, sub2(a1, a0), a0);
+                    a0 = pk(ga0.x, gb0.x); a1 = pk(ga1.x, gb1.x);
+                    const fx2 hX1 = fma2(AX, sub2(a1, a0), a0);
+                    a0 = pk(ga0.y, gb0.y); a1 = pk(ga1.y, gb1.y);
+                    const fx2 hY1 = fma2(AX, sub2(a1, a0), a0);
+                    // samples past the window's last row weigh 0
+                    const fx2 ok = pk(ra < ww ? 1.f : 0.f, rb < ww ? 1.f : 0.f), zero = pk(0.f, 0.f);
+                    const int m = pp * SEG + e;
+                    TT[m] = fma2(ok, fma2(AY, sub2(hI1, hI), hI), zero);
+                    TTX[m] = fma2(ok, fma2(AY, sub2(hX1, hX), hX), zero);
+                    TTY[m] = fma2(ok, fma2(AY, sub2(hY1, hY), hY), zero);
+                    sxx = fma2(TTX[m], TTX[m], sxx); sxy = fma2(TTX[m], TTY[m], sxy); syy = fma2(TTY[m], TTY[m], syy);
+                    hI = hI1; hX = hX1; hY = hY1;
+                }
+            }
+            float u0, u1;
+            upk(sxx, u0, u1); gxx = u0 + u1;
+            upk(sxy, u0, u1); gxy = u0 + u1;
+            upk(syy, u0, u1); gyy = u0 + u1;
+        } else {
+    #pragma unroll
+            for (int q = 0; q < Q; ++q) {
+                const PT *pI = sI + offI + scol[q];
+                const PT2 *pG = sG + offI + scol[q];
+                int o = min(srow[q], pw - 1) * swI;
+                float hI = lerpf(f1(pI[o]), f1(pI[o + 1]), ax);
+                float2 g0 = f2(pG[o]), g1 = f2(pG[o + 1]);
+                float hX = lerpf(g0.x, g1.x, ax), hY = lerpf(g0.y, g1.y, ax);
+    #pragma unroll
+                for (int e = 0; e < SEG; ++e) {
+                    const int m = q * SEG + e, rr = srow[q] + e;
+                    o = min(rr + 1, pw - 1) * swI;
+                    const float hI1 = lerpf(f1(pI[o]), f1(pI[o + 1]), ax);
+                    g0 = f2(pG[o]); g1 = f2(pG[o + 1]);
+                    const float hX1 = lerpf(g0.x, g1.x, ax), hY1 = lerpf(g0.y, g1.y, ax);
+                    const bool ok = rr < ww;
+                    const float t = lerpf(hI, hI1, ay), tx = lerpf(hX, hX1, ay), ty = lerpf(hY, hY1, ay);
+                    T[m] = ok ? t : 0.f; TX[m] = ok ? tx : 0.f; TY[m] = ok ? ty : 0.f;
+                    gxx += TX[m] * TX[m]; gxy += TX[m] * TY[m]; gyy += TY[m] * TY[m];
+                    hI = hI1; hX = hX1; hY = hY1;
+                }
             }
         }
         group_sum3<WPF>(gxx, gxy, gyy, red, wig, grp);
@@ -226,20 +274,47 @@ __device__ __noinline__ bool lk_track(const StreamDev &D, int sa, int sb, float 
             }
             const PT *sJo = sJ + oy * swJ + ox + offJ;
             float bxs = 0.f, bys = 0.f, unused = 0.f;
+            if constexpr (PAIR) {
+                const fx2 CX = pk(cx, cx), CY = pk(cy, cy);
+                fx2 ax2 = pk(0.f, 0.f), ay2 = ax2;
 #pragma unroll
-            for (int q = 0; q < Q; ++q) {
-                const PT *pJ = sJo + scol[q];
-                int o = min(srow[q], pw - 1) * swJ;
-                float h = lerpf(f1(pJ[o]), f1(pJ[o + 1]), cx);
+                for (int pp = 0; pp < Q / 2; ++pp) {
+                    const int qa = 2 * pp, qb = 2 * pp + 1;
+                    const PT *pJa = sJo + scol[qa], *pJb = sJo + scol[qb];
+                    int oa = min(srow[qa], pw - 1) * swJ, ob = min(srow[qb], pw - 1) * swJ;
+                    fx2 a0 = pk(f1(pJa[oa]), f1(pJb[ob])), a1 = pk(f1(pJa[oa + 1]), f1(pJb[ob + 1]));
+                    fx2 h = fma2(CX, sub2(a1, a0), a0);
 #pragma unroll
-                for (int e = 0; e < SEG; ++e) {
-                    const int m = q * SEG + e;
-                    o = min(srow[q] + e + 1, pw - 1) * swJ;
-                    const float h1 = lerpf(f1(pJ[o]), f1(pJ[o + 1]), cx);
-                    const float err = T[m] - lerpf(h, h1, cy);       // samples outside the window have TX = TY = 0
-                    bxs += err * TX[m];
-                    bys += err * TY[m];
-                    h = h1;
+                    for (int e = 0; e < SEG; ++e) {
+                        oa = min(srow[qa] + e + 1, pw - 1) * swJ; ob = min(srow[qb] + e + 1, pw - 1) * swJ;
+                        a0 = pk(f1(pJa[oa]), f1(pJb[ob])); a1 = pk(f1(pJa[oa + 1]), f1(pJb[ob + 1]));
+                        const fx2 h1 = fma2(CX, sub2(a1, a0), a0);
+                        const int m = pp * SEG + e;
+                        const fx2 err = sub2(TT[m], fma2(CY, sub2(h1, h), h));   // outside the window Tx = Ty = 0
+                        ax2 = fma2(err, TTX[m], ax2);
+                        ay2 = fma2(err, TTY[m], ay2);
+                        h = h1;
+                    }
+                }
+                float u0, u1;
+                upk(ax2, u0, u1); bxs = u0 + u1;
+                upk(ay2, u0, u1); bys = u0 + u1;
+            } else {
+    #pragma unroll
+                for (int q = 0; q < Q; ++q) {
+                    const PT *pJ = sJo + scol[q];
+                    int o = min(srow[q], pw - 1) * swJ;
+                    float h = lerpf(f1(pJ[o]), f1(pJ[o + 1]), cx);
+    #pragma unroll
+                    for (int e = 0; e < SEG; ++e) {
+                        const int m = q * SEG + e;
+                        o = min(srow[q] + e + 1, pw - 1) * swJ;
+                        const float h1 = lerpf(f1(pJ[o]), f1(pJ[o + 1]), cx);
+                        const float err = T[m] - lerpf(h, h1, cy);       // samples outside the window have TX = TY = 0
+                        bxs += err * TX[m];
+                        bys += err * TY[m];
+                        h = h1;
+                    }
                 }
             }
             if (WPF == 1) { bxs = wsum(bxs); bys = wsum(bys); }

@@ -52,50 +52,16 @@ __device__ __forceinline__ void cp_async16(void *smem, const void *gmem, int src
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait1() { asm volatile("cp.async.wait_group 1;\n" ::: "memory"); }
 
-// Packed pair of FP32 values (lane 0 in the low word) and the f32x2 forms.
-typedef unsigned long long f2;
-__device__ __forceinline__ f2 pk(float lo, float hi)
-{
-    f2 r;
-    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(lo), "f"(hi));
-    return r;
-}
-__device__ __forceinline__ void upk(f2 v, float &lo, float &hi) { asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(v)); }
-__device__ __forceinline__ f2 fma2(f2 a, f2 b, f2 c)
-{
-    f2 d;
-    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
-    return d;
-}
-__device__ __forceinline__ f2 add2(f2 a, f2 b)
-{
-    f2 d;
-    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
-    return d;
-}
-__device__ __forceinline__ f2 add2_rd(f2 a, f2 b)
-{
-    f2 d;
-    asm("add.rm.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
-    return d;
-}
-__device__ __forceinline__ f2 sub2(f2 a, f2 b)
-{
-    f2 d;
-    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
-    return d;
-}
-
 // Bilinear values of two pixels from biased taps (2^23 + byte), rounded half
 // up; the low byte of each lane's bits is the result.  The lerps are the fma
 // sequence of the plain form (differences of biased taps are exact, and the
 // unbiased corner is tap - 2^23).
-__device__ __forceinline__ f2 lerp2(f2 ax, f2 ay, f2 b00, f2 b01, f2 b10, f2 b11)
+__device__ __forceinline__ fx2 lerp2(fx2 ax, fx2 ay, fx2 b00, fx2 b01, fx2 b10, fx2 b11)
 {
-    const f2 t23 = pk(kTwo23, kTwo23), half = pk(0.5f, 0.5f);
-    const f2 top = fma2(ax, sub2(b01, b00), sub2(b00, t23));
-    const f2 bot = fma2(ax, sub2(b11, b10), sub2(b10, t23));
-    const f2 v = fma2(ay, sub2(bot, top), top);
+    const fx2 t23 = pk(kTwo23, kTwo23), half = pk(0.5f, 0.5f);
+    const fx2 top = fma2(ax, sub2(b01, b00), sub2(b00, t23));
+    const fx2 bot = fma2(ax, sub2(b11, b10), sub2(b10, t23));
+    const fx2 v = fma2(ay, sub2(bot, top), top);
     return add2_rd(add2(v, half), t23);
 }
 
@@ -226,8 +192,8 @@ __device__ __forceinline__ void warp_staged(const uint8_t *__restrict__ sb, cons
     const float xf0 = (float)x, fw = (float)w, fh = (float)h;
     const int base = -j.by0 * WS_BYTES - j.b0;
     const float m0 = j.M[0], m1 = j.M[1], m2 = j.M[2], m3 = j.M[3], m4 = j.M[4], m5 = j.M[5];
-    const f2 M0 = pk(m0, m0), M3 = pk(m3, m3), MAG = pk(kFloorMagic, kFloorMagic);
-    const f2 X01 = pk(xf0, __fadd_rn(xf0, 1.f)), X23 = pk(__fadd_rn(xf0, 2.f), __fadd_rn(xf0, 3.f));
+    const fx2 M0 = pk(m0, m0), M3 = pk(m3, m3), MAG = pk(kFloorMagic, kFloorMagic);
+    const fx2 X01 = pk(xf0, __fadd_rn(xf0, 1.f)), X23 = pk(__fadd_rn(xf0, 2.f), __fadd_rn(xf0, 3.f));
     uint8_t *drow = j.dst + (size_t)x * C;
 #pragma unroll 1
     for (int rr = 0; rr < 2; ++rr) {
@@ -235,13 +201,13 @@ __device__ __forceinline__ void warp_staged(const uint8_t *__restrict__ sb, cons
         if (y >= h) break;
         const float yf = (float)y;
         const float qx0 = __fmaf_rn(m1, yf, m2), qy0 = __fmaf_rn(m4, yf, m5);
-        const f2 QX0 = pk(qx0, qx0), QY0 = pk(qy0, qy0);
+        const fx2 QX0 = pk(qx0, qx0), QY0 = pk(qy0, qy0);
         unsigned res[4 * C];
 #pragma unroll
         for (int pp = 0; pp < 2; ++pp) {
-            const f2 qx = fma2(M0, pp ? X23 : X01, QX0), qy = fma2(M3, pp ? X23 : X01, QY0);
-            const f2 rx = add2_rd(qx, MAG), ry = add2_rd(qy, MAG);
-            const f2 ax = sub2(qx, sub2(rx, MAG)), ay = sub2(qy, sub2(ry, MAG));
+            const fx2 qx = fma2(M0, pp ? X23 : X01, QX0), qy = fma2(M3, pp ? X23 : X01, QY0);
+            const fx2 rx = add2_rd(qx, MAG), ry = add2_rd(qy, MAG);
+            const fx2 ax = sub2(qx, sub2(rx, MAG)), ay = sub2(qy, sub2(ry, MAG));
             float q[2][2], rf[2][2];
             upk(qx, q[0][0], q[1][0]); upk(qy, q[0][1], q[1][1]);
             upk(rx, rf[0][0], rf[1][0]); upk(ry, rf[0][1], rf[1][1]);
@@ -264,15 +230,15 @@ __device__ __forceinline__ void warp_staged(const uint8_t *__restrict__ sb, cons
                     a0[e] = __byte_perm(w0[0], w0[1], sel); a1[e] = __byte_perm(w0[1], w0[2], sel);
                     c0[e] = __byte_perm(w1[0], w1[1], sel); c1[e] = __byte_perm(w1[1], w1[2], sel);
                 }
-                const f2 r0 = lerp2(ax, ay, pk(byte_biased<0>(a0[0]), byte_biased<0>(a0[1])),
+                const fx2 r0 = lerp2(ax, ay, pk(byte_biased<0>(a0[0]), byte_biased<0>(a0[1])),
                                     pk(byte_biased<3>(a0[0]), byte_biased<3>(a0[1])),
                                     pk(byte_biased<0>(c0[0]), byte_biased<0>(c0[1])),
                                     pk(byte_biased<3>(c0[0]), byte_biased<3>(c0[1])));
-                const f2 r1 = lerp2(ax, ay, pk(byte_biased<1>(a0[0]), byte_biased<1>(a0[1])),
+                const fx2 r1 = lerp2(ax, ay, pk(byte_biased<1>(a0[0]), byte_biased<1>(a0[1])),
                                     pk(byte_biased<0>(a1[0]), byte_biased<0>(a1[1])),
                                     pk(byte_biased<1>(c0[0]), byte_biased<1>(c0[1])),
                                     pk(byte_biased<0>(c1[0]), byte_biased<0>(c1[1])));
-                const f2 r2 = lerp2(ax, ay, pk(byte_biased<2>(a0[0]), byte_biased<2>(a0[1])),
+                const fx2 r2 = lerp2(ax, ay, pk(byte_biased<2>(a0[0]), byte_biased<2>(a0[1])),
                                     pk(byte_biased<1>(a1[0]), byte_biased<1>(a1[1])),
                                     pk(byte_biased<2>(c0[0]), byte_biased<2>(c0[1])),
                                     pk(byte_biased<1>(c1[0]), byte_biased<1>(c1[1])));
@@ -284,7 +250,7 @@ __device__ __forceinline__ void warp_staged(const uint8_t *__restrict__ sb, cons
                     for (int c = 0; c < 3; ++c) res[3 * (2 * pp + e) + c] = ok[e] ? __float_as_uint(v[c][e]) : 0u;
             } else {
                 const uint8_t *p0 = sb + o[0], *p1 = sb + o[1];
-                const f2 r0 = lerp2(ax, ay, pk(__uint_as_float(0x4B000000u | p0[0]), __uint_as_float(0x4B000000u | p1[0])),
+                const fx2 r0 = lerp2(ax, ay, pk(__uint_as_float(0x4B000000u | p0[0]), __uint_as_float(0x4B000000u | p1[0])),
                                     pk(__uint_as_float(0x4B000000u | p0[1]), __uint_as_float(0x4B000000u | p1[1])),
                                     pk(__uint_as_float(0x4B000000u | p0[WS_BYTES]), __uint_as_float(0x4B000000u | p1[WS_BYTES])),
                                     pk(__uint_as_float(0x4B000000u | p0[WS_BYTES + 1]),
