@@ -177,13 +177,7 @@ __global__ void __launch_bounds__(STAB_RS_THREADS) k_response(const StreamDev *_
                 for (int q = 0; q < nk; ++q) {
                     if (pos + q < D.cand_cap) D.cand[pos + q] = keys[q];
                     else set_err(st, STAB_ERR_CAPACITY);
-                }
-                // histogram counts, one atomic per distinct bin of the warp
-#pragma unroll
-                for (int q = 0; q < 2; ++q) {
-                    const unsigned bin = q < nk ? (unsigned)(keys[q] >> (32 + STAB_HSHIFT)) : 0xFFFFFFFFu;
-                    const unsigned peers = __match_any_sync(0xffffffffu, bin);
-                    if (q < nk && __ffs(peers) - 1 == lane) atomicAdd(&D.hist[bin], (unsigned)__popc(peers));
+                    atomicAdd(&D.hist[(unsigned)(keys[q] >> (32 + STAB_HSHIFT))], 1u);
                 }
             }
             // shift the row windows
