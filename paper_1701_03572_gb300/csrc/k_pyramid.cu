@@ -190,88 +190,47 @@ __global__ void __launch_bounds__(L0_GROUPS) k_level0(const StreamDev *__restric
 }
 
 // Level l >= 1 from level l-1: REDUCE over a tile of 64 x 16 outputs plus a
-// one-pixel ring (needed for the central differences of this level).  The
-// input footprint of an interior tile is copied with 16-byte cp.async one tile
-// ahead into the other of two buffers, so its load overlaps the previous
-// tile's filtering; border tiles (reflect-101) are staged synchronously.
-__device__ __forceinline__ void rd_cp16(void *sdst, const void *gsrc)
-{
-    const unsigned d = (unsigned)__cvta_generic_to_shared(sdst);
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(d), "l"(gsrc) : "memory");
-}
-
-struct RdTile {
-    const uint8_t *in;
-    int wi, hi, pi, wo, ho, x0, y0, ix0, iy0, b0, nvec, slot, s;
-    bool vec;
-};
-
-template <int IW, int IH>
-__device__ __forceinline__ RdTile rd_tile(const StreamDev *__restrict__ S, const WorkList &wl, int item, int l,
-                                          int slot_ov)
-{
-    RdTile t;
-    t.s = wl_stream(wl, item);
-    const StreamDev &D = S[t.s];
-    const int local = item - __ldg(&wl.prefix[t.s]);
-    t.slot = slot_ov >= 0 ? slot_ov : (int)(D.st->t & 1);
-    t.in = D.u8[t.slot][l - 1];
-    t.wi = D.lw[l - 1]; t.hi = D.lh[l - 1]; t.pi = D.lp[l - 1];
-    t.wo = D.lw[l]; t.ho = D.lh[l];
-    const int tx = (t.wo + STAB_TW - 1) / STAB_TW;
-    t.x0 = (local % tx) * STAB_TW; t.y0 = (local / tx) * STAB_TH;
-    t.ix0 = 2 * t.x0 - 4; t.iy0 = 2 * t.y0 - 4;
-    t.b0 = t.ix0 & ~15;
-    t.nvec = (t.ix0 - t.b0 + IW + 15) >> 4;
-    t.vec = t.ix0 >= 0 && t.iy0 >= 0 && t.ix0 + IW <= t.wi && t.iy0 + IH <= t.hi && t.b0 + t.nvec * 16 <= t.pi;
-    return t;
-}
-
+// one-pixel ring (needed for the central differences of this level).
 template <typename PT>
 __global__ void __launch_bounds__(256) k_pyr_down(const StreamDev *__restrict__ S, WorkList wl, int l, int slot_ov)
 {
     constexpr int OW = STAB_TW + 2, OH = STAB_TH + 2;   // outputs with ring: 66 x 18
     constexpr int IW = 2 * OW + 3, IH = 2 * OH + 3;     // input footprint: 135 x 39
     constexpr int SW = 160;                             // staged row: IW bytes + up to 15 of alignment
-    __shared__ __align__(16) uint8_t sin_[2][IH][SW];
+    __shared__ __align__(16) uint8_t sin_[IH][SW];
     __shared__ uint16_t shs[IH][OW];
     __shared__ uint8_t sout[OH][OW + 2];
-    const int G = gridDim.x;
-    int item = blockIdx.x;
-    if (item < wl.total) {
-        const RdTile t = rd_tile<IW, IH>(S, wl, item, l, slot_ov);
-        if (t.vec)
-            for (int e = threadIdx.x; e < IH * t.nvec; e += blockDim.x) {
-                const int r = e / t.nvec, v = e - r * t.nvec;
-                rd_cp16(&sin_[0][r][16 * v], t.in + (size_t)(t.iy0 + r) * t.pi + t.b0 + 16 * v);
+    for (int item = blockIdx.x; item < wl.total; item += gridDim.x) {
+        const int s = wl_stream(wl, item);
+        const StreamDev &D = S[s];
+        const int local = item - __ldg(&wl.prefix[s]);
+        const int slot = slot_ov >= 0 ? slot_ov : (int)(D.st->t & 1);
+        const uint8_t *in = D.u8[slot][l - 1];
+        const int wi = D.lw[l - 1], hi = D.lh[l - 1], pi = D.lp[l - 1];
+        const int wo = D.lw[l], ho = D.lh[l];
+        const int tx = (wo + STAB_TW - 1) / STAB_TW;
+        const int x0 = (local % tx) * STAB_TW, y0 = (local / tx) * STAB_TH;
+        const int ix0 = 2 * x0 - 4, iy0 = 2 * y0 - 4;
+        // interior tiles: aligned 16-byte row loads (no border reflection needed)
+        const int b0 = ix0 & ~15, off = ix0 - b0, nvec = (off + IW + 15) >> 4;
+        const bool vec = ix0 >= 0 && iy0 >= 0 && ix0 + IW <= wi && iy0 + IH <= hi && b0 + nvec * 16 <= pi;
+        if (vec) {
+            for (int e = threadIdx.x; e < IH * nvec; e += blockDim.x) {
+                const int r = e / nvec, v = e - r * nvec;
+                *reinterpret_cast<uint4 *>(&sin_[r][16 * v]) =
+                    __ldg(reinterpret_cast<const uint4 *>(in + (size_t)(iy0 + r) * pi + b0 + 16 * v));
             }
-    }
-    asm volatile("cp.async.commit_group;\n" ::: "memory");
-    for (int it = 0; item < wl.total; item += G, ++it) {
-        if (item + G < wl.total) {
-            const RdTile t = rd_tile<IW, IH>(S, wl, item + G, l, slot_ov);
-            if (t.vec)
-                for (int e = threadIdx.x; e < IH * t.nvec; e += blockDim.x) {
-                    const int r = e / t.nvec, v = e - r * t.nvec;
-                    rd_cp16(&sin_[(it + 1) & 1][r][16 * v], t.in + (size_t)(t.iy0 + r) * t.pi + t.b0 + 16 * v);
-                }
-        }
-        asm volatile("cp.async.commit_group;\n" ::: "memory");
-        const RdTile t = rd_tile<IW, IH>(S, wl, item, l, slot_ov);
-        const StreamDev &D = S[t.s];
-        uint8_t (*buf)[SW] = sin_[it & 1];
-        if (!t.vec) {
+        } else {
             for (int i = threadIdx.x; i < IH * IW; i += blockDim.x) {
                 int r = i / IW, c = i - r * IW;
-                buf[r][c] = __ldg(t.in + (size_t)reflect101(t.iy0 + r, t.hi) * t.pi + reflect101(t.ix0 + c, t.wi));
+                sin_[r][c] = __ldg(in + (size_t)reflect101(iy0 + r, hi) * pi + reflect101(ix0 + c, wi));
             }
         }
-        asm volatile("cp.async.wait_group 1;\n" ::: "memory");
         __syncthreads();
-        const int so = t.vec ? t.ix0 - t.b0 : 0;
+        const int so = vec ? off : 0;
         for (int i = threadIdx.x; i < IH * OW; i += blockDim.x) {
             int r = i / OW, c = i - r * OW;
-            const uint8_t *q = &buf[r][2 * c + so];
+            const uint8_t *q = &sin_[r][2 * c + so];
             shs[r][c] = (uint16_t)(q[0] + 4 * q[1] + 6 * q[2] + 4 * q[3] + q[4]);
         }
         __syncthreads();
@@ -283,18 +242,18 @@ __global__ void __launch_bounds__(256) k_pyr_down(const StreamDev *__restrict__ 
         }
         __syncthreads();
         const int row = threadIdx.x >> 4, c4 = (threadIdx.x & 15) * 4;
-        const int y = t.y0 + row, x = t.x0 + c4;
-        if (y < t.ho && x < t.wo) {
+        const int y = y0 + row, x = x0 + c4;
+        if (y < ho && x < wo) {
             int v[3][6];
 #pragma unroll
             for (int r = 0; r < 3; ++r) {
-                int sr = clampi(y + r - 1, 0, t.ho - 1) - (t.y0 - 1);
+                int sr = clampi(y + r - 1, 0, ho - 1) - (y0 - 1);
 #pragma unroll
-                for (int c = 0; c < 6; ++c) v[r][c] = sout[sr][clampi(x + c - 1, 0, t.wo - 1) - (t.x0 - 1)];
+                for (int c = 0; c < 6; ++c) v[r][c] = sout[sr][clampi(x + c - 1, 0, wo - 1) - (x0 - 1)];
             }
-            emit4<PT>(D, t.slot, l, x, y, v);
+            emit4<PT>(D, slot, l, x, y, v);
         }
-        __syncthreads();   // the buffers are refilled by the next tiles' copies
+        __syncthreads();
     }
 }
 
