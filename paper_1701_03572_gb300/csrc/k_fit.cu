@@ -172,24 +172,39 @@ __device__ __forceinline__ float4 corrected(float4 m, float4 S, float4 C)
 
 __device__ __forceinline__ float4 mot4(const stab_motion &m) { return make_float4(m.tx, m.ty, m.theta, m.log_scale); }
 
+// Called by the 32 lanes of one warp.  Lane 0 appends C_t; the lanes then load
+// the window's trajectory entries together and every lane sums them in the
+// order k = lo .. t (the offline smoother's order, so both emit the same
+// bits); lane 0 writes the inverse warp.  Returns u (or -1) on every lane.
 __device__ int smooth_step(stab_motion *mring, float4 *cring, long long t, int W, int w, int h, float zoom,
                            float *Minv)
 {
-    const int CR = STAB_CRING;
-    const float4 Cp = t > 0 ? cring[(t - 1) % CR] : make_float4(0.f, 0.f, 0.f, 0.f);
-    const float4 Ct = add4(Cp, mot4(mring[t % CR]));
-    cring[t % CR] = Ct;
+    const int CR = STAB_CRING, lane = threadIdx.x & 31;
+    if (lane == 0) {
+        const float4 Cp = t > 0 ? cring[(t - 1) % CR] : make_float4(0.f, 0.f, 0.f, 0.f);
+        cring[t % CR] = add4(Cp, mot4(mring[t % CR]));
+    }
+    __syncwarp();
     const long long u = t - 1 - W / 2;
     if (u < 0) return -1;
     const long long j = u + 1;
     long long lo = j - (W - 1) / 2;
     if (lo < 0) lo = 0;
-    float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
-    for (long long k = lo; k <= t; ++k) acc = add4(acc, cring[k % CR]);
-    const float cnt = (float)(t - lo + 1);
+    const int n = (int)(t - lo + 1);   // <= W < CR
+    const float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
+    const float4 v0 = lane < n ? cring[(lo + lane) % CR] : z;
+    const float4 v1 = lane + 32 < n ? cring[(lo + lane + 32) % CR] : z;
+    float4 acc = z;
+    for (int k = 0; k < n; ++k) {
+        const float4 src = k < 32 ? v0 : v1;
+        const float4 x = make_float4(__shfl_sync(0xffffffffu, src.x, k & 31), __shfl_sync(0xffffffffu, src.y, k & 31),
+                                     __shfl_sync(0xffffffffu, src.z, k & 31), __shfl_sync(0xffffffffu, src.w, k & 31));
+        acc = add4(acc, x);
+    }
+    const float cnt = (float)n;
     const float4 Sm = make_float4(__fdiv_rn(acc.x, cnt), __fdiv_rn(acc.y, cnt), __fdiv_rn(acc.z, cnt),
                                   __fdiv_rn(acc.w, cnt));
-    inverse_warp(corrected(mot4(mring[j % CR]), Sm, cring[j % CR]), w, h, zoom, Minv);
+    if (lane == 0) inverse_warp(corrected(mot4(mring[j % CR]), Sm, cring[j % CR]), w, h, zoom, Minv);
     return (int)u;
 }
 
@@ -341,10 +356,12 @@ __global__ void __launch_bounds__(512) k_fit(const StreamDev *__restrict__ S, Fi
     if (tid == 0) {
         if (decide) st->hyb_rigid = rigid;
         if (io.out) *io.out = out;
-        if (!io.src) {
-            D.mring[t % STAB_CRING] = out;
-            if (streaming) st->out_frame = smooth_step(D.mring, D.cring, t, D.W, D.w, D.h, D.zoom, D.Minv);
-        }
+        if (!io.src) D.mring[t % STAB_CRING] = out;
+    }
+    if (tid < 32 && !io.src && streaming) {
+        __syncwarp();
+        const int u = smooth_step(D.mring, D.cring, t, D.W, D.w, D.h, D.zoom, D.Minv);
+        if (tid == 0) st->out_frame = u;
     }
 }
 
@@ -514,14 +531,16 @@ __global__ void k_smooth_minv(const float *mprime, int T, int w, int h, float zo
 __global__ void k_smooth_push(const StreamDev *__restrict__ S, long long t, const stab_motion *m, float *Minv,
                               int *ready)
 {
-    if (threadIdx.x != 0 || blockIdx.x != 0) return;
-    const StreamDev &D = S[0];
-    D.mring[t % STAB_CRING] = *m;
+    const StreamDev &D = S[0];   // one warp
+    if (threadIdx.x == 0) D.mring[t % STAB_CRING] = *m;
+    __syncwarp();
     float M[6];
-    int u = smooth_step(D.mring, D.cring, t, D.W, D.w, D.h, D.zoom, M);
-    if (u >= 0)
-        for (int k = 0; k < 6; ++k) Minv[k] = M[k];
-    *ready = u;
+    const int u = smooth_step(D.mring, D.cring, t, D.W, D.w, D.h, D.zoom, M);
+    if (threadIdx.x == 0) {
+        if (u >= 0)
+            for (int k = 0; k < 6; ++k) Minv[k] = M[k];
+        *ready = u;
+    }
 }
 
 __global__ void k_advance(const StreamDev *__restrict__ S, int n)
