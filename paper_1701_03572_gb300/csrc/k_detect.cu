@@ -54,23 +54,35 @@ __global__ void k_begin(const StreamDev *__restrict__ S, int n, long long t_ov, 
     st->tpl = 0;
 }
 
-// One pixel row's bytes at columns x-3 .. x+6 (clamped into the frame; three
-// aligned words when the run lies inside the row).
-__device__ __forceinline__ void rs_pixels(const uint8_t *__restrict__ g, int pitch, int w, int h, int x, int yy,
-                                          bool fast, int (&p)[10])
+// One pixel row's bytes at columns x-3 .. x+6, clamped into the frame.  Inside
+// the row they come from three aligned words (columns x-4 .. x+7), which the
+// caller loads one row ahead (rs_words); near a border they are read singly.
+struct RsWords { unsigned w0, w1, w2; };
+
+__device__ __forceinline__ RsWords rs_words(const uint8_t *__restrict__ g, int pitch, int h, int x, int yy)
 {
-    const uint8_t *row = g + (size_t)clampi(yy, 0, h - 1) * pitch;
+    const unsigned *q = reinterpret_cast<const unsigned *>(g + (size_t)clampi(yy, 0, h - 1) * pitch + x - 4);
+    return RsWords{__ldg(q), __ldg(q + 1), __ldg(q + 2)};
+}
+
+__device__ __forceinline__ void rs_pixels(const uint8_t *__restrict__ g, int pitch, int w, int h, int x, int yy,
+                                          bool fast, RsWords v, int (&p)[10])
+{
     if (fast) {
-        const unsigned *q = reinterpret_cast<const unsigned *>(row + x - 4);
-        const unsigned w0 = __ldg(q), w1 = __ldg(q + 1), w2 = __ldg(q + 2);
-        p[0] = (w0 >> 8) & 255u; p[1] = (w0 >> 16) & 255u; p[2] = w0 >> 24;
-        p[3] = w1 & 255u; p[4] = (w1 >> 8) & 255u; p[5] = (w1 >> 16) & 255u; p[6] = w1 >> 24;
-        p[7] = w2 & 255u; p[8] = (w2 >> 8) & 255u; p[9] = (w2 >> 16) & 255u;
+        p[0] = (v.w0 >> 8) & 255u; p[1] = (v.w0 >> 16) & 255u; p[2] = v.w0 >> 24;
+        p[3] = v.w1 & 255u; p[4] = (v.w1 >> 8) & 255u; p[5] = (v.w1 >> 16) & 255u; p[6] = v.w1 >> 24;
+        p[7] = v.w2 & 255u; p[8] = (v.w2 >> 8) & 255u; p[9] = (v.w2 >> 16) & 255u;
     } else {
+        const uint8_t *row = g + (size_t)clampi(yy, 0, h - 1) * pitch;
 #pragma unroll
         for (int k = 0; k < 10; ++k) p[k] = __ldg(row + clampi(x - 3 + k, 0, w - 1));
     }
 }
+
+// Candidates of a strip are collected in shared memory and appended to the
+// stream's list with one global atomic per block (a full buffer appends the
+// warp's candidates directly).
+constexpr int RS_CAP = 1024;
 
 // Corner response (Eq. 2), NMS and candidate list as barrier-free vertical
 // strips: a thread owns ROI columns x .. x+3 of a 32-row strip and walks its
@@ -84,8 +96,9 @@ __device__ __forceinline__ void rs_pixels(const uint8_t *__restrict__ g, int pit
 __global__ void __launch_bounds__(STAB_RS_THREADS) k_response(const StreamDev *__restrict__ S, WorkList wl, DetIO io)
 {
     __shared__ unsigned smax;
-    __shared__ int s_last;
+    __shared__ int s_last, s_n, s_valid, s_base;
     __shared__ unsigned s_cnt[256];
+    __shared__ unsigned long long s_keys[RS_CAP];
     const int tid = threadIdx.x, lane = tid & 31;
     for (int item = blockIdx.x; item < wl.total; item += gridDim.x) {
         const int s = wl_stream(wl, item);
@@ -105,17 +118,20 @@ __global__ void __launch_bounds__(STAB_RS_THREADS) k_response(const StreamDev *_
         const int y0 = D.roi_y0 + (local / ngx) * STAB_RS_ROWS;
         const int nrows = min(STAB_RS_ROWS, ry1 - y0);
         const bool fast = x >= 4 && x + 8 <= w && ((x | pitch) & 3) == 0 && (reinterpret_cast<uintptr_t>(g) & 3) == 0;
-        if (tid == 0) smax = 0;
+        if (tid == 0) { smax = 0; s_n = 0; s_valid = RS_CAP; }
         __syncthreads();
         int d1[8] = {0}, d2[8] = {0}, s1[8] = {0}, s2[8] = {0};      // Sobel parts of pixel rows py-1, py-2
         int ha1[6] = {0}, hb1[6] = {0}, hc1[6] = {0};                // tensor row sums of row py-2
         int ha2[6] = {0}, hb2[6] = {0}, hc2[6] = {0};                // ... of row py-3
         float l1[6] = {0.f}, l2[6] = {0.f};                          // scores of rows py-3, py-4
         unsigned lmax = 0;
+        RsWords nxt = fast ? rs_words(g, pitch, h, x, y0 - 3) : RsWords{0u, 0u, 0u};
         for (int k = 0; k < nrows + 6; ++k) {
             const int py = y0 - 3 + k;
+            const RsWords cur = nxt;
+            if (fast && k + 1 < nrows + 6) nxt = rs_words(g, pitch, h, x, py + 1);   // next row in flight
             int p[10];
-            rs_pixels(g, pitch, w, h, x, py, fast, p);
+            rs_pixels(g, pitch, w, h, x, py, fast, cur, p);
             int d0[8], s0[8];
 #pragma unroll
             for (int j = 0; j < 8; ++j) {
@@ -162,7 +178,7 @@ __global__ void __launch_bounds__(STAB_RS_THREADS) k_response(const StreamDev *_
                     }
                 }
             }
-            // warp-aggregated append of this row's candidates
+            // warp-aggregated append of this row's candidates to the block's buffer
             if (__any_sync(0xffffffffu, nk > 0)) {
                 int incl = nk;
                 for (int o = 1; o < 32; o <<= 1) {
@@ -171,13 +187,24 @@ __global__ void __launch_bounds__(STAB_RS_THREADS) k_response(const StreamDev *_
                 }
                 const int tot = __shfl_sync(0xffffffffu, incl, 31);
                 int base = 0;
-                if (lane == 31) base = atomicAdd(&st->n_cand, tot);
+                if (lane == 31) base = atomicAdd(&s_n, tot);
                 base = __shfl_sync(0xffffffffu, base, 31);
+                // reservations only grow, so the buffered entries are those below the
+                // first reservation that did not fit
+                const bool full = base + tot > RS_CAP;
+                if (full && lane == 31) {
+                    atomicMin(&s_valid, base);
+                    base = atomicAdd(&st->n_cand, tot);   // this warp's candidates go straight out
+                }
+                if (full) base = __shfl_sync(0xffffffffu, base, 31);
                 const int pos = base + incl - nk;
                 for (int q = 0; q < nk; ++q) {
-                    if (pos + q < D.cand_cap) D.cand[pos + q] = keys[q];
-                    else set_err(st, STAB_ERR_CAPACITY);
-                    atomicAdd(&D.hist[(unsigned)(keys[q] >> (32 + STAB_HSHIFT))], 1u);
+                    if (!full) s_keys[pos + q] = keys[q];
+                    else {
+                        if (pos + q < D.cand_cap) D.cand[pos + q] = keys[q];
+                        else set_err(st, STAB_ERR_CAPACITY);
+                        atomicAdd(&D.hist[(unsigned)(keys[q] >> (32 + STAB_HSHIFT))], 1u);
+                    }
                 }
             }
             // shift the row windows
@@ -189,9 +216,19 @@ __global__ void __launch_bounds__(STAB_RS_THREADS) k_response(const StreamDev *_
                 l2[i] = l1[i]; l1[i] = l0[i];
             }
         }
-        // block max of the score
+        // block max of the score; the buffered candidates go out with one atomic
         for (int o = 16; o; o >>= 1) lmax = max(lmax, __shfl_xor_sync(0xffffffffu, lmax, o));
         if (lane == 0) atomicMax(&smax, lmax);
+        __syncthreads();
+        const int nb = min(s_n, s_valid);
+        if (tid == 0) s_base = nb ? atomicAdd(&st->n_cand, nb) : 0;
+        __syncthreads();
+        for (int i = tid; i < nb; i += blockDim.x) {
+            const unsigned long long key = s_keys[i];
+            if (s_base + i < D.cand_cap) D.cand[s_base + i] = key;
+            else set_err(st, STAB_ERR_CAPACITY);
+            atomicAdd(&D.hist[(unsigned)(key >> (32 + STAB_HSHIFT))], 1u);
+        }
         __syncthreads();
         if (tid == 0) {
             atomicMax(&st->lam_max, smax);

@@ -124,27 +124,60 @@ __device__ __forceinline__ void tile_box(const float M[6], int x0, int y0, int w
     by1 = (int)floorf(mxy) + 2;
 }
 
-__device__ __forceinline__ void make_job(const StreamDev *__restrict__ S, const WorkList &wl, const WarpIO &io,
-                                         int item, WJob &j)
+// Per-stream facts a tile's job needs, gathered once per block into shared
+// memory (batches of up to 64 streams), so that deriving a job reads shared
+// memory only.
+constexpr int WT_MAXS = 64;
+struct WStream {
+    const uint8_t *src;
+    uint8_t *dst;
+    int sp, dp, w, h, C, first, valid;
+    float M[6];
+};
+
+__device__ __forceinline__ WStream stream_facts(const StreamDev *__restrict__ S, const WarpIO &io, const WorkList &wl,
+                                                int s)
 {
-    const int s = wl_stream(wl, item);
     const StreamDev &D = S[s];
-    const int local = item - __ldg(&wl.prefix[s]);
+    WStream f;
+    f.w = D.w; f.h = D.h; f.first = __ldg(&wl.prefix[s]); f.valid = 1;
     const float *Mp;
-    j.mode = 0;
     if (io.src) {
-        j.src = io.src; j.sp = io.sp; j.dst = io.dst; j.dp = io.dp; j.C = io.C; Mp = io.Minv;
+        f.src = io.src; f.sp = io.sp; f.dst = io.dst; f.dp = io.dp; f.C = io.C; Mp = io.Minv;
     } else {
         const int u = D.st->out_frame;
-        if (u < 0) return;
-        j.src = D.ring + (long long)(u % D.ring_len) * D.slot_bytes;
+        f.valid = u >= 0;
+        f.src = D.ring + (long long)(max(u, 0) % D.ring_len) * D.slot_bytes;
         // two output buffers by step parity: the host copy of one overlaps the next step
-        j.sp = D.in_pitch; j.dst = D.out + (long long)(D.st->t & 1) * D.slot_bytes; j.dp = D.out_pitch; j.C = D.C;
+        f.sp = D.in_pitch; f.dst = D.out + (long long)(D.st->t & 1) * D.slot_bytes; f.dp = D.out_pitch; f.C = D.C;
         Mp = D.Minv;
     }
 #pragma unroll
-    for (int k = 0; k < 6; ++k) j.M[k] = Mp[k];
-    j.w = D.w; j.h = D.h;
+    for (int k = 0; k < 6; ++k) f.M[k] = Mp[k];
+    return f;
+}
+
+__device__ __forceinline__ void make_job(const StreamDev *__restrict__ S, const WorkList &wl, const WarpIO &io,
+                                         const WStream *tab, int item, WJob &j)
+{
+    j.mode = 0;
+    WStream f;
+    if (tab) {   // stream of the item by binary search of the first items in shared memory
+        int lo = 0, hi = wl.n - 1;
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (tab[mid].first <= item) lo = mid;
+            else hi = mid - 1;
+        }
+        f = tab[lo];
+    } else {
+        f = stream_facts(S, io, wl, wl_stream(wl, item));
+    }
+    if (!f.valid) return;
+    const int local = item - f.first;
+    j.src = f.src; j.sp = f.sp; j.dst = f.dst; j.dp = f.dp; j.C = f.C; j.w = f.w; j.h = f.h;
+#pragma unroll
+    for (int k = 0; k < 6; ++k) j.M[k] = f.M[k];
     const int tx = (j.w + STAB_TW - 1) / STAB_TW;
     j.x0 = (local % tx) * STAB_TW; j.y0 = (local / tx) * STAB_WTH;
     int bx0, by0, bx1, by1;
@@ -315,13 +348,18 @@ __global__ void __launch_bounds__(256, 4) k_warp(const StreamDev *__restrict__ S
 {
     __shared__ __align__(16) uint8_t sbox[2][WS_BUF];
     __shared__ WJob sjob[3];   // jobs of tiles it, it + 1, it + 2 (slot k % 3), derived by warp 0
+    __shared__ WStream stab[WT_MAXS];
+    const WStream *tab = wl.n <= WT_MAXS ? stab : nullptr;
+    if (tab)
+        for (int s = threadIdx.x; s < wl.n; s += blockDim.x) stab[s] = stream_facts(S, io, wl, s);
+    __syncthreads();
     const int G = gridDim.x;
     int item = blockIdx.x;
     if (threadIdx.x < 32) {
         for (int k = 0; k < 2; ++k) {
             WJob j;
             j.mode = 0;
-            if (item + k * G < wl.total) make_job(S, wl, io, item + k * G, j);
+            if (item + k * G < wl.total) make_job(S, wl, io, tab, item + k * G, j);
             if (threadIdx.x == 0) sjob[k] = j;
         }
     }
@@ -336,7 +374,7 @@ __global__ void __launch_bounds__(256, 4) k_warp(const StreamDev *__restrict__ S
         if (threadIdx.x < 32) {
             WJob j;
             j.mode = 0;
-            if (item + 2 * G < wl.total) make_job(S, wl, io, item + 2 * G, j);
+            if (item + 2 * G < wl.total) make_job(S, wl, io, tab, item + 2 * G, j);
             if (threadIdx.x == 0) sjob[(it + 2) % 3] = j;
         }
         cp_async_wait1();

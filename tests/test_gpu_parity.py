@@ -86,6 +86,25 @@ def test_detect_bit_exact(cfg, K):
     assert np.array_equal(lam.cpu().numpy()[:n[0]], rl)
 
 
+@pytest.mark.parametrize("K", [50, 2048])
+def test_detect_dense_candidates(K):
+    """Uniform noise gives about 7 % strict local maxima, more candidates than a
+    512 x 32 strip's shared buffer holds (1024), so some warps append theirs
+    directly: the candidate count and the corner list still match."""
+    rng = np.random.default_rng(123)
+    w, h = 1100, 200
+    g = rng.integers(0, 256, (h, w), dtype=np.uint8)
+    ctx = S.Context(w, h, _params(max_corners=K, levels=3))
+    pts, lam, n = ctx.detect(_cuda(g))
+    torch.cuda.synchronize()
+    rp, rl, nc = O.detect(g, O.roi_of(w, h), K)
+    n = n.cpu().numpy()
+    assert nc > 1024 and n[0] == len(rp) and n[1] == nc
+    assert np.array_equal(pts.cpu().numpy()[:n[0]], rp)
+    assert np.array_equal(lam.cpu().numpy()[:n[0]], rl)
+    assert ctx.sync() == 0
+
+
 def test_detect_ties_flat_and_tiny_k():
     w, h = 96, 80
     img = np.full((h, w), 40, np.uint8)
