@@ -45,8 +45,10 @@ FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
 # (7) + residual (1) + b accumulation (2 FMA = 4) = 12.
 LK_FLOP_TEMPLATE, LK_FLOP_ITER = 27, 12
 # DRAM traffic per launch of the dominant kernel from an ncu capture
-# (profiles/); used only while the kernel source is unchanged.
-TRAFFIC = {}
+# (profiles/lk_dram_16x1080p.md: dram__bytes_read.sum + dram__bytes_write.sum
+# of one launch on this workload, 16 streams); used only while the kernel
+# source is unchanged.
+TRAFFIC = {"lk": {"file": "k_lk.cu", "sha": "8e5fe466ad942f07", "bytes_per_launch": 190478592 + 3550208}}
 
 
 def config_dict(streams):
