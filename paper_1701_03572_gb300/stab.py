@@ -370,7 +370,7 @@ class Batch:
     def autotune(self, cache_path: str | None = None, stream=None):
         """Pick the fastest tracker variant; returns (variant, {variant: ms})."""
         v = C.c_int(-1)
-        ms = (C.c_float * 8)()
+        ms = (C.c_float * 8)(*([-1.0] * 8))      # entries of variants that do not exist stay -1
         self._chk(lib().stab_batch_autotune(self._h, cache_path.encode() if cache_path else None, C.byref(v), ms,
                                             _s(stream)), "stab_batch_autotune")
         return v.value, {k: ms[k] for k in range(8) if ms[k] >= 0}
