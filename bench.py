@@ -350,6 +350,23 @@ def run_plain(S, clip, ring, steps, dev):
         t += 1
     torch.cuda.synchronize()
     stream = torch.cuda.current_stream()
+    # pick the tracker variant for a single stream (few features per SM favour two
+    # warps per feature), timing a few frames of each
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    tune = {}
+    for v in range(5):
+        ctx.set_lk_variant(v)
+        frame_step(t)
+        t += 1
+        e0.record(stream)
+        for _ in range(6):
+            frame_step(t)
+            t += 1
+        e1.record(stream)
+        torch.cuda.synchronize()
+        tune[v] = e0.elapsed_time(e1) / 6
+    best = min(tune, key=tune.get)
+    ctx.set_lk_variant(best)
     ev = [torch.cuda.Event(enable_timing=True) for _ in range(steps + 1)]
     ev[0].record(stream)
     for k in range(steps):
@@ -363,7 +380,8 @@ def run_plain(S, clip, ring, steps, dev):
     lat = sorted(ms)
     return {"value": round(steps / (tot / 1e3), 1), "unit": "frames/s", "p50_ms": round(lat[len(lat) // 2], 4),
             "p99_ms": round(lat[min(len(lat) - 1, int(math.ceil(0.99 * len(lat))) - 1)], 4),
-            "config": "1 stream 1920x1080 RGB, FP32 planes, single-stream calls (no graph)", "frames": steps}
+            "config": "1 stream 1920x1080 RGB, FP32 planes, single-stream calls (no graph)", "frames": steps,
+            "lk_variant": best, "lk_variant_frame_ms": {str(k): round(v, 4) for k, v in tune.items()}}
 
 
 def run_e2e(S, batch, clips, offs, ring, steps, B):
