@@ -131,7 +131,7 @@ __device__ __forceinline__ float lerpf(float a, float b, float f) { return fmaf(
 // one copy of its unrolled body keeps the instruction working set small.
 template <typename PT, int NS, int RC, int WPF>
 __device__ __noinline__ bool lk_track(const StreamDev &D, int sa, int sb, float ux, float uy, float &vx, float &vy, int &iters,
-                         int &tpl, unsigned char *gbase, int bI, int bJ, float *red, int tig, int grp)
+                         int &tpl, PT *sI, typename Plane2<PT>::type *sG, PT *sJ, float *red, int tig, int grp)
 {
     typedef typename Plane2<PT>::type PT2;
     constexpr int NT = 32 * WPF;
@@ -155,40 +155,9 @@ __device__ __noinline__ bool lk_track(const StreamDev &D, int sa, int sb, float 
     constexpr int NP = PAIR ? NS / 2 : 1;
     float T[PAIR ? 1 : NS], TX[PAIR ? 1 : NS], TY[PAIR ? 1 : NS];
     fx2 TT[NP], TTX[NP], TTY[NP];
-    // Two patch buffers per group: level l works in buffer (L-1-l) & 1 while the
-    // next level's I and (Ix, Iy) patches (which depend on the feature only) and
-    // its next-frame patch (placed around twice the current guess; a window that
-    // ends up outside the margin is re-staged by the iteration loop) stream into
-    // the other.
-    const int bbuf = 3 * bI + bJ;
-    int offI = 0, offJ = 0, jx0 = 0, jy0 = 0;
-    bool jin = false;
-    // stage level l of the track into buffer b around the guess (g0x, g0y)
-    auto stage_level = [&](int l, int b, float g0x, float g0y) {
-        const int wl = D.lw[l], hl = D.lh[l], p = D.lp[l];
-        const float sc = __int_as_float((127 - l) << 23);   // 2^-l
-        const float px = ux * sc, py = uy * sc;
-        const int ix = (int)floorf(fminf(fmaxf(px, -64.f), (float)wl + 64.f)) - r;
-        const int iy = (int)floorf(fminf(fmaxf(py, -64.f), (float)hl + 64.f)) - r;
-        const bool inside = ix >= 0 && ix + ww <= wl - 1 && iy >= 0 && iy + ww <= hl - 1;
-        jx0 = (int)floorf(fminf(fmaxf(px + g0x, -64.f), (float)wl + 64.f)) - r - LK_MARGIN;
-        jy0 = (int)floorf(fminf(fmaxf(py + g0y, -64.f), (float)hl + 64.f)) - r - LK_MARGIN;
-        jin = jx0 >= 0 && jx0 + pj - 1 <= wl - 1 && jy0 >= 0 && jy0 + pj - 1 <= hl - 1;
-        unsigned char *bb = gbase + b * bbuf;
-        offI = stage<PT, NT>(reinterpret_cast<const PT *>(D.pI[sa][l]), p, wl, hl, ix, iy, pw, swI, inside,
-                             reinterpret_cast<PT *>(bb), tig);
-        stage<PT2, NT>(reinterpret_cast<const PT2 *>(D.pG[sa][l]), p, wl, hl, ix, iy, pw, swI, inside,
-                       reinterpret_cast<PT2 *>(bb + bI), tig);
-        offJ = stage<PT, NT>(reinterpret_cast<const PT *>(D.pI[sb][l]), p, wl, hl, jx0, jy0, pj, swJ, jin,
-                             reinterpret_cast<PT *>(bb + 3 * bI), tig);
-    };
-    group_sync<WPF>(grp);
-    stage_level(D.L - 1, 0, 0.f, 0.f);
     for (int l = D.L - 1; l >= 0; --l) {
-        const int buf = (D.L - 1 - l) & 1;
-        const PT *sI = reinterpret_cast<const PT *>(gbase + buf * bbuf);
-        const PT2 *sG = reinterpret_cast<const PT2 *>(gbase + buf * bbuf + bI);
-        PT *sJ = reinterpret_cast<PT *>(gbase + buf * bbuf + 3 * bI);
+        const PT *Ia = reinterpret_cast<const PT *>(D.pI[sa][l]);
+        const PT2 *Ga = reinterpret_cast<const PT2 *>(D.pG[sa][l]);
         const PT *Jb = reinterpret_cast<const PT *>(D.pI[sb][l]);
         const int wl = D.lw[l], hl = D.lh[l], p = D.lp[l];
         const float sc = __int_as_float((127 - l) << 23);   // 2^-l
@@ -197,9 +166,16 @@ __device__ __noinline__ bool lk_track(const StreamDev &D, int sa, int sb, float 
         const float by = fminf(fmaxf(py, -64.f), (float)hl + 64.f);
         const float fx = floorf(bx), fy = floorf(by);
         const float ax = bx - fx, ay = by - fy;
-        const int offIl = offI;
-        int offJl = offJ, jx0l = jx0, jy0l = jy0;
-        bool jinl = jin;
+        const int ix = (int)fx - r, iy = (int)fy - r;
+        const bool inside = ix >= 0 && ix + ww <= wl - 1 && iy >= 0 && iy + ww <= hl - 1;
+        // next frame's patch around the level's initial guess, with a margin
+        int jx0 = (int)floorf(fminf(fmaxf(px + gx, -64.f), (float)wl + 64.f)) - r - LK_MARGIN;
+        int jy0 = (int)floorf(fminf(fmaxf(py + gy, -64.f), (float)hl + 64.f)) - r - LK_MARGIN;
+        bool jin = jx0 >= 0 && jx0 + pj - 1 <= wl - 1 && jy0 >= 0 && jy0 + pj - 1 <= hl - 1;
+        group_sync<WPF>(grp);
+        const int offI = stage<PT, NT>(Ia, p, wl, hl, ix, iy, pw, swI, inside, sI, tig);
+        stage<PT2, NT>(Ga, p, wl, hl, ix, iy, pw, swI, inside, sG, tig);
+        int offJ = stage<PT, NT>(Jb, p, wl, hl, jx0, jy0, pj, swJ, jin, sJ, tig);
         cpa_wait_all();
         group_sync<WPF>(grp);
         float gxx = 0.f, gxy = 0.f, gyy = 0.f;
@@ -209,8 +185,8 @@ __device__ __noinline__ bool lk_track(const StreamDev &D, int sa, int sb, float 
 #pragma unroll
             for (int pp = 0; pp < Q / 2; ++pp) {
                 const int qa = 2 * pp, qb = 2 * pp + 1;
-                const PT *pIa = sI + offIl + scol[qa], *pIb = sI + offIl + scol[qb];
-                const PT2 *pGa = sG + offIl + scol[qa], *pGb = sG + offIl + scol[qb];
+                const PT *pIa = sI + offI + scol[qa], *pIb = sI + offI + scol[qb];
+                const PT2 *pGa = sG + offI + scol[qa], *pGb = sG + offI + scol[qb];
                 int oa = min(srow[qa], pw - 1) * swI, ob = min(srow[qb], pw - 1) * swI;
                 float2 ga0 = f2(pGa[oa]), ga1 = f2(pGa[oa + 1]), gb0 = f2(pGb[ob]), gb1 = f2(pGb[ob + 1]);
                 fx2 a0 = pk(f1(pIa[oa]), f1(pIb[ob])), a1 = pk(f1(pIa[oa + 1]), f1(pIb[ob + 1]));
@@ -247,8 +223,8 @@ __device__ __noinline__ bool lk_track(const StreamDev &D, int sa, int sb, float 
         } else {
     #pragma unroll
             for (int q = 0; q < Q; ++q) {
-                const PT *pI = sI + offIl + scol[q];
-                const PT2 *pG = sG + offIl + scol[q];
+                const PT *pI = sI + offI + scol[q];
+                const PT2 *pG = sG + offI + scol[q];
                 int o = min(srow[q], pw - 1) * swI;
                 float hI = lerpf(f1(pI[o]), f1(pI[o + 1]), ax);
                 float2 g0 = f2(pG[o]), g1 = f2(pG[o + 1]);
@@ -277,7 +253,6 @@ __device__ __noinline__ bool lk_track(const StreamDev &D, int sa, int sb, float 
             return false;
         }
         const float idet = 1.f / det;
-        if (l > 0) stage_level(l - 1, buf ^ 1, 2.f * gx, 2.f * gy);   // in flight during the iterations
         float nx = 0.f, ny = 0.f;
         for (int it = 0; it < D.max_iters; ++it) {
             const float qx = fminf(fmaxf(px + gx + nx, -64.f), (float)wl + 64.f);
@@ -285,19 +260,19 @@ __device__ __noinline__ bool lk_track(const StreamDev &D, int sa, int sb, float 
             const float fqx = floorf(qx), fqy = floorf(qy);
             const float cx = qx - fqx, cy = qy - fqy;
             const int jx = (int)fqx - r, jy = (int)fqy - r;
-            int ox = jx - jx0l, oy = jy - jy0l;
+            int ox = jx - jx0, oy = jy - jy0;
             if (ox < 0 || ox > 2 * LK_MARGIN || oy < 0 || oy > 2 * LK_MARGIN) {   // same for the whole group
-                jx0l = jx - LK_MARGIN;
-                jy0l = jy - LK_MARGIN;
-                jinl = jx0l >= 0 && jx0l + pj - 1 <= wl - 1 && jy0l >= 0 && jy0l + pj - 1 <= hl - 1;
+                jx0 = jx - LK_MARGIN;
+                jy0 = jy - LK_MARGIN;
+                jin = jx0 >= 0 && jx0 + pj - 1 <= wl - 1 && jy0 >= 0 && jy0 + pj - 1 <= hl - 1;
                 group_sync<WPF>(grp);
-                offJl = stage<PT, NT>(Jb, p, wl, hl, jx0l, jy0l, pj, swJ, jinl, sJ, tig);
+                offJ = stage<PT, NT>(Jb, p, wl, hl, jx0, jy0, pj, swJ, jin, sJ, tig);
                 cpa_wait_all();
                 group_sync<WPF>(grp);
                 ox = LK_MARGIN;
                 oy = LK_MARGIN;
             }
-            const PT *sJo = sJ + oy * swJ + ox + offJl;
+            const PT *sJo = sJ + oy * swJ + ox + offJ;
             float bxs = 0.f, bys = 0.f, unused = 0.f;
             if constexpr (PAIR) {
                 const fx2 CX = pk(cx, cx), CY = pk(cy, cy);
@@ -367,12 +342,7 @@ __host__ __device__ constexpr int lk_bytes_J(int r, int es)
 {
     return lk_al16((2 * r + 2 + 2 * LK_MARGIN) * lk_sw(2 * r + 2 + 2 * LK_MARGIN) * es);
 }
-// Two buffers (the level being tracked and the next level's prefetch) plus the
-// reduction floats.
-__host__ __device__ constexpr int lk_group_bytes(int r, int es)
-{
-    return 2 * (3 * lk_bytes_I(r, es) + lk_bytes_J(r, es)) + 32;
-}
+__host__ __device__ constexpr int lk_group_bytes(int r, int es) { return 3 * lk_bytes_I(r, es) + lk_bytes_J(r, es) + 32; }
 
 template <typename PT, int NS, int RC, int WPF, int MINB>
 __global__ void __launch_bounds__(128, MINB) k_lk(const StreamDev *__restrict__ S, WorkList wl, LkIO io, int rmax)
@@ -383,8 +353,11 @@ __global__ void __launch_bounds__(128, MINB) k_lk(const StreamDev *__restrict__ 
     const int grp = threadIdx.x / NT, tig = threadIdx.x - grp * NT;
     unsigned char *base = lk_smem + grp * lk_group_bytes(rmax, ES);
     // regions sized for rmax; a stream with a smaller radius uses a prefix
-    const int bI = lk_bytes_I(rmax, ES), bJ = lk_bytes_J(rmax, ES);
-    float *red = reinterpret_cast<float *>(base + 2 * (3 * bI + bJ));
+    const int bI = lk_bytes_I(rmax, ES);
+    PT *sI = reinterpret_cast<PT *>(base);
+    PT2 *sG = reinterpret_cast<PT2 *>(base + bI);
+    PT *sJ = reinterpret_cast<PT *>(base + 3 * bI);
+    float *red = reinterpret_cast<float *>(base + 3 * bI + lk_bytes_J(rmax, ES));
     const int ngroups = (gridDim.x * blockDim.x) / NT;
     for (int item = (blockIdx.x * blockDim.x + threadIdx.x) / NT; item < wl.total; item += ngroups) {
         const int s = wl_stream(wl, item);
@@ -402,10 +375,10 @@ __global__ void __launch_bounds__(128, MINB) k_lk(const StreamDev *__restrict__ 
         const float2 u = pts[f];
         int iters = 0, tpl = 0;
         float vx, vy, bx = u.x, by = u.y;
-        const bool ok1 = lk_track<PT, NS, RC, WPF>(D, sp, sp ^ 1, u.x, u.y, vx, vy, iters, tpl, base, bI, bJ, red, tig,
+        const bool ok1 = lk_track<PT, NS, RC, WPF>(D, sp, sp ^ 1, u.x, u.y, vx, vy, iters, tpl, sI, sG, sJ, red, tig,
                                                    grp);
         bool ok2 = false;
-        if (ok1) ok2 = lk_track<PT, NS, RC, WPF>(D, sp ^ 1, sp, vx, vy, bx, by, iters, tpl, base, bI, bJ, red, tig,
+        if (ok1) ok2 = lk_track<PT, NS, RC, WPF>(D, sp ^ 1, sp, vx, vy, bx, by, iters, tpl, sI, sG, sJ, red, tig,
                                                     grp);
         if (!ok1) { bx = u.x; by = u.y; }
         const float ex = bx - u.x, ey = by - u.y;
