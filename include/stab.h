@@ -293,7 +293,7 @@ stab_status stab_batch_step_host(stab_batch *b, const uint8_t *const *frames_hos
  * *variant (may be NULL) receives the choice; ms_out (may be NULL, one float
  * per variant) the measured mean ms per launch (-1 when taken from the cache). */
 stab_status stab_batch_autotune(stab_batch *b, const char *cache_path, int *variant, float *ms_out, void *stream);
-/* Force a tracker variant (0..4) for a batch or a single-stream context. */
+/* Force a tracker variant (0..3) for a batch or a single-stream context. */
 stab_status stab_batch_set_lk_variant(stab_batch *b, int variant);
 stab_status stab_set_lk_variant(stab_ctx *ctx, int variant);
 /* Copy the motions of the last step (n entries) to host memory (synchronous). */

@@ -428,7 +428,6 @@ struct LkKernel {
 //   1: one warp per feature, <= 168 registers (3 blocks / SM)
 //   2: two warps per feature, <= 80 registers (6 blocks / SM)
 //   3: two warps per feature, <= 128 registers (4 blocks / SM)
-//   4: one warp per feature, <= 102 registers (5 blocks / SM)
 // Other radii use the runtime-radius build of variant 0.
 // rcode: the window radius shared by every stream, or minus the largest
 // radius when streams differ (then the runtime-radius build, sized for it).
@@ -440,7 +439,6 @@ void run_variant(int v, const Launch &L, const StreamDev *S, WorkList wl, LkIO i
         case 1: LkKernel<PT, 14, 10, 1, 3>::run(L, S, wl, io, 10); return;
         case 2: LkKernel<PT, 7, 10, 2, 6>::run(L, S, wl, io, 10); return;
         case 3: LkKernel<PT, 7, 10, 2, 4>::run(L, S, wl, io, 10); return;
-        case 4: LkKernel<PT, 14, 10, 1, 5>::run(L, S, wl, io, 10); return;
         default: LkKernel<PT, 14, 10, 1, 4>::run(L, S, wl, io, 10); return;
         }
     }
@@ -455,7 +453,7 @@ void warm_all()
     for (int r = 1; r <= STAB_MAXR; ++r) {
         if (r == 10) {
             LkKernel<PT, 14, 10, 1, 4>::occ(r); LkKernel<PT, 14, 10, 1, 3>::occ(r);
-            LkKernel<PT, 7, 10, 2, 6>::occ(r); LkKernel<PT, 7, 10, 2, 4>::occ(r); LkKernel<PT, 14, 10, 1, 5>::occ(r);
+            LkKernel<PT, 7, 10, 2, 6>::occ(r); LkKernel<PT, 7, 10, 2, 4>::occ(r);
             LkKernel<PT, 14, 0, 1, 4>::occ(r);
         } else if (r < 10) {
             LkKernel<PT, 14, 0, 1, 4>::occ(r);
@@ -467,7 +465,7 @@ void warm_all()
 
 }  // namespace
 
-int lk_variants() { return 5; }
+int lk_variants() { return 4; }
 
 void warm_lk()
 {

@@ -373,7 +373,7 @@ class Batch:
         ms = (C.c_float * 8)(*([-1.0] * 8))      # entries of variants that do not exist stay -1
         self._chk(lib().stab_batch_autotune(self._h, cache_path.encode() if cache_path else None, C.byref(v), ms,
                                             _s(stream)), "stab_batch_autotune")
-        return v.value, {k: ms[k] for k in range(8) if ms[k] >= 0}
+        return v.value, {k: ms[k] for k in range(4) if ms[k] >= 0}
 
     def set_lk_variant(self, v: int):
         self._chk(lib().stab_batch_set_lk_variant(self._h, v), "stab_batch_set_lk_variant")

@@ -134,7 +134,6 @@ def _lk_case(cfg, seed, K, L):
 
 
 @pytest.mark.parametrize("cfg,K,L,variant", [(0, 200, 3, 0), (0, 200, 3, 1), (0, 200, 3, 2), (0, 200, 3, 3),
-                                              (0, 200, 3, 4),
                                               (1, 500, 4, 1), (2, 1000, 5, 1), (2, 1000, 5, 3)])
 def test_lk_parity(cfg, K, L, variant):
     f0, f1, pts, w, h = _lk_case(cfg, 20 + cfg, K, L)
@@ -373,7 +372,7 @@ def test_autotuner_picks_a_variant_and_caches_it(tmp_path):
         b.step()
         if t == 2:
             v, ms = b.autotune(cache)
-            assert 0 <= v < 5 and len(ms) == 5 and all(x > 0 for x in ms.values())
+            assert 0 <= v < 4 and len(ms) == 4 and all(x > 0 for x in ms.values())
             v2, ms2 = b.autotune(cache)          # second call: from the cache, no timing
             assert v2 == v and ms2 == {}
     assert b.sync() == 0
