@@ -38,6 +38,9 @@ struct Pipeline {
     // host-buffer steps: input copies, the step and output copies on three
     // streams chained by events, so copies of neighbouring steps overlap the step
     cudaStream_t hs_in = nullptr, hs_comp = nullptr, hs_out = nullptr;
+    // second branch of the step: detection runs beside the pyramid levels >= 1
+    cudaStream_t side = nullptr;
+    cudaEvent_t ev_fork = nullptr, ev_det = nullptr;
     cudaEvent_t ev_in[2] = {}, ev_comp[4] = {}, ev_out[4] = {}, ev_join = nullptr;
     bool host_mode = false;   // the last step was a host-buffer step
     int wmax = 1;             // largest smoothing window of the batch
@@ -59,8 +62,10 @@ struct Pipeline {
         if (gexec) cudaGraphExecDestroy(gexec);
         if (graph) cudaGraphDestroy(graph);
         if (cap) cudaStreamDestroy(cap);
-        for (cudaStream_t x : {hs_in, hs_comp, hs_out})
+        for (cudaStream_t x : {hs_in, hs_comp, hs_out, side})
             if (x) cudaStreamDestroy(x);
+        for (cudaEvent_t e : {ev_fork, ev_det})
+            if (e) cudaEventDestroy(e);
         for (cudaEvent_t e : {ev_in[0], ev_in[1], ev_comp[0], ev_comp[1], ev_comp[2], ev_comp[3], ev_out[0], ev_out[1],
                               ev_out[2], ev_out[3], ev_join})
             if (e) cudaEventDestroy(e);
@@ -289,16 +294,30 @@ void enqueue_step(Pipeline &pp, cudaStream_t s, Prof *pf = nullptr)
     mark("begin");
     launch_level0(L, pp.prec, pp.ds, pp.wl_l0, FrameSrc{nullptr, 0, 0, 0});
     mark("level0");
-    for (int l = 1; l < pp.Lmax; ++l) {
-        launch_pyr_down(L, pp.prec, pp.ds, pp.wl_pyr[l], l, -1);
-        mark(pyr_names[l]);
+    if (pf) {   // measured one kernel at a time
+        for (int l = 1; l < pp.Lmax; ++l) {
+            launch_pyr_down(L, pp.prec, pp.ds, pp.wl_pyr[l], l, -1);
+            mark(pyr_names[l]);
+        }
+        launch_response(L, pp.ds, pp.wl_resp, DetIO{});
+        mark("response");
+        launch_filter(L, pp.ds, pp.wl_filter);
+        mark("filter");
+        launch_select(L, pp.ds, pp.n, DetIO{});
+        mark("select");
+    } else {
+        // two branches after level 0: corner detection (level 0 only) beside the
+        // pyramid levels >= 1; the tracker waits for both
+        const Launch Ls{pp.side, pp.sms};
+        cudaEventRecord(pp.ev_fork, s);
+        cudaStreamWaitEvent(pp.side, pp.ev_fork, 0);
+        launch_response(Ls, pp.ds, pp.wl_resp, DetIO{});
+        launch_filter(Ls, pp.ds, pp.wl_filter);
+        launch_select(Ls, pp.ds, pp.n, DetIO{});
+        cudaEventRecord(pp.ev_det, pp.side);
+        for (int l = 1; l < pp.Lmax; ++l) launch_pyr_down(L, pp.prec, pp.ds, pp.wl_pyr[l], l, -1);
+        cudaStreamWaitEvent(s, pp.ev_det, 0);
     }
-    launch_response(L, pp.ds, pp.wl_resp, DetIO{});
-    mark("response");
-    launch_filter(L, pp.ds, pp.wl_filter);
-    mark("filter");
-    launch_select(L, pp.ds, pp.n, DetIO{});
-    mark("select");
     launch_lk(L, pp.prec, pp.rcode(), pp.lk_variant, pp.ds, pp.wl_lk, LkIO{});
     mark("lk");
     launch_compact(L, pp.ds, pp.n, CompactIO{});
@@ -549,7 +568,10 @@ stab_status stab_batch_create(int n, const stab_stream_desc *d, int ring, stab_b
     b->C = C;
     stab_status s = build(b->pp, n, w.data(), h.data(), C.data(), P.data(), ring);
     for (int i = 0; i < n; ++i) b->pp.wmax = std::max(b->pp.wmax, P[i].smooth_window);
-    if (s == STAB_OK && cudaStreamCreateWithFlags(&b->pp.cap, cudaStreamNonBlocking) != cudaSuccess)
+    if (s == STAB_OK && (cudaStreamCreateWithFlags(&b->pp.cap, cudaStreamNonBlocking) != cudaSuccess ||
+                         cudaStreamCreateWithFlags(&b->pp.side, cudaStreamNonBlocking) != cudaSuccess ||
+                         cudaEventCreateWithFlags(&b->pp.ev_fork, cudaEventDisableTiming) != cudaSuccess ||
+                         cudaEventCreateWithFlags(&b->pp.ev_det, cudaEventDisableTiming) != cudaSuccess))
         s = cuda_check(b->pp.err, "stream create");
     if (s != STAB_OK) {
         fprintf(stderr, "stab_batch_create: %s\n", b->pp.err.c_str());
