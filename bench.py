@@ -172,9 +172,10 @@ def run_ours(args):
         for s in range(ring):
             batch.input_slot(i, s).copy_(clips[i % len(clips)][(s + offs[i]) % ring])
     stream = torch.cuda.current_stream()
-    # prime the smoother's lookahead (no composed frame before step A + 1),
+    # prime the smoother's lookahead (no composed frame before step A + 2: the
+    # step tracks one frame behind the frame it ingests),
     # pick the tracker variant for this GPU and batch shape, then warm up
-    for _ in range(A + 2):
+    for _ in range(A + 2 + S.BATCH_LAG):
         batch.step(True)
     tuned = None
     if not args.no_autotune:
@@ -438,7 +439,7 @@ def run_mixed(S, dev, steps, warmup):
     for i, (k, off) in enumerate(src):
         for sl in range(ring):
             b.input_slot(i, sl).copy_(clips[k][(sl + off) % ring])
-    for _ in range(W15 // 2 + 2):
+    for _ in range(W15 // 2 + 2 + S.BATCH_LAG):
         b.step(True)
     v, _ = b.autotune(None)
     for _ in range(warmup):

@@ -255,16 +255,20 @@ stab_status stab_warp(stab_ctx *ctx, const uint8_t *src_dev, int src_pitch, uint
 
 /* ---------------------------------------------------------------------- */
 /* Batched multi-stream pipeline (one CUDA-graph launch per frame step).
- * Stream i has its own size, channel count and parameters.  Each step takes
- * frame t of every stream from its input ring slot (t % ring), runs the whole
- * path and writes the stabilised frame u = t - 1 - W_i/2 of stream i to its
- * output buffer (when u >= 0). */
+ * Stream i has its own size, channel count and parameters.  The step that
+ * takes frame t of every stream from its input ring slot (t % ring) builds
+ * frame t's pyramid and, as a parallel branch of the same graph, tracks the
+ * previous transition (frames t-2 -> t-1: detection when due, tracker, fit,
+ * smoothing) and writes the stabilised frame u = t - 2 - W_i/2 of stream i to
+ * its output buffer (when u >= 0).  The motions it reports are those of the
+ * transition t-1; the results equal those of the single-stream calls. */
 typedef struct {
     int w, h, channels;
     stab_params params;
 } stab_stream_desc;
 
-/* ring >= W/2 + 2 frames per stream (0 = that minimum). */
+/* ring >= W/2 + 3 frames per stream (0 = that minimum); with ring >= W/2 + 4
+ * the input copies of stab_batch_step_host run two steps ahead. */
 stab_status stab_batch_create(int n, const stab_stream_desc *descs, int ring, stab_batch **out);
 void stab_batch_destroy(stab_batch *b);
 /* Device pointer of input slot `slot` of stream i (w * channels bytes per
@@ -289,7 +293,8 @@ stab_status stab_batch_step_host(stab_batch *b, const uint8_t *const *frames_hos
  * state with CUDA events and keeps the fastest for later steps.  cache_path
  * (may be NULL) names a JSON file of earlier choices keyed by GPU name and
  * batch shape; a cached choice is applied without timing and new choices are
- * added to it.  Needs at least two steps run; synchronous on `stream`.
+ * added to it.  Needs at least three steps run (the tracker has features from
+ * the third); synchronous on `stream`.
  * *variant (may be NULL) receives the choice; ms_out (may be NULL, one float
  * per variant) the measured mean ms per launch (-1 when taken from the cache). */
 stab_status stab_batch_autotune(stab_batch *b, const char *cache_path, int *variant, float *ms_out, void *stream);

@@ -16,6 +16,10 @@
 #define STAB_MAXL 8          // pyramid levels
 #define STAB_MAXK 2048       // corners per stream
 #define STAB_MAXR 12         // LK window radius
+// Pyramid slots: frame f lives in slot f mod 3, so a batched step can build
+// frame t's pyramid while it tracks frames t-2 -> t-1.
+#define STAB_PSLOTS 3
+__host__ __device__ inline int stab_pslot(long long f) { return (int)(((f % STAB_PSLOTS) + STAB_PSLOTS) % STAB_PSLOTS); }
 #define STAB_CRING 64        // trajectory / motion ring (smoothing window <= 63)
 #define STAB_HBINS 4096      // response histogram: top 12 bits of the (non-negative) float score
 #define STAB_HSHIFT 19
@@ -57,13 +61,14 @@ struct StreamDev {
     int lw[STAB_MAXL], lh[STAB_MAXL], lp[STAB_MAXL];   // level sizes, pitch (elements)
     // parameters
     int r, max_iters, period, min_tracks, min_fit, H, model, dwell, W, prec;
+    int lag;   // tracking runs this many frames behind the frame being ingested (batches: 1)
     float eps2, min_eig, quality, fb2, tau2, zoom;
     unsigned long long seed;
     int roi_x0, roi_y0, roi_x1, roi_y1;
     // pyramids: two slots (frame parity); u8 levels and I / (Ix, Iy) planes
-    uint8_t *u8[2][STAB_MAXL];
-    void *pI[2][STAB_MAXL];   // float or __half
-    void *pG[2][STAB_MAXL];   // float2 or __half2
+    uint8_t *u8[STAB_PSLOTS][STAB_MAXL];
+    void *pI[STAB_PSLOTS][STAB_MAXL];   // float or __half
+    void *pG[STAB_PSLOTS][STAB_MAXL];   // float2 or __half2
     // features and tracks
     float2 *feat;
     float2 *fwd, *back;

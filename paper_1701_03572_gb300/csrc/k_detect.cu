@@ -41,9 +41,10 @@ __global__ void k_begin(const StreamDev *__restrict__ S, int n, long long t_ov, 
     StreamState *st = D.st;
     long long t = t_ov >= 0 ? t_ov : st->t;
     st->t = t;
+    const long long tb = t - D.lag;   // transition tracked by this step: frames tb-1 -> tb
     int due;
     if (force_due) due = 1;
-    else due = (t >= 1) && (st->n_feat == 0 || ((t - 1) % D.period) == 0 || st->n_feat < D.min_tracks);
+    else due = (tb >= 1) && (st->n_feat == 0 || ((tb - 1) % D.period) == 0 || st->n_feat < D.min_tracks);
     st->due = due;
     st->n_cand = 0;
     st->n_sel = 0;
@@ -110,7 +111,7 @@ __global__ void __launch_bounds__(STAB_RS_THREADS) k_response(const StreamDev *_
         const uint8_t *g;
         int pitch;
         if (io.gray) { g = io.gray; pitch = io.pitch; }
-        else { g = D.u8[(int)((st->t - 1) & 1)][0]; pitch = D.lp[0]; }
+        else { g = D.u8[stab_pslot(st->t - D.lag - 1)][0]; pitch = D.lp[0]; }
         const int w = D.w, h = D.h;
         const int rx1 = D.roi_x1, ry1 = D.roi_y1;
         const int ngx = (rx1 - D.roi_x0 + 4 * STAB_RS_THREADS - 1) / (4 * STAB_RS_THREADS);

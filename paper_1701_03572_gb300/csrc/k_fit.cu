@@ -94,7 +94,7 @@ __global__ void __launch_bounds__(1024) k_compact(const StreamDev *__restrict__ 
     const StreamDev &D = S[blockIdx.x];
     StreamState *st = D.st;
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
-    const int n = st->t >= 1 ? st->n_feat : 0;
+    const int n = st->t - D.lag >= 1 ? st->n_feat : 0;
     // two consecutive features per thread (K <= 2048)
     const int f0 = 2 * tid;
     const int k0 = (f0 < n) && D.status[f0], k1 = (f0 + 1 < n) && D.status[f0 + 1];
@@ -305,7 +305,11 @@ __global__ void __launch_bounds__(512) k_fit(const StreamDev *__restrict__ S, Fi
     const StreamDev &D = S[blockIdx.x];
     StreamState *st = D.st;
     const int tid = threadIdx.x;
-    const long long t = io.src ? io.t : st->t;
+    const long long t = io.src ? io.t : st->t - D.lag;   // transition tracked by this step
+    if (!io.src && t < 0) {   // a batch's first step: no transition yet (nothing to record)
+        if (threadIdx.x == 0) st->out_frame = -1;
+        return;
+    }
     int n = io.src ? *io.n : (t >= 1 ? st->n_pairs : 0);
     n = min(max(n, 0), D.K);
     const float2 *src = io.src ? io.src : D.pair_src;

@@ -364,21 +364,22 @@ __global__ void __launch_bounds__(128, MINB) k_lk(const StreamDev *__restrict__ 
         const StreamDev &D = S[s];
         StreamState *st = D.st;
         const int f = item - __ldg(&wl.prefix[s]);
-        int n, sp;
+        int n, sp, sn;
         const float2 *pts;
-        if (io.pts) { n = io.n; pts = io.pts; sp = io.slot_prev; }
+        if (io.pts) { n = io.n; pts = io.pts; sp = io.slot_prev; sn = io.slot_next; }
         else {
-            if (st->t < 1) continue;
-            n = st->n_feat; pts = D.feat; sp = (int)((st->t - 1) & 1);
+            const long long tb = st->t - D.lag;   // frames tb-1 -> tb
+            if (tb < 1) continue;
+            n = st->n_feat; pts = D.feat; sp = stab_pslot(tb - 1); sn = stab_pslot(tb);
         }
         if (f >= n) continue;
         const float2 u = pts[f];
         int iters = 0, tpl = 0;
         float vx, vy, bx = u.x, by = u.y;
-        const bool ok1 = lk_track<PT, NS, RC, WPF>(D, sp, sp ^ 1, u.x, u.y, vx, vy, iters, tpl, sI, sG, sJ, red, tig,
+        const bool ok1 = lk_track<PT, NS, RC, WPF>(D, sp, sn, u.x, u.y, vx, vy, iters, tpl, sI, sG, sJ, red, tig,
                                                    grp);
         bool ok2 = false;
-        if (ok1) ok2 = lk_track<PT, NS, RC, WPF>(D, sp ^ 1, sp, vx, vy, bx, by, iters, tpl, sI, sG, sJ, red, tig,
+        if (ok1) ok2 = lk_track<PT, NS, RC, WPF>(D, sn, sp, vx, vy, bx, by, iters, tpl, sI, sG, sJ, red, tig,
                                                     grp);
         if (!ok1) { bx = u.x; by = u.y; }
         const float ex = bx - u.x, ey = by - u.y;

@@ -163,7 +163,7 @@ __global__ void __launch_bounds__(L0_GROUPS) k_level0(const StreamDev *__restric
             src = ov.ptr; pitch = ov.pitch; C = ov.channels; slot = ov.slot;
         } else {
             long long t = D.st->t;
-            slot = (int)(t & 1);
+            slot = stab_pslot(t);
             src = D.ring + (t % D.ring_len) * D.slot_bytes;
             pitch = D.in_pitch; C = D.C;
         }
@@ -204,7 +204,7 @@ __global__ void __launch_bounds__(256) k_pyr_down(const StreamDev *__restrict__ 
         const int s = wl_stream(wl, item);
         const StreamDev &D = S[s];
         const int local = item - __ldg(&wl.prefix[s]);
-        const int slot = slot_ov >= 0 ? slot_ov : (int)(D.st->t & 1);
+        const int slot = slot_ov >= 0 ? slot_ov : stab_pslot(D.st->t);
         const uint8_t *in = D.u8[slot][l - 1];
         const int wi = D.lw[l - 1], hi = D.lh[l - 1], pi = D.lp[l - 1];
         const int wo = D.lw[l], ho = D.lh[l];

@@ -28,7 +28,7 @@ struct FrameSrc {
 struct LkIO {
     const float2 *pts;
     int n;
-    int slot_prev;
+    int slot_prev, slot_next;
     float2 *fwd, *back;
     float *fb;
     uint8_t *status, *status_fwd;

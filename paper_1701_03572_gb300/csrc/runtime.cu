@@ -76,6 +76,9 @@ struct Pipeline {
 };
 
 inline int up(int v, int a) { return (v + a - 1) / a * a; }
+// A batched step ingests frame t and tracks frames t-2 -> t-1 (the two run as
+// parallel branches of the step's graph), so its tracking lags one frame.
+constexpr int kBatchLag = 1;
 inline int tiles(int w, int h) { return ((w + STAB_TW - 1) / STAB_TW) * ((h + STAB_TH - 1) / STAB_TH); }
 
 stab_status fail(std::string &err, stab_status code, const std::string &msg)
@@ -122,7 +125,7 @@ stab_status check_params(const stab_params &p, int w, int h, std::string &err)
 }
 
 // Build a pipeline; C[i] = channels of stream i's ring frames (0 = no ring).
-stab_status build(Pipeline &pp, int n, const int *w, const int *h, const int *C, const stab_params *P, int ring)
+stab_status build(Pipeline &pp, int n, const int *w, const int *h, const int *C, const stab_params *P, int ring, int lag)
 {
     pp.n = n;
     pp.ring = std::max(ring, 1);
@@ -173,7 +176,8 @@ stab_status build(Pipeline &pp, int n, const int *w, const int *h, const int *C,
             int mx = p.roi_margin_x < 0 ? std::max(w[i] / 10, p.win_radius + 2) : p.roi_margin_x;
             int my = p.roi_margin_y < 0 ? std::max(h[i] / 10, p.win_radius + 2) : p.roi_margin_y;
             D.roi_x0 = mx; D.roi_y0 = my; D.roi_x1 = w[i] - mx; D.roi_y1 = h[i] - my;
-            for (int s = 0; s < 2; ++s)
+            D.lag = lag;
+            for (int s = 0; s < STAB_PSLOTS; ++s)
                 for (int l = 0; l < D.L; ++l) {
                     size_t px = (size_t)D.lp[l] * D.lh[l];
                     D.u8[s][l] = (uint8_t *)take(px);
@@ -292,9 +296,9 @@ void enqueue_step(Pipeline &pp, cudaStream_t s, Prof *pf = nullptr)
     mark(nullptr);
     launch_begin(L, pp.ds, pp.n, -1, 0);
     mark("begin");
-    launch_level0(L, pp.prec, pp.ds, pp.wl_l0, FrameSrc{nullptr, 0, 0, 0});
-    mark("level0");
     if (pf) {   // measured one kernel at a time
+        launch_level0(L, pp.prec, pp.ds, pp.wl_l0, FrameSrc{nullptr, 0, 0, 0});
+        mark("level0");
         for (int l = 1; l < pp.Lmax; ++l) {
             launch_pyr_down(L, pp.prec, pp.ds, pp.wl_pyr[l], l, -1);
             mark(pyr_names[l]);
@@ -305,27 +309,33 @@ void enqueue_step(Pipeline &pp, cudaStream_t s, Prof *pf = nullptr)
         mark("filter");
         launch_select(L, pp.ds, pp.n, DetIO{});
         mark("select");
+        launch_lk(L, pp.prec, pp.rcode(), pp.lk_variant, pp.ds, pp.wl_lk, LkIO{});
+        mark("lk");
+        launch_compact(L, pp.ds, pp.n, CompactIO{});
+        mark("compact");
+        launch_fit(L, pp.ds, pp.n, FitIO{}, 1);
+        mark("fit");
+        launch_warp(L, pp.ds, pp.wl_warp, WarpIO{});
+        mark("warp");
     } else {
-        // two branches after level 0: corner detection (level 0 only) beside the
-        // pyramid levels >= 1; the tracker waits for both
+        // Two branches: the pyramid of frame t (ring slot t, pyramid slot t mod 3)
+        // beside the tracking of frames t-2 -> t-1 (detection on frame t-2 when
+        // due, tracker, fit, smoothing, warp); they share no buffer.
         const Launch Ls{pp.side, pp.sms};
         cudaEventRecord(pp.ev_fork, s);
         cudaStreamWaitEvent(pp.side, pp.ev_fork, 0);
         launch_response(Ls, pp.ds, pp.wl_resp, DetIO{});
         launch_filter(Ls, pp.ds, pp.wl_filter);
         launch_select(Ls, pp.ds, pp.n, DetIO{});
+        launch_lk(Ls, pp.prec, pp.rcode(), pp.lk_variant, pp.ds, pp.wl_lk, LkIO{});
+        launch_compact(Ls, pp.ds, pp.n, CompactIO{});
+        launch_fit(Ls, pp.ds, pp.n, FitIO{}, 1);
+        launch_warp(Ls, pp.ds, pp.wl_warp, WarpIO{});
         cudaEventRecord(pp.ev_det, pp.side);
+        launch_level0(L, pp.prec, pp.ds, pp.wl_l0, FrameSrc{nullptr, 0, 0, 0});
         for (int l = 1; l < pp.Lmax; ++l) launch_pyr_down(L, pp.prec, pp.ds, pp.wl_pyr[l], l, -1);
         cudaStreamWaitEvent(s, pp.ev_det, 0);
     }
-    launch_lk(L, pp.prec, pp.rcode(), pp.lk_variant, pp.ds, pp.wl_lk, LkIO{});
-    mark("lk");
-    launch_compact(L, pp.ds, pp.n, CompactIO{});
-    mark("compact");
-    launch_fit(L, pp.ds, pp.n, FitIO{}, 1);
-    mark("fit");
-    launch_warp(L, pp.ds, pp.wl_warp, WarpIO{});
-    mark("warp");
     launch_advance(L, pp.ds, pp.n);
     mark("advance");
 }
@@ -401,7 +411,7 @@ stab_status stab_create(int w, int h, const stab_params *p, stab_ctx **out)
     if (!p) { stab_default_params(&d); p = &d; }
     stab_ctx *c = new stab_ctx();
     int C0 = 0;
-    stab_status s = build(c->pp, 1, &w, &h, &C0, p, 1);
+    stab_status s = build(c->pp, 1, &w, &h, &C0, p, 1, 0);
     if (s != STAB_OK) {
         fprintf(stderr, "stab_create: %s\n", c->pp.err.c_str());
         delete c;
@@ -476,7 +486,7 @@ stab_status stab_lk(stab_ctx *c, const uint8_t *prev, const uint8_t *next, int p
     if (n > 0) {
         WorkList wl = pp.wl_lk;
         wl.total = n;
-        LkIO io{(const float2 *)pts, n, 0, (float2 *)fwd, (float2 *)back, fb, status, status_fwd};
+        LkIO io{(const float2 *)pts, n, 0, 1, (float2 *)fwd, (float2 *)back, fb, status, status_fwd};
         uint8_t *scratch_status_fwd = nullptr;
         if (!status_fwd) {
             scratch_status_fwd = pp.hs[0].status_fwd;
@@ -494,7 +504,7 @@ stab_status stab_track(stab_ctx *c, const uint8_t *prev, const uint8_t *next, in
     if (pitch < c->pp.hs[0].w * channels) return STAB_ERR_INVALID_ARG;
     CTX_LAUNCH(c, stream);
     const long long t = ++c->t_track;
-    const int sp = (int)((t - 1) & 1), sn = (int)(t & 1);
+    const int sp = stab_pslot(t - 1), sn = stab_pslot(t);
     if (!(flags & STAB_TRACK_CONTINUE) || t == 1) build_pyr(pp, L, prev, pitch, channels, sp);
     build_pyr(pp, L, next, pitch, channels, sn);
     launch_begin(L, pp.ds, 1, t, 0);
@@ -560,13 +570,13 @@ stab_status stab_batch_create(int n, const stab_stream_desc *d, int ring, stab_b
     for (int i = 0; i < n; ++i) {
         if (d[i].channels != 1 && d[i].channels != 3) return STAB_ERR_INVALID_ARG;
         w[i] = d[i].w; h[i] = d[i].h; C[i] = d[i].channels; P[i] = d[i].params;
-        need = std::max(need, P[i].smooth_window / 2 + 2);
+        need = std::max(need, P[i].smooth_window / 2 + 2 + kBatchLag);
     }
     if (ring <= 0) ring = need;
     if (ring < need) return STAB_ERR_INVALID_ARG;
     stab_batch *b = new stab_batch();
     b->C = C;
-    stab_status s = build(b->pp, n, w.data(), h.data(), C.data(), P.data(), ring);
+    stab_status s = build(b->pp, n, w.data(), h.data(), C.data(), P.data(), ring, kBatchLag);
     for (int i = 0; i < n; ++i) b->pp.wmax = std::max(b->pp.wmax, P[i].smooth_window);
     if (s == STAB_OK && (cudaStreamCreateWithFlags(&b->pp.cap, cudaStreamNonBlocking) != cudaSuccess ||
                          cudaStreamCreateWithFlags(&b->pp.side, cudaStreamNonBlocking) != cudaSuccess ||
@@ -766,7 +776,8 @@ stab_status stab_batch_autotune(stab_batch *b, const char *cache_path, int *vari
 {
     if (!b) return STAB_ERR_INVALID_ARG;
     Pipeline &pp = b->pp;
-    if (pp.t_host < 2) return fail(pp.err, STAB_ERR_INVALID_ARG, "autotune needs the batch to have run two steps");
+    if (pp.t_host < 2 + kBatchLag)
+        return fail(pp.err, STAB_ERR_INVALID_ARG, "autotune needs the batch to have run three steps");
     const std::string sig = batch_signature(pp);
     int v = -1;
     const int nv = lk_variants();
@@ -819,8 +830,9 @@ static stab_status host_streams(Pipeline &pp)
 
 // Host-buffer step t: copies of frame t into ring slot t % ring on hs_in, the
 // step on hs_comp, copies of the composed frames on hs_out, chained by events.
-// Slot t % ring is last read by the warp of step t - ring + 1 + W/2, done once
-// step t - 2 is done when ring >= W/2 + 3 (else the copies wait for step t - 1);
+// Slot t % ring is last read by the warp of step t - ring + 2 + W/2 (the warp
+// composes frame t - 2 - W/2), done once step t - 2 is done when
+// ring >= W/2 + 4 (else the copies wait for step t - 1);
 // the output buffer of step t (parity t) was last read by the output copies
 // of step t - 2.  The caller's stream waits for this step's output copies.
 stab_status stab_batch_step_host(stab_batch *b, const uint8_t *const *frames, uint8_t *const *outs, void *stream)
@@ -839,7 +851,7 @@ stab_status stab_batch_step_host(stab_batch *b, const uint8_t *const *frames, ui
         cudaStreamWaitEvent(pp.hs_comp, pp.ev_join, 0);
         cudaStreamWaitEvent(pp.hs_out, pp.ev_join, 0);
     }
-    const long long back = pp.ring >= pp.wmax / 2 + 3 ? 2 : 1;
+    const long long back = pp.ring >= pp.wmax / 2 + kBatchLag + 3 ? 2 : 1;
     if (pp.host_mode && t >= back) cudaStreamWaitEvent(pp.hs_in, pp.ev_comp[(t - back) & 3], 0);
     for (int i = 0; i < pp.n; ++i) {
         const StreamDev &D = pp.hs[i];
@@ -856,7 +868,7 @@ stab_status stab_batch_step_host(stab_batch *b, const uint8_t *const *frames, ui
     if (outs)
         for (int i = 0; i < pp.n; ++i) {
             const StreamDev &D = pp.hs[i];
-            if (outs[i] && t - 1 - pp.P[i].smooth_window / 2 >= 0)
+            if (outs[i] && t - kBatchLag - 1 - pp.P[i].smooth_window / 2 >= 0)
                 cudaMemcpy2DAsync(outs[i], (size_t)D.w * D.C, D.out + (size_t)(t & 1) * D.slot_bytes, D.out_pitch,
                                   (size_t)D.w * D.C, D.h, cudaMemcpyDeviceToHost, pp.hs_out);
         }
@@ -879,7 +891,7 @@ stab_status stab_batch_motions(stab_batch *b, stab_motion *out)
     if (!b || !out) return STAB_ERR_INVALID_ARG;
     Pipeline &pp = b->pp;
     if (cudaStreamSynchronize(pp.last) != cudaSuccess) return cuda_check(pp.err, "stream synchronize");
-    const long long t = pp.t_host - 1;
+    const long long t = pp.t_host - 1 - kBatchLag;   // transition tracked by the last step
     for (int i = 0; i < pp.n; ++i) {
         if (t < 0) { std::memset(&out[i], 0, sizeof(stab_motion)); continue; }
         cudaMemcpy(&out[i], pp.hs[i].mring + (t % STAB_CRING), sizeof(stab_motion), cudaMemcpyDeviceToHost);

@@ -207,7 +207,7 @@ def test_batch_hybrid_and_crop_equal_single_stream_path():
         torch.cuda.synchronize()
         for i in range(len(clips)):
             motions[i].append(b.motions()[i])
-            if t - 1 - 9 // 2 >= 0:
+            if t - S.BATCH_LAG - 1 - 9 // 2 >= 0:
                 outs[i].append(b.output(i).cpu().numpy().copy())
     assert b.sync() == 0
     for i, f in enumerate(clips):
@@ -215,11 +215,12 @@ def test_batch_hybrid_and_crop_equal_single_stream_path():
         p32.precision = 0
         raw, Minv, o = _gpu_clip(f, p32, T)
         m = S.motions_from_raw(raw)
-        for t in range(1, T):
-            assert np.array_equal(np.array(motions[i][t]["m"], np.float32), m["m"][t].astype(np.float32)), (i, t)
+        for t in range(1 + S.BATCH_LAG, T):   # step t tracked the transition t - BATCH_LAG
+            tt = t - S.BATCH_LAG
+            assert np.array_equal(np.array(motions[i][t]["m"], np.float32), m["m"][tt].astype(np.float32)), (i, t)
             keep = ~S.STAB_FLAG_DETECTED          # set by the batched step only
-            assert motions[i][t]["flags"] & keep == m["flags"][t] & keep, (i, t)
-            assert np.float32(motions[i][t]["e_rigid"]) == m["e_rigid"][t]
+            assert motions[i][t]["flags"] & keep == m["flags"][tt] & keep, (i, t)
+            assert np.float32(motions[i][t]["e_rigid"]) == m["e_rigid"][tt]
         oc = o.cpu().numpy()
         for k, frame in enumerate(outs[i]):
             assert np.array_equal(frame, oc[k]), (i, k)

@@ -344,7 +344,7 @@ def test_batch_graph_equals_single_stream_path():
         torch.cuda.synchronize()
         for i in range(len(specs)):
             motions[i].append(b.motions()[i])
-            if t - 1 - 9 // 2 >= 0:
+            if t - S.BATCH_LAG - 1 - 9 // 2 >= 0:
                 outs[i].append(b.output(i).cpu().numpy().copy())
     assert b.sync() == 0
     for i, f in enumerate(clips):
@@ -352,9 +352,10 @@ def test_batch_graph_equals_single_stream_path():
         p32.precision = 0
         raw, Minv, o = _gpu_clip(f, p32, T)
         m = S.motions_from_raw(raw)
-        for t in range(1, T):
-            assert np.array_equal(np.array(motions[i][t]["m"], np.float32), m["m"][t].astype(np.float32)), (i, t)
-            assert motions[i][t]["inliers"] == m["inliers"][t]
+        for t in range(1 + S.BATCH_LAG, T):   # step t tracked the transition t - BATCH_LAG
+            tt = t - S.BATCH_LAG
+            assert np.array_equal(np.array(motions[i][t]["m"], np.float32), m["m"][tt].astype(np.float32)), (i, t)
+            assert motions[i][t]["inliers"] == m["inliers"][tt]
         oc = o.cpu().numpy()
         for k, frame in enumerate(outs[i]):
             assert np.array_equal(frame, oc[k]), (i, k)
@@ -392,10 +393,11 @@ def test_autotuner_picks_a_variant_and_caches_it(tmp_path):
         m = S.motions_from_raw(raw)
         # steps before the switch used the default variant; the last motion is
         # compared only where both paths ran the same variant throughout
+        tt = T - 1 - S.BATCH_LAG
         if v == 1:
-            assert np.array_equal(np.array(mot[i]["m"], np.float32), m["m"][T - 1].astype(np.float32))
+            assert np.array_equal(np.array(mot[i]["m"], np.float32), m["m"][tt].astype(np.float32))
         else:
-            assert np.abs(np.array(mot[i]["m"]) - m["m"][T - 1]).max() < 1e-3
+            assert np.abs(np.array(mot[i]["m"]) - m["m"][tt]).max() < 1e-3
 
 
 def test_batch_host_buffers_pipelined_equal_device_path():
@@ -407,7 +409,7 @@ def test_batch_host_buffers_pipelined_equal_device_path():
     clips = [_clip(0, T, s)["frames"].numpy() for s in (91, 92)]
     params = [_params(max_corners=200, levels=3, smooth_window=W, precision=1),
               _params(max_corners=150, levels=3, smooth_window=W, precision=1, crop_zoom=1.05)]
-    ring = W // 2 + 3
+    ring = W // 2 + S.BATCH_LAG + 3      # large enough for the input copies to run two steps ahead
     bd = S.Batch([(320, 240, 1, p) for p in params], ring=ring)
     ref = [[None] * T for _ in clips]
     for t in range(T):
@@ -415,7 +417,7 @@ def test_batch_host_buffers_pipelined_equal_device_path():
             bd.input_slot(i, t % bd.ring).copy_(_cuda(f[t]))
         bd.step(use_graph=True)
         torch.cuda.synchronize()
-        if t - 1 - W // 2 >= 0:
+        if t - S.BATCH_LAG - 1 - W // 2 >= 0:
             for i in range(len(clips)):
                 ref[i][t] = bd.output(i).cpu().numpy().copy()
     assert bd.sync() == 0
