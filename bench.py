@@ -37,7 +37,7 @@ METRIC = "1080p stabilized frames/s on 1 GB300 (batched vs plain); p99 frame lat
 W, H, CH = 1920, 1080, 3
 STREAMS = 16
 PARAMS = dict(max_corners=1000, levels=5, hypotheses=100, smooth_window=30, model=1)
-RING = 2 * (PARAMS["smooth_window"] // 2 + 2)   # >= W/2 + 2 frames, even for the retracing clip
+RING = 2 * (PARAMS["smooth_window"] // 2 + 2)   # >= W/2 + 5 frames, even for the retracing clip
 FP32_PEAK_NOTE = "152 SMs x 128 FP32 lanes x 2 flop x 2.07 GHz max SM clock"
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
 # LK algorithmic work per window sample: template pass = bilinear I, Ix, Iy
@@ -172,10 +172,11 @@ def run_ours(args):
         for s in range(ring):
             batch.input_slot(i, s).copy_(clips[i % len(clips)][(s + offs[i]) % ring])
     stream = torch.cuda.current_stream()
-    # prime the smoother's lookahead (no composed frame before step A + 2: the
-    # step tracks one frame behind the frame it ingests),
+    # prime the smoother's lookahead (no composed frame before step A + 3: the
+    # step tracks one frame behind the frame it ingests and composes one step
+    # after the fit),
     # pick the tracker variant for this GPU and batch shape, then warm up
-    for _ in range(A + 2 + S.BATCH_LAG):
+    for _ in range(A + 2 + S.BATCH_OUT_LAG):
         batch.step(True)
     tuned = None
     if not args.no_autotune:
@@ -439,7 +440,7 @@ def run_mixed(S, dev, steps, warmup):
     for i, (k, off) in enumerate(src):
         for sl in range(ring):
             b.input_slot(i, sl).copy_(clips[k][(sl + off) % ring])
-    for _ in range(W15 // 2 + 2 + S.BATCH_LAG):
+    for _ in range(W15 // 2 + 2 + S.BATCH_OUT_LAG):
         b.step(True)
     v, _ = b.autotune(None)
     for _ in range(warmup):

@@ -259,15 +259,17 @@ stab_status stab_warp(stab_ctx *ctx, const uint8_t *src_dev, int src_pitch, uint
  * takes frame t of every stream from its input ring slot (t % ring) builds
  * frame t's pyramid and, as a parallel branch of the same graph, tracks the
  * previous transition (frames t-2 -> t-1: detection when due, tracker, fit,
- * smoothing) and writes the stabilised frame u = t - 2 - W_i/2 of stream i to
- * its output buffer (when u >= 0).  The motions it reports are those of the
- * transition t-1; the results equal those of the single-stream calls. */
+ * smoothing); after the pyramid it composes the frame whose smoothed map the
+ * previous step produced and writes the stabilised frame u = t - 3 - W_i/2 of
+ * stream i to its output buffer (when u >= 0).  The motions it reports are
+ * those of the transition t-1; the results equal those of the single-stream
+ * calls. */
 typedef struct {
     int w, h, channels;
     stab_params params;
 } stab_stream_desc;
 
-/* ring >= W/2 + 3 frames per stream (0 = that minimum); with ring >= W/2 + 4
+/* ring >= W/2 + 4 frames per stream (0 = that minimum); with ring >= W/2 + 5
  * the input copies of stab_batch_step_host run two steps ahead. */
 stab_status stab_batch_create(int n, const stab_stream_desc *descs, int ring, stab_batch **out);
 void stab_batch_destroy(stab_batch *b);

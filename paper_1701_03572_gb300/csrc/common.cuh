@@ -47,7 +47,7 @@ struct StreamState {
     unsigned lam_max;     // bits of the largest score (scores >= 0 order like unsigned)
     unsigned bin_lo;      // histogram bin where the top-K starts
     unsigned thr_bits;    // bits of quality * max score
-    int out_frame;        // frame warped by this step (-1 none)
+    int out_frame[2];     // frame to compose, by the parity of the step whose fit set it (-1 none)
     int err;              // first device error (stab_status), 0 if none
     long long iters;      // LK iterations of this step (statistic)
     long long tpl;        // LK template passes (feature x level x direction) of this step
@@ -84,7 +84,7 @@ struct StreamDev {
     // fit / smoothing
     stab_motion *mring;   // STAB_CRING motions
     float4 *cring;        // STAB_CRING trajectory values
-    float *Minv;          // 6 floats: inverse warp of the frame composed this step
+    float *Minv;          // 2 x 8 floats: inverse warps, by the parity of the step whose fit set them
     // batched frames
     uint8_t *ring;
     long long slot_bytes;

@@ -307,7 +307,7 @@ __global__ void __launch_bounds__(512) k_fit(const StreamDev *__restrict__ S, Fi
     const int tid = threadIdx.x;
     const long long t = io.src ? io.t : st->t - D.lag;   // transition tracked by this step
     if (!io.src && t < 0) {   // a batch's first step: no transition yet (nothing to record)
-        if (threadIdx.x == 0) st->out_frame = -1;
+        if (threadIdx.x == 0) st->out_frame[st->t & 1] = -1;
         return;
     }
     int n = io.src ? *io.n : (t >= 1 ? st->n_pairs : 0);
@@ -364,8 +364,10 @@ __global__ void __launch_bounds__(512) k_fit(const StreamDev *__restrict__ S, Fi
     }
     if (tid < 32 && !io.src && streaming) {
         __syncwarp();
-        const int u = smooth_step(D.mring, D.cring, t, D.W, D.w, D.h, D.zoom, D.Minv);
-        if (tid == 0) st->out_frame = u;
+        // this step's slot; the next step's warp composes frame u with it
+        const int slot = (int)(st->t & 1);
+        const int u = smooth_step(D.mring, D.cring, t, D.W, D.w, D.h, D.zoom, D.Minv + 8 * slot);
+        if (tid == 0) st->out_frame[slot] = u;
     }
 }
 

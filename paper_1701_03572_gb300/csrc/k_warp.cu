@@ -145,12 +145,16 @@ __device__ __forceinline__ WStream stream_facts(const StreamDev *__restrict__ S,
     if (io.src) {
         f.src = io.src; f.sp = io.sp; f.dst = io.dst; f.dp = io.dp; f.C = io.C; Mp = io.Minv;
     } else {
-        const int u = D.st->out_frame;
+        // the frame and map the previous step's fit produced (this step's fit is
+        // writing the other slot)
+        const long long t = D.st->t;
+        const int slot = (int)((t - 1) & 1);
+        const int u = t >= 1 ? D.st->out_frame[slot] : -1;
         f.valid = u >= 0;
         f.src = D.ring + (long long)(max(u, 0) % D.ring_len) * D.slot_bytes;
         // two output buffers by step parity: the host copy of one overlaps the next step
         f.sp = D.in_pitch; f.dst = D.out + (long long)(D.st->t & 1) * D.slot_bytes; f.dp = D.out_pitch; f.C = D.C;
-        Mp = D.Minv;
+        Mp = D.Minv + 8 * slot;
     }
 #pragma unroll
     for (int k = 0; k < 6; ++k) f.M[k] = Mp[k];

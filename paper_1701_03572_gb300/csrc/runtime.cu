@@ -77,8 +77,9 @@ struct Pipeline {
 
 inline int up(int v, int a) { return (v + a - 1) / a * a; }
 // A batched step ingests frame t and tracks frames t-2 -> t-1 (the two run as
-// parallel branches of the step's graph), so its tracking lags one frame.
-constexpr int kBatchLag = 1;
+// parallel branches of the step's graph), so its tracking lags one frame; and
+// it composes the frame whose smoothed map the previous step's fit produced.
+constexpr int kBatchLag = 1, kWarpLag = 1;
 inline int tiles(int w, int h) { return ((w + STAB_TW - 1) / STAB_TW) * ((h + STAB_TH - 1) / STAB_TH); }
 
 stab_status fail(std::string &err, stab_status code, const std::string &msg)
@@ -200,7 +201,7 @@ stab_status build(Pipeline &pp, int n, const int *w, const int *h, const int *C,
             D.det_lam = (float *)take(K * 4);
             D.mring = (stab_motion *)take(STAB_CRING * sizeof(stab_motion));
             D.cring = (float4 *)take(STAB_CRING * sizeof(float4));
-            D.Minv = (float *)take(8 * 4);
+            D.Minv = (float *)take(16 * 4);
             D.ring_len = pp.ring;
             D.in_pitch = up(D.w * D.C, 64);
             D.slot_bytes = (long long)D.in_pitch * D.h;
@@ -318,9 +319,10 @@ void enqueue_step(Pipeline &pp, cudaStream_t s, Prof *pf = nullptr)
         launch_warp(L, pp.ds, pp.wl_warp, WarpIO{});
         mark("warp");
     } else {
-        // Two branches: the pyramid of frame t (ring slot t, pyramid slot t mod 3)
-        // beside the tracking of frames t-2 -> t-1 (detection on frame t-2 when
-        // due, tracker, fit, smoothing, warp); they share no buffer.
+        // Two branches that share no buffer: the tracking of frames t-2 -> t-1
+        // (detection on frame t-2 when due, tracker, fit, smoothing), and the
+        // pyramid of frame t (ring slot t, pyramid slot t mod 3) followed by the
+        // composition of the frame whose map the previous step's fit produced.
         const Launch Ls{pp.side, pp.sms};
         cudaEventRecord(pp.ev_fork, s);
         cudaStreamWaitEvent(pp.side, pp.ev_fork, 0);
@@ -330,10 +332,10 @@ void enqueue_step(Pipeline &pp, cudaStream_t s, Prof *pf = nullptr)
         launch_lk(Ls, pp.prec, pp.rcode(), pp.lk_variant, pp.ds, pp.wl_lk, LkIO{});
         launch_compact(Ls, pp.ds, pp.n, CompactIO{});
         launch_fit(Ls, pp.ds, pp.n, FitIO{}, 1);
-        launch_warp(Ls, pp.ds, pp.wl_warp, WarpIO{});
         cudaEventRecord(pp.ev_det, pp.side);
         launch_level0(L, pp.prec, pp.ds, pp.wl_l0, FrameSrc{nullptr, 0, 0, 0});
         for (int l = 1; l < pp.Lmax; ++l) launch_pyr_down(L, pp.prec, pp.ds, pp.wl_pyr[l], l, -1);
+        launch_warp(L, pp.ds, pp.wl_warp, WarpIO{});
         cudaStreamWaitEvent(s, pp.ev_det, 0);
     }
     launch_advance(L, pp.ds, pp.n);
@@ -570,7 +572,7 @@ stab_status stab_batch_create(int n, const stab_stream_desc *d, int ring, stab_b
     for (int i = 0; i < n; ++i) {
         if (d[i].channels != 1 && d[i].channels != 3) return STAB_ERR_INVALID_ARG;
         w[i] = d[i].w; h[i] = d[i].h; C[i] = d[i].channels; P[i] = d[i].params;
-        need = std::max(need, P[i].smooth_window / 2 + 2 + kBatchLag);
+        need = std::max(need, P[i].smooth_window / 2 + 2 + kBatchLag + kWarpLag);
     }
     if (ring <= 0) ring = need;
     if (ring < need) return STAB_ERR_INVALID_ARG;
@@ -830,9 +832,9 @@ static stab_status host_streams(Pipeline &pp)
 
 // Host-buffer step t: copies of frame t into ring slot t % ring on hs_in, the
 // step on hs_comp, copies of the composed frames on hs_out, chained by events.
-// Slot t % ring is last read by the warp of step t - ring + 2 + W/2 (the warp
-// composes frame t - 2 - W/2), done once step t - 2 is done when
-// ring >= W/2 + 4 (else the copies wait for step t - 1);
+// Slot t % ring is last read by the warp of step t - ring + 3 + W/2 (the warp
+// composes frame t - 3 - W/2), done once step t - 2 is done when
+// ring >= W/2 + 5 (else the copies wait for step t - 1);
 // the output buffer of step t (parity t) was last read by the output copies
 // of step t - 2.  The caller's stream waits for this step's output copies.
 stab_status stab_batch_step_host(stab_batch *b, const uint8_t *const *frames, uint8_t *const *outs, void *stream)
@@ -851,7 +853,7 @@ stab_status stab_batch_step_host(stab_batch *b, const uint8_t *const *frames, ui
         cudaStreamWaitEvent(pp.hs_comp, pp.ev_join, 0);
         cudaStreamWaitEvent(pp.hs_out, pp.ev_join, 0);
     }
-    const long long back = pp.ring >= pp.wmax / 2 + kBatchLag + 3 ? 2 : 1;
+    const long long back = pp.ring >= pp.wmax / 2 + kBatchLag + kWarpLag + 3 ? 2 : 1;
     if (pp.host_mode && t >= back) cudaStreamWaitEvent(pp.hs_in, pp.ev_comp[(t - back) & 3], 0);
     for (int i = 0; i < pp.n; ++i) {
         const StreamDev &D = pp.hs[i];
@@ -868,7 +870,7 @@ stab_status stab_batch_step_host(stab_batch *b, const uint8_t *const *frames, ui
     if (outs)
         for (int i = 0; i < pp.n; ++i) {
             const StreamDev &D = pp.hs[i];
-            if (outs[i] && t - kBatchLag - 1 - pp.P[i].smooth_window / 2 >= 0)
+            if (outs[i] && t - kBatchLag - kWarpLag - 1 - pp.P[i].smooth_window / 2 >= 0)
                 cudaMemcpy2DAsync(outs[i], (size_t)D.w * D.C, D.out + (size_t)(t & 1) * D.slot_bytes, D.out_pitch,
                                   (size_t)D.w * D.C, D.h, cudaMemcpyDeviceToHost, pp.hs_out);
         }

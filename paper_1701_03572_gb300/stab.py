@@ -21,6 +21,7 @@ STAB_TRACK_CONTINUE = 1
 STAB_FLAG_SKIPPED, STAB_FLAG_DETECTED, STAB_FLAG_RIGID, STAB_FLAG_DECISION = 1, 2, 4, 8
 MOTION_WORDS = 10          # 4-byte words of one stab_motion record
 BATCH_LAG = 1              # a batched step ingests frame t and tracks frames t-2 -> t-1
+BATCH_OUT_LAG = 2          # ... and composes frame t - BATCH_OUT_LAG - 1 - W/2
 
 
 class StabParams(C.Structure):

@@ -207,7 +207,7 @@ def test_batch_hybrid_and_crop_equal_single_stream_path():
         torch.cuda.synchronize()
         for i in range(len(clips)):
             motions[i].append(b.motions()[i])
-            if t - S.BATCH_LAG - 1 - 9 // 2 >= 0:
+            if t - S.BATCH_OUT_LAG - 1 - 9 // 2 >= 0:
                 outs[i].append(b.output(i).cpu().numpy().copy())
     assert b.sync() == 0
     for i, f in enumerate(clips):

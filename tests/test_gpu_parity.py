@@ -344,7 +344,7 @@ def test_batch_graph_equals_single_stream_path():
         torch.cuda.synchronize()
         for i in range(len(specs)):
             motions[i].append(b.motions()[i])
-            if t - S.BATCH_LAG - 1 - 9 // 2 >= 0:
+            if t - S.BATCH_OUT_LAG - 1 - 9 // 2 >= 0:
                 outs[i].append(b.output(i).cpu().numpy().copy())
     assert b.sync() == 0
     for i, f in enumerate(clips):
@@ -409,7 +409,7 @@ def test_batch_host_buffers_pipelined_equal_device_path():
     clips = [_clip(0, T, s)["frames"].numpy() for s in (91, 92)]
     params = [_params(max_corners=200, levels=3, smooth_window=W, precision=1),
               _params(max_corners=150, levels=3, smooth_window=W, precision=1, crop_zoom=1.05)]
-    ring = W // 2 + S.BATCH_LAG + 3      # large enough for the input copies to run two steps ahead
+    ring = W // 2 + S.BATCH_OUT_LAG + 3  # large enough for the input copies to run two steps ahead
     bd = S.Batch([(320, 240, 1, p) for p in params], ring=ring)
     ref = [[None] * T for _ in clips]
     for t in range(T):
@@ -417,7 +417,7 @@ def test_batch_host_buffers_pipelined_equal_device_path():
             bd.input_slot(i, t % bd.ring).copy_(_cuda(f[t]))
         bd.step(use_graph=True)
         torch.cuda.synchronize()
-        if t - S.BATCH_LAG - 1 - W // 2 >= 0:
+        if t - S.BATCH_OUT_LAG - 1 - W // 2 >= 0:
             for i in range(len(clips)):
                 ref[i][t] = bd.output(i).cpu().numpy().copy()
     assert bd.sync() == 0
