@@ -140,14 +140,23 @@ __device__ __noinline__ bool lk_track(const StreamDev &D, int sa, int sb, float 
     const int pj = pw + 2 * LK_MARGIN;
     const int swI = lk_sw(pw), swJ = lk_sw(pj);
     constexpr int SEG = lk_seg(NS), Q = NS / SEG;
+    // EXACT: segments tile the window's rows exactly, so every row a segment
+    // reads (its SEG + 1 rows) lies in the patch and needs no clamp; a thread
+    // without a segment reads rows 0 .. SEG (finite, staged) with weight 0.
+    constexpr bool EXACT = RC > 0 && (2 * RC + 1) % SEG == 0;
     const int nseg = (ww + SEG - 1) / SEG;
-    int scol[Q], srow[Q];   // this thread's segments (first row ww: none)
+    int scol[Q], srow[Q];   // this thread's segments (sv false: none)
+    bool sv[Q];
 #pragma unroll
     for (int q = 0; q < Q; ++q) {
         const int sgi = tig + NT * q;
+        sv[q] = sgi < ww * nseg;
         scol[q] = sgi % ww;
-        srow[q] = sgi < ww * nseg ? (sgi / ww) * SEG : ww;
+        srow[q] = sv[q] ? (sgi / ww) * SEG : (EXACT ? 0 : ww);
     }
+    // row k of segment q (k = 0 .. SEG) and whether its sample e lies in the window
+    auto srw = [&](int q, int k) { return EXACT ? srow[q] + k : min(srow[q] + k, pw - 1); };
+    auto sok = [&](int q, int e) { return EXACT ? sv[q] : srow[q] + e < ww; };
     float gx = 0.f, gy = 0.f, dx = 0.f, dy = 0.f;
     // An even number of segments per thread runs as pairs (segments 2p, 2p+1
     // in the two lanes of packed f32x2 arithmetic); T, Tx, Ty are kept as pairs.
@@ -187,7 +196,7 @@ __device__ __noinline__ bool lk_track(const StreamDev &D, int sa, int sb, float 
                 const int qa = 2 * pp, qb = 2 * pp + 1;
                 const PT *pIa = sI + offI + scol[qa], *pIb = sI + offI + scol[qb];
                 const PT2 *pGa = sG + offI + scol[qa], *pGb = sG + offI + scol[qb];
-                int oa = min(srow[qa], pw - 1) * swI, ob = min(srow[qb], pw - 1) * swI;
+                int oa = srw(qa, 0) * swI, ob = srw(qb, 0) * swI;
                 float2 ga0 = f2(pGa[oa]), ga1 = f2(pGa[oa + 1]), gb0 = f2(pGb[ob]), gb1 = f2(pGb[ob + 1]);
                 fx2 a0 = pk(f1(pIa[oa]), f1(pIb[ob])), a1 = pk(f1(pIa[oa + 1]), f1(pIb[ob + 1]));
                 fx2 hI = fma2(AX, sub2(a1, a0), a0);
@@ -197,8 +206,7 @@ __device__ __noinline__ bool lk_track(const StreamDev &D, int sa, int sb, float 
                 fx2 hY = fma2(AX, sub2(a1, a0), a0);
 #pragma unroll
                 for (int e = 0; e < SEG; ++e) {
-                    const int ra = srow[qa] + e, rb = srow[qb] + e;
-                    oa = min(ra + 1, pw - 1) * swI; ob = min(rb + 1, pw - 1) * swI;
+                    oa = srw(qa, e + 1) * swI; ob = srw(qb, e + 1) * swI;
                     ga0 = f2(pGa[oa]); ga1 = f2(pGa[oa + 1]); gb0 = f2(pGb[ob]); gb1 = f2(pGb[ob + 1]);
                     a0 = pk(f1(pIa[oa]), f1(pIb[ob])); a1 = pk(f1(pIa[oa + 1]), f1(pIb[ob + 1]));
                     const fx2 hI1 = fma2(AX, sub2(a1, a0), a0);
@@ -207,7 +215,7 @@ __device__ __noinline__ bool lk_track(const StreamDev &D, int sa, int sb, float 
                     a0 = pk(ga0.y, gb0.y); a1 = pk(ga1.y, gb1.y);
                     const fx2 hY1 = fma2(AX, sub2(a1, a0), a0);
                     // samples past the window's last row weigh 0
-                    const fx2 ok = pk(ra < ww ? 1.f : 0.f, rb < ww ? 1.f : 0.f), zero = pk(0.f, 0.f);
+                    const fx2 ok = pk(sok(qa, e) ? 1.f : 0.f, sok(qb, e) ? 1.f : 0.f), zero = pk(0.f, 0.f);
                     const int m = pp * SEG + e;
                     TT[m] = fma2(ok, fma2(AY, sub2(hI1, hI), hI), zero);
                     TTX[m] = fma2(ok, fma2(AY, sub2(hX1, hX), hX), zero);
@@ -225,18 +233,18 @@ __device__ __noinline__ bool lk_track(const StreamDev &D, int sa, int sb, float 
             for (int q = 0; q < Q; ++q) {
                 const PT *pI = sI + offI + scol[q];
                 const PT2 *pG = sG + offI + scol[q];
-                int o = min(srow[q], pw - 1) * swI;
+                int o = srw(q, 0) * swI;
                 float hI = lerpf(f1(pI[o]), f1(pI[o + 1]), ax);
                 float2 g0 = f2(pG[o]), g1 = f2(pG[o + 1]);
                 float hX = lerpf(g0.x, g1.x, ax), hY = lerpf(g0.y, g1.y, ax);
     #pragma unroll
                 for (int e = 0; e < SEG; ++e) {
-                    const int m = q * SEG + e, rr = srow[q] + e;
-                    o = min(rr + 1, pw - 1) * swI;
+                    const int m = q * SEG + e;
+                    o = srw(q, e + 1) * swI;
                     const float hI1 = lerpf(f1(pI[o]), f1(pI[o + 1]), ax);
                     g0 = f2(pG[o]); g1 = f2(pG[o + 1]);
                     const float hX1 = lerpf(g0.x, g1.x, ax), hY1 = lerpf(g0.y, g1.y, ax);
-                    const bool ok = rr < ww;
+                    const bool ok = sok(q, e);
                     const float t = lerpf(hI, hI1, ay), tx = lerpf(hX, hX1, ay), ty = lerpf(hY, hY1, ay);
                     T[m] = ok ? t : 0.f; TX[m] = ok ? tx : 0.f; TY[m] = ok ? ty : 0.f;
                     gxx += TX[m] * TX[m]; gxy += TX[m] * TY[m]; gyy += TY[m] * TY[m];
@@ -281,12 +289,12 @@ __device__ __noinline__ bool lk_track(const StreamDev &D, int sa, int sb, float 
                 for (int pp = 0; pp < Q / 2; ++pp) {
                     const int qa = 2 * pp, qb = 2 * pp + 1;
                     const PT *pJa = sJo + scol[qa], *pJb = sJo + scol[qb];
-                    int oa = min(srow[qa], pw - 1) * swJ, ob = min(srow[qb], pw - 1) * swJ;
+                    int oa = srw(qa, 0) * swJ, ob = srw(qb, 0) * swJ;
                     fx2 a0 = pk(f1(pJa[oa]), f1(pJb[ob])), a1 = pk(f1(pJa[oa + 1]), f1(pJb[ob + 1]));
                     fx2 h = fma2(CX, sub2(a1, a0), a0);
 #pragma unroll
                     for (int e = 0; e < SEG; ++e) {
-                        oa = min(srow[qa] + e + 1, pw - 1) * swJ; ob = min(srow[qb] + e + 1, pw - 1) * swJ;
+                        oa = srw(qa, e + 1) * swJ; ob = srw(qb, e + 1) * swJ;
                         a0 = pk(f1(pJa[oa]), f1(pJb[ob])); a1 = pk(f1(pJa[oa + 1]), f1(pJb[ob + 1]));
                         const fx2 h1 = fma2(CX, sub2(a1, a0), a0);
                         const int m = pp * SEG + e;
@@ -303,12 +311,12 @@ __device__ __noinline__ bool lk_track(const StreamDev &D, int sa, int sb, float 
     #pragma unroll
                 for (int q = 0; q < Q; ++q) {
                     const PT *pJ = sJo + scol[q];
-                    int o = min(srow[q], pw - 1) * swJ;
+                    int o = srw(q, 0) * swJ;
                     float h = lerpf(f1(pJ[o]), f1(pJ[o + 1]), cx);
     #pragma unroll
                     for (int e = 0; e < SEG; ++e) {
                         const int m = q * SEG + e;
-                        o = min(srow[q] + e + 1, pw - 1) * swJ;
+                        o = srw(q, e + 1) * swJ;
                         const float h1 = lerpf(f1(pJ[o]), f1(pJ[o + 1]), cx);
                         const float err = T[m] - lerpf(h, h1, cy);       // samples outside the window have TX = TY = 0
                         bxs += err * TX[m];
