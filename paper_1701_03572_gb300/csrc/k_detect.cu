@@ -21,15 +21,31 @@
 
 namespace {
 
+// Round-to-nearest-even FP32 value of an integer 0 <= v < 2^57, without the
+// 64-bit conversion instruction (GB300 runs it on its narrow FP64 pipe): v >> s
+// keeps v's 26 leading bits and every bit shifted out is ORed into the lowest
+// (sticky) bit, so rounding those 26 bits to 24 picks the same significand as
+// rounding v; the scale by 2^s is then exact.
+__device__ __forceinline__ float u57_to_f32(unsigned long long v)
+{
+    const unsigned hi = (unsigned)(v >> 32), lo = (unsigned)v;
+    const int s = hi ? 38 - __clz(hi) : 0;   // hi < 2^25: s <= 31
+    const unsigned z = __funnelshift_r(lo, hi, s) | (unsigned)((lo & ((1u << s) - 1u)) != 0u);
+    return __fmul_rn(__uint2float_rn(z), __int_as_float((127 + s) << 23));
+}
+
+// a, c <= 9 (4 * 255)^2 < 2^24, so tr < 2^25 converts from 32 bits; det < 2^47
+// and disc <= tr^2 < 2^50 are non-negative (the tensor is a sum of outer
+// products) and exact in 64 bits.
 __device__ __forceinline__ float lambda32(int a, int b, int c)
 {
-    long long tr = (long long)a + c;
+    const int tr = a + c;
     if (tr == 0) return 0.0f;
-    long long det = (long long)a * c - (long long)b * b;
-    long long d = (long long)a - c;
-    long long disc = d * d + 4 * (long long)b * b;
-    float num = __ll2float_rn(2 * det);
-    float den = __fadd_rn(__ll2float_rn(tr), __fsqrt_rn(__ll2float_rn(disc)));
+    const long long det = (long long)a * c - (long long)b * b;
+    const int d = a - c;
+    const long long disc = (long long)d * d + 4 * ((long long)b * b);
+    const float num = __fmul_rn(2.0f, u57_to_f32((unsigned long long)det));
+    const float den = __fadd_rn(__int2float_rn(tr), __fsqrt_rn(u57_to_f32((unsigned long long)disc)));
     return __fdiv_rn(num, den);
 }
 
