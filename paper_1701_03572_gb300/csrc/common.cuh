@@ -33,6 +33,15 @@ __host__ __device__ inline int stab_resp_items(int rw, int rh)
 {
     return ((rw + 4 * STAB_RS_THREADS - 1) / (4 * STAB_RS_THREADS)) * ((rh + STAB_RS_ROWS - 1) / STAB_RS_ROWS);
 }
+// REDUCE work: a warp owns a strip of STAB_PD_ROWS output rows and STAB_PD_COLS
+// output columns (lanes 1..30, 4 columns each; lanes 0 and 31 compute the
+// neighbouring columns only).
+#define STAB_PD_COLS 120
+#define STAB_PD_ROWS 16
+__host__ __device__ inline int stab_pd_items(int w, int h)
+{
+    return ((w + STAB_PD_COLS - 1) / STAB_PD_COLS) * ((h + STAB_PD_ROWS - 1) / STAB_PD_ROWS);
+}
 #define STAB_WTH 32          // warp output tile: 64 x 32 pixels, 256 threads x 2 rows x 4 pixels
 
 // Per-stream mutable state (device memory).

@@ -2,14 +2,14 @@
 // generating kernel [1 4 6 4 1] / 16) and the I / Ix / Iy planes the tracker
 // reads (central differences, replicated border), in FP32 or FP16 storage.
 //
-// Both kernels are persistent grid-stride loops over a work list of 64 x 16
-// tiles spanning every stream of the batch.  A tile is staged in shared memory
-// with its halo; each thread then emits 4 consecutive pixels with vector
-// stores (uchar4 for the u8 level, float4 / uint2 for I, 2 x float4 / uint4
-// for the gradient pair).  The integer blur is exact, so every level is
-// bit-identical to the definition; FP16 holds the integers and half-integers
-// of I and its central differences exactly, so both storages carry the same
-// values.
+// Both kernels are persistent grid-stride loops over a work list of vertical
+// strips spanning every stream of the batch, with no shared memory and no
+// barrier: a thread walks down 4 consecutive columns, keeping the rows it
+// still needs in registers, and emits each row's 4 pixels with vector stores
+// (one word for the u8 level, float4 / uint2 for I, 2 x float4 / uint4 for the
+// gradient pair).  The integer blur is exact, so every level is bit-identical
+// to the definition; FP16 holds the integers and half-integers of I and its
+// central differences exactly, so both storages carry the same values.
 #include "kernels.cuh"
 
 namespace {
@@ -129,12 +129,12 @@ __device__ __forceinline__ void luma_row(const uint8_t *__restrict__ src, int pi
 }
 
 template <typename PT>
-__device__ __forceinline__ void emit_row(const StreamDev &D, int slot, int x, int y, int w, unsigned up, unsigned lo,
-                                         unsigned mid, unsigned hi, unsigned dn)
+__device__ __forceinline__ void emit_row(const StreamDev &D, int slot, int l, int x, int y, int w, unsigned up,
+                                         unsigned lo, unsigned mid, unsigned hi, unsigned dn)
 {
     typedef typename Plane2<PT>::type PT2;
-    const size_t o = (size_t)y * D.lp[0] + x;
-    *reinterpret_cast<unsigned *>(D.u8[slot][0] + o) = mid;
+    const size_t o = (size_t)y * D.lp[l] + x;
+    *reinterpret_cast<unsigned *>(D.u8[slot][l] + o) = mid;
     const int b[6] = {(int)lo, (int)(mid & 255u), (int)((mid >> 8) & 255u), (int)((mid >> 16) & 255u),
                       (int)(mid >> 24), (int)hi};
     float I[4], gx[4], gy[4];
@@ -146,8 +146,8 @@ __device__ __forceinline__ void emit_row(const StreamDev &D, int slot, int x, in
         gx[k] = 0.5f * (float)(r - b[k]);
         gy[k] = 0.5f * (float)((int)((dn >> (8 * k)) & 255u) - (int)((up >> (8 * k)) & 255u));
     }
-    store_I(reinterpret_cast<PT *>(D.pI[slot][0]) + o, I);
-    store_G(reinterpret_cast<PT2 *>(D.pG[slot][0]) + o, gx, gy);
+    store_I(reinterpret_cast<PT *>(D.pI[slot][l]) + o, I);
+    store_G(reinterpret_cast<PT2 *>(D.pG[slot][l]) + o, gx, gy);
 }
 
 template <typename PT>
@@ -182,25 +182,79 @@ __global__ void __launch_bounds__(L0_GROUPS) k_level0(const StreamDev *__restric
         for (int y = y0; y < y1; ++y) {
             unsigned nlo, nmid, nhi;
             luma_row(src, pitch, C, w, x, min(y + 1, h - 1), fast, nlo, nmid, nhi);
-            emit_row<PT>(D, slot, x, y, w, pmid, clo, cmid, chi, nmid);
+            emit_row<PT>(D, slot, 0, x, y, w, pmid, clo, cmid, chi, nmid);
             pmid = cmid;
             clo = nlo; cmid = nmid; chi = nhi;
         }
     }
 }
 
-// Level l >= 1 from level l-1: REDUCE over a tile of 64 x 16 outputs plus a
-// one-pixel ring (needed for the central differences of this level).
-template <typename PT>
-__global__ void __launch_bounds__(256) k_pyr_down(const StreamDev *__restrict__ S, WorkList wl, int l, int slot_ov)
+// Level l >= 1 from level l-1 (REDUCE), as barrier-free strips: a warp owns
+// STAB_PD_ROWS output rows of STAB_PD_COLS columns, a thread 4 columns x ..
+// x+3, and walks down them.  Per input row it loads the bytes 2x-2 .. 2x+8
+// (three aligned loads inside the row; singly with reflect-101 at the row
+// ends) and forms the [1 4 6 4 1] row sums of columns 2x, 2x+2, 2x+4, 2x+6 as
+// two pairs of 16-bit lanes, so every add and multiply-add serves two outputs
+// (a lane's sum is at most 16 * 255 = 4080).  Five such rows give an output row
+// the same way (at most 65280 + 128 per lane), rounded and packed to bytes by
+// one byte permutation.  An output row is emitted (u8, I, Ix, Iy) once the
+// row below it exists; the columns beside a thread's four come from the
+// neighbouring lanes, which is why lanes 0 and 31 emit nothing.
+
+// Input bytes 2x-2 .. 2x+8 of one row: wl holds 2x-2, 2x-1 in bytes 2, 3; w0 and
+// w1 hold 2x .. 2x+7; wr holds 2x+8 in byte 0.
+struct PdWords { unsigned wl, w0, w1, wr; };
+
+__device__ __forceinline__ PdWords pd_words(const uint8_t *__restrict__ row, int x, int wi, bool fast)
 {
-    constexpr int OW = STAB_TW + 2, OH = STAB_TH + 2;   // outputs with ring: 66 x 18
-    constexpr int IW = 2 * OW + 3, IH = 2 * OH + 3;     // input footprint: 135 x 39
-    constexpr int SW = 160;                             // staged row: IW bytes + up to 15 of alignment
-    __shared__ __align__(16) uint8_t sin_[IH][SW];
-    __shared__ uint16_t shs[IH][OW];
-    __shared__ uint8_t sout[OH][OW + 2];
-    for (int item = blockIdx.x; item < wl.total; item += gridDim.x) {
+    PdWords v;
+    if (fast) {
+        const unsigned *q = reinterpret_cast<const unsigned *>(row + 2 * x);
+        const uint2 m = __ldg(reinterpret_cast<const uint2 *>(q));
+        v.wl = __ldg(q - 1); v.w0 = m.x; v.w1 = m.y; v.wr = __ldg(q + 2);
+    } else {
+        unsigned b[11];
+#pragma unroll
+        for (int k = 0; k < 11; ++k) b[k] = __ldg(row + reflect101(2 * x - 2 + k, wi));
+        v.wl = (b[0] << 16) | (b[1] << 24);
+        v.w0 = b[2] | (b[3] << 8) | (b[4] << 16) | (b[5] << 24);
+        v.w1 = b[6] | (b[7] << 8) | (b[8] << 16) | (b[9] << 24);
+        v.wr = b[10];
+    }
+    return v;
+}
+
+// Row sums of columns 2x, 2x+2 (h01: low, high lane) and 2x+4, 2x+6 (h23).
+// With b_k the byte at column 2x+k: e0 = (b0, b2), o0 = (b1, b3), e1 = (b4, b6),
+// o1 = (b5, b7), and the shifted pairs (b-2, b0), (b-1, b1), (b2, b4), (b3, b5),
+// (b6, b8) come from single byte permutations.
+__device__ __forceinline__ void pd_hsum(const PdWords &v, unsigned &h01, unsigned &h23)
+{
+    const unsigned e0 = __byte_perm(v.w0, 0u, 0x4240), o0 = __byte_perm(v.w0, 0u, 0x4341);
+    const unsigned e1 = __byte_perm(v.w1, 0u, 0x4240), o1 = __byte_perm(v.w1, 0u, 0x4341);
+    const unsigned sl = __byte_perm(v.wl, e0, 0x5452), tl = __byte_perm(v.wl, o0, 0x5453);
+    const unsigned sm = __byte_perm(e0, e1, 0x5432), tm = __byte_perm(o0, o1, 0x5432);
+    const unsigned sr = __byte_perm(e1, v.wr, 0x3432);
+    h01 = sl + 4u * (tl + o0) + 6u * e0 + sm;
+    h23 = sm + 4u * (tm + o1) + 6u * e1 + sr;
+}
+
+// (sum of [1 4 6 4 1] x five rows of lane pairs + 128) >> 8 for both pairs,
+// packed as the bytes of columns x .. x+3.
+__device__ __forceinline__ unsigned pd_vsum(unsigned a0, unsigned a1, unsigned a2, unsigned a3, unsigned a4,
+                                            unsigned b0, unsigned b1, unsigned b2, unsigned b3, unsigned b4)
+{
+    const unsigned va = a0 + a4 + 4u * (a1 + a3) + 6u * a2 + 0x00800080u;
+    const unsigned vb = b0 + b4 + 4u * (b1 + b3) + 6u * b2 + 0x00800080u;
+    return __byte_perm(va, vb, 0x7531);
+}
+
+template <typename PT>
+__global__ void __launch_bounds__(128) k_pyr_down(const StreamDev *__restrict__ S, WorkList wl, int l, int slot_ov)
+{
+    const int lane = threadIdx.x & 31;
+    const int nwarps = gridDim.x * (blockDim.x >> 5);
+    for (int item = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); item < wl.total; item += nwarps) {
         const int s = wl_stream(wl, item);
         const StreamDev &D = S[s];
         const int local = item - __ldg(&wl.prefix[s]);
@@ -208,52 +262,38 @@ __global__ void __launch_bounds__(256) k_pyr_down(const StreamDev *__restrict__ 
         const uint8_t *in = D.u8[slot][l - 1];
         const int wi = D.lw[l - 1], hi = D.lh[l - 1], pi = D.lp[l - 1];
         const int wo = D.lw[l], ho = D.lh[l];
-        const int tx = (wo + STAB_TW - 1) / STAB_TW;
-        const int x0 = (local % tx) * STAB_TW, y0 = (local / tx) * STAB_TH;
-        const int ix0 = 2 * x0 - 4, iy0 = 2 * y0 - 4;
-        // interior tiles: aligned 16-byte row loads (no border reflection needed)
-        const int b0 = ix0 & ~15, off = ix0 - b0, nvec = (off + IW + 15) >> 4;
-        const bool vec = ix0 >= 0 && iy0 >= 0 && ix0 + IW <= wi && iy0 + IH <= hi && b0 + nvec * 16 <= pi;
-        if (vec) {
-            for (int e = threadIdx.x; e < IH * nvec; e += blockDim.x) {
-                const int r = e / nvec, v = e - r * nvec;
-                *reinterpret_cast<uint4 *>(&sin_[r][16 * v]) =
-                    __ldg(reinterpret_cast<const uint4 *>(in + (size_t)(iy0 + r) * pi + b0 + 16 * v));
-            }
-        } else {
-            for (int i = threadIdx.x; i < IH * IW; i += blockDim.x) {
-                int r = i / IW, c = i - r * IW;
-                sin_[r][c] = __ldg(in + (size_t)reflect101(iy0 + r, hi) * pi + reflect101(ix0 + c, wi));
-            }
+        const int ncx = (wo + STAB_PD_COLS - 1) / STAB_PD_COLS;
+        const int x = (local % ncx) * STAB_PD_COLS + 4 * (lane - 1), y0 = (local / ncx) * STAB_PD_ROWS;
+        const int y1 = min(y0 + STAB_PD_ROWS, ho);
+        // bytes 2x-4 .. 2x+11 lie inside the padded row and 2x-2 .. 2x+8 inside the image row
+        const bool fast = x >= 4 && 2 * x + 8 <= wi - 1 && 2 * x + 12 <= pi;
+        // row sums of input rows 2r-2, 2r-1, 2r, where r is the next output row
+        int r = max(y0 - 1, 0);
+        unsigned a0, b0, a1, b1, a2, b2;
+        pd_hsum(pd_words(in + (size_t)reflect101(2 * r - 2, hi) * pi, x, wi, fast), a0, b0);
+        pd_hsum(pd_words(in + (size_t)reflect101(2 * r - 1, hi) * pi, x, wi, fast), a1, b1);
+        pd_hsum(pd_words(in + (size_t)reflect101(2 * r, hi) * pi, x, wi, fast), a2, b2);
+        auto next_row = [&]() -> unsigned {
+            unsigned a3, b3, a4, b4;
+            pd_hsum(pd_words(in + (size_t)reflect101(2 * r + 1, hi) * pi, x, wi, fast), a3, b3);
+            pd_hsum(pd_words(in + (size_t)reflect101(2 * r + 2, hi) * pi, x, wi, fast), a4, b4);
+            const unsigned o = pd_vsum(a0, a1, a2, a3, a4, b0, b1, b2, b3, b4);
+            a0 = a2; b0 = b2; a1 = a3; b1 = b3; a2 = a4; b2 = b4;
+            ++r;
+            return o;
+        };
+        // rows y-1, y (replicated above row 0) and y+1 (replicated below row ho-1)
+        unsigned up = next_row();
+        unsigned mid = y0 == 0 ? up : next_row();
+        for (int y = y0; y < y1; ++y) {
+            const unsigned dn = y + 1 <= ho - 1 ? next_row() : mid;
+            unsigned lo = __shfl_up_sync(0xffffffffu, mid, 1) >> 24;
+            const unsigned hb = __shfl_down_sync(0xffffffffu, mid, 1) & 255u;
+            if (x == 0) lo = mid & 255u;   // replicated left border
+            if (lane >= 1 && lane <= 30 && x < wo) emit_row<PT>(D, slot, l, x, y, wo, up, lo, mid, hb, dn);
+            up = mid;
+            mid = dn;
         }
-        __syncthreads();
-        const int so = vec ? off : 0;
-        for (int i = threadIdx.x; i < IH * OW; i += blockDim.x) {
-            int r = i / OW, c = i - r * OW;
-            const uint8_t *q = &sin_[r][2 * c + so];
-            shs[r][c] = (uint16_t)(q[0] + 4 * q[1] + 6 * q[2] + 4 * q[3] + q[4]);
-        }
-        __syncthreads();
-        for (int i = threadIdx.x; i < OH * OW; i += blockDim.x) {
-            int r = i / OW, c = i - r * OW;
-            int sum = shs[2 * r][c] + 4 * shs[2 * r + 1][c] + 6 * shs[2 * r + 2][c] + 4 * shs[2 * r + 3][c] +
-                      shs[2 * r + 4][c];
-            sout[r][c] = (uint8_t)((sum + 128) >> 8);
-        }
-        __syncthreads();
-        const int row = threadIdx.x >> 4, c4 = (threadIdx.x & 15) * 4;
-        const int y = y0 + row, x = x0 + c4;
-        if (y < ho && x < wo) {
-            int v[3][6];
-#pragma unroll
-            for (int r = 0; r < 3; ++r) {
-                int sr = clampi(y + r - 1, 0, ho - 1) - (y0 - 1);
-#pragma unroll
-                for (int c = 0; c < 6; ++c) v[r][c] = sout[sr][clampi(x + c - 1, 0, wo - 1) - (x0 - 1)];
-            }
-            emit4<PT>(D, slot, l, x, y, v);
-        }
-        __syncthreads();
     }
 }
 
@@ -284,9 +324,10 @@ void launch_level0(const Launch &L, int prec, const StreamDev *S, WorkList wl, F
 
 void launch_pyr_down(const Launch &L, int prec, const StreamDev *S, WorkList wl, int l, int slot_ov)
 {
-    int g = grid_for(L, wl.total, prec ? occ_pyr_h() : occ_pyr_f());
-    if (prec) k_pyr_down<__half><<<g, 256, 0, L.stream>>>(S, wl, l, slot_ov);
-    else k_pyr_down<float><<<g, 256, 0, L.stream>>>(S, wl, l, slot_ov);
+    // one warp per strip, four warps per block
+    int g = grid_for(L, (wl.total + 3) / 4, prec ? occ_pyr_h() : occ_pyr_f());
+    if (prec) k_pyr_down<__half><<<g, 128, 0, L.stream>>>(S, wl, l, slot_ov);
+    else k_pyr_down<float><<<g, 128, 0, L.stream>>>(S, wl, l, slot_ov);
 }
 
 void launch_plane_f32(const Launch &L, int prec, const StreamDev *S, int slot, int l, float *I, float *Ix, float *Iy)
@@ -295,17 +336,6 @@ void launch_plane_f32(const Launch &L, int prec, const StreamDev *S, int slot, i
     else k_plane_f32<float><<<4 * L.sms, 256, 0, L.stream>>>(S, slot, l, I, Ix, Iy);
 }
 
-#define OCC_FN(name, kern)                                                        \
-    int name()                                                                    \
-    {                                                                             \
-        static int v = 0;                                                         \
-        if (!v) {                                                                 \
-            if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, kern, 256, 0) != \
-                cudaSuccess || v < 1)                                             \
-                v = 1;                                                            \
-        }                                                                         \
-        return v;                                                                 \
-    }
 #define OCC_FN128(name, kern)                                                                  \
     int name()                                                                                 \
     {                                                                                          \
@@ -318,5 +348,5 @@ void launch_plane_f32(const Launch &L, int prec, const StreamDev *S, int slot, i
     }
 OCC_FN128(occ_level0_f, k_level0<float>)
 OCC_FN128(occ_level0_h, k_level0<__half>)
-OCC_FN(occ_pyr_f, k_pyr_down<float>)
-OCC_FN(occ_pyr_h, k_pyr_down<__half>)
+OCC_FN128(occ_pyr_f, k_pyr_down<float>)
+OCC_FN128(occ_pyr_h, k_pyr_down<__half>)

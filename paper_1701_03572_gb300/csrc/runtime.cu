@@ -80,7 +80,6 @@ inline int up(int v, int a) { return (v + a - 1) / a * a; }
 // parallel branches of the step's graph), so its tracking lags one frame; and
 // it composes the frame whose smoothed map the previous step's fit produced.
 constexpr int kBatchLag = 1, kWarpLag = 1;
-inline int tiles(int w, int h) { return ((w + STAB_TW - 1) / STAB_TW) * ((h + STAB_TH - 1) / STAB_TH); }
 
 stab_status fail(std::string &err, stab_status code, const std::string &msg)
 {
@@ -241,7 +240,7 @@ stab_status build(Pipeline &pp, int n, const int *w, const int *h, const int *C,
     // level 0: strips of 512 columns x 32 rows (one thread per 4 columns)
     mk(&pp.wl_l0, [](const StreamDev &D) { return ((D.w + 511) / 512) * ((D.h + 31) / 32); });
     for (int l = 1; l < STAB_MAXL; ++l)
-        mk(&pp.wl_pyr[l], [l](const StreamDev &D) { return l < D.L ? tiles(D.lw[l], D.lh[l]) : 0; });
+        mk(&pp.wl_pyr[l], [l](const StreamDev &D) { return l < D.L ? stab_pd_items(D.lw[l], D.lh[l]) : 0; });
     mk(&pp.wl_resp, [](const StreamDev &D) { return stab_resp_items(D.roi_x1 - D.roi_x0, D.roi_y1 - D.roi_y0); });
     mk(&pp.wl_filter, [](const StreamDev &D) { return (D.cand_cap + 2047) / 2048; });
     mk(&pp.wl_lk, [](const StreamDev &D) { return D.K; });
