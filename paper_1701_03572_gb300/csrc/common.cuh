@@ -33,14 +33,16 @@ __host__ __device__ inline int stab_resp_items(int rw, int rh)
 {
     return ((rw + 4 * STAB_RS_THREADS - 1) / (4 * STAB_RS_THREADS)) * ((rh + STAB_RS_ROWS - 1) / STAB_RS_ROWS);
 }
-// REDUCE work: a warp owns a strip of STAB_PD_ROWS output rows and STAB_PD_COLS
-// output columns (lanes 1..30, 4 columns each; lanes 0 and 31 compute the
-// neighbouring columns only).
+// REDUCE work: a warp owns a strip of stab_pd_rows(h) output rows and
+// STAB_PD_COLS output columns (lanes 1..30, 4 columns each; lanes 0 and 31
+// compute the neighbouring columns only).  Small levels take shorter strips:
+// more warps, each with fewer dependent rows.
 #define STAB_PD_COLS 120
-#define STAB_PD_ROWS 16
+__host__ __device__ inline int stab_pd_rows(int h) { return h >= 400 ? 16 : h >= 200 ? 8 : 4; }
 __host__ __device__ inline int stab_pd_items(int w, int h)
 {
-    return ((w + STAB_PD_COLS - 1) / STAB_PD_COLS) * ((h + STAB_PD_ROWS - 1) / STAB_PD_ROWS);
+    const int R = stab_pd_rows(h);
+    return ((w + STAB_PD_COLS - 1) / STAB_PD_COLS) * ((h + R - 1) / R);
 }
 #define STAB_WTH 32          // warp output tile: 64 x 32 pixels, 256 threads x 2 rows x 4 pixels
 

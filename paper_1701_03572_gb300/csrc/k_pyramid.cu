@@ -190,8 +190,9 @@ __global__ void __launch_bounds__(L0_GROUPS) k_level0(const StreamDev *__restric
 }
 
 // Level l >= 1 from level l-1 (REDUCE), as barrier-free strips: a warp owns
-// STAB_PD_ROWS output rows of STAB_PD_COLS columns, a thread 4 columns x ..
-// x+3, and walks down them.  Per input row it loads the bytes 2x-2 .. 2x+8
+// stab_pd_rows output rows of STAB_PD_COLS columns, a thread 4 columns x ..
+// x+3, and walks down them, loading the next output row's input rows while it
+// computes the current one.  Per input row it loads the bytes 2x-2 .. 2x+8
 // (three aligned loads inside the row; singly with reflect-101 at the row
 // ends) and forms the [1 4 6 4 1] row sums of columns 2x, 2x+2, 2x+4, 2x+6 as
 // two pairs of 16-bit lanes, so every add and multiply-add serves two outputs
@@ -262,21 +263,27 @@ __global__ void __launch_bounds__(128) k_pyr_down(const StreamDev *__restrict__ 
         const uint8_t *in = D.u8[slot][l - 1];
         const int wi = D.lw[l - 1], hi = D.lh[l - 1], pi = D.lp[l - 1];
         const int wo = D.lw[l], ho = D.lh[l];
-        const int ncx = (wo + STAB_PD_COLS - 1) / STAB_PD_COLS;
-        const int x = (local % ncx) * STAB_PD_COLS + 4 * (lane - 1), y0 = (local / ncx) * STAB_PD_ROWS;
-        const int y1 = min(y0 + STAB_PD_ROWS, ho);
+        const int ncx = (wo + STAB_PD_COLS - 1) / STAB_PD_COLS, R = stab_pd_rows(ho);
+        const int x = (local % ncx) * STAB_PD_COLS + 4 * (lane - 1), y0 = (local / ncx) * R;
+        const int y1 = min(y0 + R, ho);
         // bytes 2x-4 .. 2x+11 lie inside the padded row and 2x-2 .. 2x+8 inside the image row
         const bool fast = x >= 4 && 2 * x + 8 <= wi - 1 && 2 * x + 12 <= pi;
-        // row sums of input rows 2r-2, 2r-1, 2r, where r is the next output row
+        auto words = [&](int yy) { return pd_words(in + (size_t)reflect101(yy, hi) * pi, x, wi, fast); };
+        // row sums of input rows 2r-2, 2r-1, 2r, where r is the next output row;
+        // the bytes of rows 2r+1, 2r+2 are loaded one output row ahead
         int r = max(y0 - 1, 0);
         unsigned a0, b0, a1, b1, a2, b2;
-        pd_hsum(pd_words(in + (size_t)reflect101(2 * r - 2, hi) * pi, x, wi, fast), a0, b0);
-        pd_hsum(pd_words(in + (size_t)reflect101(2 * r - 1, hi) * pi, x, wi, fast), a1, b1);
-        pd_hsum(pd_words(in + (size_t)reflect101(2 * r, hi) * pi, x, wi, fast), a2, b2);
+        PdWords n1 = words(2 * r + 1), n2 = words(2 * r + 2);
+        pd_hsum(words(2 * r - 2), a0, b0);
+        pd_hsum(words(2 * r - 1), a1, b1);
+        pd_hsum(words(2 * r), a2, b2);
         auto next_row = [&]() -> unsigned {
+            const PdWords c1 = n1, c2 = n2;
+            n1 = words(2 * r + 3);
+            n2 = words(2 * r + 4);
             unsigned a3, b3, a4, b4;
-            pd_hsum(pd_words(in + (size_t)reflect101(2 * r + 1, hi) * pi, x, wi, fast), a3, b3);
-            pd_hsum(pd_words(in + (size_t)reflect101(2 * r + 2, hi) * pi, x, wi, fast), a4, b4);
+            pd_hsum(c1, a3, b3);
+            pd_hsum(c2, a4, b4);
             const unsigned o = pd_vsum(a0, a1, a2, a3, a4, b0, b1, b2, b3, b4);
             a0 = a2; b0 = b2; a1 = a3; b1 = b3; a2 = a4; b2 = b4;
             ++r;
