@@ -135,6 +135,41 @@ __device__ __forceinline__ void emit_row(const StreamDev &D, int slot, int l, in
     typedef typename Plane2<PT>::type PT2;
     const size_t o = (size_t)y * D.lp[l] + x;
     *reinterpret_cast<unsigned *>(D.u8[slot][l] + o) = mid;
+    if constexpr (sizeof(PT) == 2) {
+        // FP16: a byte b under the exponent of 1024 is the half 1024 + b (exact,
+        // b < 2^10), so one packed subtract gives b itself and the difference
+        // of two such halves is exactly the difference of the bytes.
+        constexpr unsigned M = 0x64646464u;
+        const __half2 k1024 = __half2half2(__ushort_as_half((unsigned short)0x6400u));
+        const __half2 half = __half2half2(__ushort_as_half((unsigned short)0x3800u));
+        auto h2 = [](unsigned u) { return *reinterpret_cast<const __half2 *>(&u); };
+        auto u32 = [](__half2 h) { return *reinterpret_cast<const unsigned *>(&h); };
+        uint2 iv;
+        iv.x = u32(__hsub2(h2(__byte_perm(mid, M, 0x4140)), k1024));
+        iv.y = u32(__hsub2(h2(__byte_perm(mid, M, 0x4342)), k1024));
+        *reinterpret_cast<uint2 *>(reinterpret_cast<__half *>(D.pI[slot][l]) + o) = iv;
+        // right and left neighbours of columns x .. x+3 (beyond the image edge
+        // the last column replicates), paired byte-wise with the rows below / above
+        unsigned rt = __byte_perm(mid, hi, 0x4321);
+        if (x + 4 > w - 1) {
+#pragma unroll
+            for (int k = 0; k < 4; ++k)
+                if (x + k + 1 > w - 1) rt = (rt & ~(255u << (8 * k))) | (mid & (255u << (8 * k)));
+        }
+        const unsigned lf = __byte_perm(mid, lo, 0x2104);
+        const unsigned rd01 = __byte_perm(rt, dn, 0x5140), rd23 = __byte_perm(rt, dn, 0x7362);
+        const unsigned lu01 = __byte_perm(lf, up, 0x5140), lu23 = __byte_perm(lf, up, 0x7362);
+        auto g = [&](unsigned rd, unsigned lu, unsigned sel) {   // (gx, gy) of one pixel
+            return u32(__hmul2(__hsub2(h2(__byte_perm(rd, M, sel)), h2(__byte_perm(lu, M, sel))), half));
+        };
+        uint4 gv;
+        gv.x = g(rd01, lu01, 0x4140);
+        gv.y = g(rd01, lu01, 0x4342);
+        gv.z = g(rd23, lu23, 0x4140);
+        gv.w = g(rd23, lu23, 0x4342);
+        *reinterpret_cast<uint4 *>(reinterpret_cast<PT2 *>(D.pG[slot][l]) + o) = gv;
+        return;
+    }
     const int b[6] = {(int)lo, (int)(mid & 255u), (int)((mid >> 8) & 255u), (int)((mid >> 16) & 255u),
                       (int)(mid >> 24), (int)hi};
     float I[4], gx[4], gy[4];
