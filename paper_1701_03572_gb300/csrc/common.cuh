@@ -38,7 +38,7 @@ __host__ __device__ inline int stab_resp_items(int rw, int rh)
 // compute the neighbouring columns only).  Small levels take shorter strips:
 // more warps, each with fewer dependent rows.
 #define STAB_PD_COLS 120
-__host__ __device__ inline int stab_pd_rows(int h) { return h >= 400 ? 16 : h >= 200 ? 8 : 4; }
+__host__ __device__ inline int stab_pd_rows(int h) { return h >= 400 ? 16 : h >= 200 ? 4 : 2; }
 __host__ __device__ inline int stab_pd_items(int w, int h)
 {
     const int R = stab_pd_rows(h);

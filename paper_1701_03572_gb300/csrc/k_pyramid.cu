@@ -28,50 +28,11 @@ __device__ __forceinline__ void store_I(float *p, const float v[4])
 {
     *reinterpret_cast<float4 *>(p) = make_float4(v[0], v[1], v[2], v[3]);
 }
-__device__ __forceinline__ void store_I(__half *p, const float v[4])
-{
-    __half2 a = __floats2half2_rn(v[0], v[1]), b = __floats2half2_rn(v[2], v[3]);
-    uint2 u;
-    u.x = *reinterpret_cast<unsigned *>(&a);
-    u.y = *reinterpret_cast<unsigned *>(&b);
-    *reinterpret_cast<uint2 *>(p) = u;
-}
 __device__ __forceinline__ void store_G(float2 *p, const float gx[4], const float gy[4])
 {
     float4 *q = reinterpret_cast<float4 *>(p);
     q[0] = make_float4(gx[0], gy[0], gx[1], gy[1]);
     q[1] = make_float4(gx[2], gy[2], gx[3], gy[3]);
-}
-__device__ __forceinline__ void store_G(__half2 *p, const float gx[4], const float gy[4])
-{
-    uint4 u;
-    __half2 h0 = __floats2half2_rn(gx[0], gy[0]), h1 = __floats2half2_rn(gx[1], gy[1]);
-    __half2 h2 = __floats2half2_rn(gx[2], gy[2]), h3 = __floats2half2_rn(gx[3], gy[3]);
-    u.x = *reinterpret_cast<unsigned *>(&h0);
-    u.y = *reinterpret_cast<unsigned *>(&h1);
-    u.z = *reinterpret_cast<unsigned *>(&h2);
-    u.w = *reinterpret_cast<unsigned *>(&h3);
-    *reinterpret_cast<uint4 *>(p) = u;
-}
-
-// Emit 4 pixels (x..x+3, y) of level l from a 3 x 6 neighbourhood v (rows
-// y-1..y+1, columns x-1..x+4, already border-replicated).
-template <typename PT>
-__device__ __forceinline__ void emit4(const StreamDev &D, int slot, int l, int x, int y, const int v[3][6])
-{
-    typedef typename Plane2<PT>::type PT2;
-    size_t o = (size_t)y * D.lp[l] + x;
-    *reinterpret_cast<uchar4 *>(D.u8[slot][l] + o) =
-        make_uchar4((uint8_t)v[1][1], (uint8_t)v[1][2], (uint8_t)v[1][3], (uint8_t)v[1][4]);
-    float I[4], gx[4], gy[4];
-#pragma unroll
-    for (int k = 0; k < 4; ++k) {
-        I[k] = (float)v[1][k + 1];
-        gx[k] = 0.5f * (float)(v[1][k + 2] - v[1][k]);
-        gy[k] = 0.5f * (float)(v[2][k + 1] - v[0][k + 1]);
-    }
-    store_I(reinterpret_cast<PT *>(D.pI[slot][l]) + o, I);
-    store_G(reinterpret_cast<PT2 *>(D.pG[slot][l]) + o, gx, gy);
 }
 
 // Level 0: frame (gray, or RGB converted to luma) -> u8 level 0 + planes.
@@ -168,21 +129,21 @@ __device__ __forceinline__ void emit_row(const StreamDev &D, int slot, int l, in
         gv.z = g(rd23, lu23, 0x4140);
         gv.w = g(rd23, lu23, 0x4342);
         *reinterpret_cast<uint4 *>(reinterpret_cast<PT2 *>(D.pG[slot][l]) + o) = gv;
-        return;
-    }
-    const int b[6] = {(int)lo, (int)(mid & 255u), (int)((mid >> 8) & 255u), (int)((mid >> 16) & 255u),
-                      (int)(mid >> 24), (int)hi};
-    float I[4], gx[4], gy[4];
+    } else {
+        const int b[6] = {(int)lo, (int)(mid & 255u), (int)((mid >> 8) & 255u), (int)((mid >> 16) & 255u),
+                          (int)(mid >> 24), (int)hi};
+        float I[4], gx[4], gy[4];
 #pragma unroll
-    for (int k = 0; k < 4; ++k) {
-        // columns beyond the image edge replicate the last column
-        const int r = (x + k + 1 <= w - 1) ? b[k + 2] : b[k + 1];
-        I[k] = (float)b[k + 1];
-        gx[k] = 0.5f * (float)(r - b[k]);
-        gy[k] = 0.5f * (float)((int)((dn >> (8 * k)) & 255u) - (int)((up >> (8 * k)) & 255u));
+        for (int k = 0; k < 4; ++k) {
+            // columns beyond the image edge replicate the last column
+            const int r = (x + k + 1 <= w - 1) ? b[k + 2] : b[k + 1];
+            I[k] = (float)b[k + 1];
+            gx[k] = 0.5f * (float)(r - b[k]);
+            gy[k] = 0.5f * (float)((int)((dn >> (8 * k)) & 255u) - (int)((up >> (8 * k)) & 255u));
+        }
+        store_I(reinterpret_cast<PT *>(D.pI[slot][l]) + o, I);
+        store_G(reinterpret_cast<PT2 *>(D.pG[slot][l]) + o, gx, gy);
     }
-    store_I(reinterpret_cast<PT *>(D.pI[slot][l]) + o, I);
-    store_G(reinterpret_cast<PT2 *>(D.pG[slot][l]) + o, gx, gy);
 }
 
 template <typename PT>
@@ -226,8 +187,7 @@ __global__ void __launch_bounds__(L0_GROUPS) k_level0(const StreamDev *__restric
 
 // Level l >= 1 from level l-1 (REDUCE), as barrier-free strips: a warp owns
 // stab_pd_rows output rows of STAB_PD_COLS columns, a thread 4 columns x ..
-// x+3, and walks down them, loading the next output row's input rows while it
-// computes the current one.  Per input row it loads the bytes 2x-2 .. 2x+8
+// x+3, and walks down them.  Per input row it loads the bytes 2x-2 .. 2x+8
 // (three aligned loads inside the row; singly with reflect-101 at the row
 // ends) and forms the [1 4 6 4 1] row sums of columns 2x, 2x+2, 2x+4, 2x+6 as
 // two pairs of 16-bit lanes, so every add and multiply-add serves two outputs
@@ -304,21 +264,16 @@ __global__ void __launch_bounds__(128) k_pyr_down(const StreamDev *__restrict__ 
         // bytes 2x-4 .. 2x+11 lie inside the padded row and 2x-2 .. 2x+8 inside the image row
         const bool fast = x >= 4 && 2 * x + 8 <= wi - 1 && 2 * x + 12 <= pi;
         auto words = [&](int yy) { return pd_words(in + (size_t)reflect101(yy, hi) * pi, x, wi, fast); };
-        // row sums of input rows 2r-2, 2r-1, 2r, where r is the next output row;
-        // the bytes of rows 2r+1, 2r+2 are loaded one output row ahead
+        // row sums of input rows 2r-2, 2r-1, 2r, where r is the next output row
         int r = max(y0 - 1, 0);
         unsigned a0, b0, a1, b1, a2, b2;
-        PdWords n1 = words(2 * r + 1), n2 = words(2 * r + 2);
         pd_hsum(words(2 * r - 2), a0, b0);
         pd_hsum(words(2 * r - 1), a1, b1);
         pd_hsum(words(2 * r), a2, b2);
         auto next_row = [&]() -> unsigned {
-            const PdWords c1 = n1, c2 = n2;
-            n1 = words(2 * r + 3);
-            n2 = words(2 * r + 4);
             unsigned a3, b3, a4, b4;
-            pd_hsum(c1, a3, b3);
-            pd_hsum(c2, a4, b4);
+            pd_hsum(words(2 * r + 1), a3, b3);
+            pd_hsum(words(2 * r + 2), a4, b4);
             const unsigned o = pd_vsum(a0, a1, a2, a3, a4, b0, b1, b2, b3, b4);
             a0 = a2; b0 = b2; a1 = a3; b1 = b3; a2 = a4; b2 = b4;
             ++r;
