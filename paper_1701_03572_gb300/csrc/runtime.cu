@@ -39,8 +39,8 @@ struct Pipeline {
     // streams chained by events, so copies of neighbouring steps overlap the step
     cudaStream_t hs_in = nullptr, hs_comp = nullptr, hs_out = nullptr;
     // second branch of the step: detection runs beside the pyramid levels >= 1
-    cudaStream_t side = nullptr;
-    cudaEvent_t ev_fork = nullptr, ev_det = nullptr;
+    cudaStream_t side = nullptr, side2 = nullptr;
+    cudaEvent_t ev_fork = nullptr, ev_det = nullptr, ev_warp = nullptr;
     cudaEvent_t ev_in[2] = {}, ev_comp[4] = {}, ev_out[4] = {}, ev_join = nullptr;
     bool host_mode = false;   // the last step was a host-buffer step
     int wmax = 1;             // largest smoothing window of the batch
@@ -62,9 +62,9 @@ struct Pipeline {
         if (gexec) cudaGraphExecDestroy(gexec);
         if (graph) cudaGraphDestroy(graph);
         if (cap) cudaStreamDestroy(cap);
-        for (cudaStream_t x : {hs_in, hs_comp, hs_out, side})
+        for (cudaStream_t x : {hs_in, hs_comp, hs_out, side, side2})
             if (x) cudaStreamDestroy(x);
-        for (cudaEvent_t e : {ev_fork, ev_det})
+        for (cudaEvent_t e : {ev_fork, ev_det, ev_warp})
             if (e) cudaEventDestroy(e);
         for (cudaEvent_t e : {ev_in[0], ev_in[1], ev_comp[0], ev_comp[1], ev_comp[2], ev_comp[3], ev_out[0], ev_out[1],
                               ev_out[2], ev_out[3], ev_join})
@@ -318,13 +318,16 @@ void enqueue_step(Pipeline &pp, cudaStream_t s, Prof *pf = nullptr)
         launch_warp(L, pp.ds, pp.wl_warp, WarpIO{});
         mark("warp");
     } else {
-        // Two branches that share no buffer: the tracking of frames t-2 -> t-1
-        // (detection on frame t-2 when due, tracker, fit, smoothing), and the
-        // pyramid of frame t (ring slot t, pyramid slot t mod 3) followed by the
+        // Three branches that share no buffer: the tracking of frames t-2 -> t-1
+        // (detection on frame t-2 when due, tracker, fit, smoothing), the
+        // pyramid of frame t (ring slot t, pyramid slot t mod 3), and the
         // composition of the frame whose map the previous step's fit produced.
-        const Launch Ls{pp.side, pp.sms};
+        const Launch Ls{pp.side, pp.sms}, Lw{pp.side2, pp.sms};
         cudaEventRecord(pp.ev_fork, s);
         cudaStreamWaitEvent(pp.side, pp.ev_fork, 0);
+        cudaStreamWaitEvent(pp.side2, pp.ev_fork, 0);
+        launch_warp(Lw, pp.ds, pp.wl_warp, WarpIO{});
+        cudaEventRecord(pp.ev_warp, pp.side2);
         launch_response(Ls, pp.ds, pp.wl_resp, DetIO{});
         launch_filter(Ls, pp.ds, pp.wl_filter);
         launch_select(Ls, pp.ds, pp.n, DetIO{});
@@ -334,8 +337,8 @@ void enqueue_step(Pipeline &pp, cudaStream_t s, Prof *pf = nullptr)
         cudaEventRecord(pp.ev_det, pp.side);
         launch_level0(L, pp.prec, pp.ds, pp.wl_l0, FrameSrc{nullptr, 0, 0, 0});
         for (int l = 1; l < pp.Lmax; ++l) launch_pyr_down(L, pp.prec, pp.ds, pp.wl_pyr[l], l, -1);
-        launch_warp(L, pp.ds, pp.wl_warp, WarpIO{});
         cudaStreamWaitEvent(s, pp.ev_det, 0);
+        cudaStreamWaitEvent(s, pp.ev_warp, 0);
     }
     launch_advance(L, pp.ds, pp.n);
     mark("advance");
@@ -581,8 +584,10 @@ stab_status stab_batch_create(int n, const stab_stream_desc *d, int ring, stab_b
     for (int i = 0; i < n; ++i) b->pp.wmax = std::max(b->pp.wmax, P[i].smooth_window);
     if (s == STAB_OK && (cudaStreamCreateWithFlags(&b->pp.cap, cudaStreamNonBlocking) != cudaSuccess ||
                          cudaStreamCreateWithFlags(&b->pp.side, cudaStreamNonBlocking) != cudaSuccess ||
+                         cudaStreamCreateWithFlags(&b->pp.side2, cudaStreamNonBlocking) != cudaSuccess ||
                          cudaEventCreateWithFlags(&b->pp.ev_fork, cudaEventDisableTiming) != cudaSuccess ||
-                         cudaEventCreateWithFlags(&b->pp.ev_det, cudaEventDisableTiming) != cudaSuccess))
+                         cudaEventCreateWithFlags(&b->pp.ev_det, cudaEventDisableTiming) != cudaSuccess ||
+                         cudaEventCreateWithFlags(&b->pp.ev_warp, cudaEventDisableTiming) != cudaSuccess))
         s = cuda_check(b->pp.err, "stream create");
     if (s != STAB_OK) {
         fprintf(stderr, "stab_batch_create: %s\n", b->pp.err.c_str());
