@@ -24,12 +24,26 @@ __device__ __forceinline__ unsigned long long splitmix64(unsigned long long x)
     return z ^ (z >> 31);
 }
 
-__device__ __forceinline__ void sample_pair(unsigned long long seed, long long t, int h, int n, int &i, int &j)
+// r mod n for 64-bit r without a 64-bit division per call: with m = floor((2^64
+// - 1) / n), q = floor(r m / 2^64) satisfies r/n - 3 < q <= r/n, so r - q n lies
+// in [0, 3n) and at most two subtractions finish it (the result is exact).
+struct Mod64 { unsigned long long m, n; };
+__device__ __forceinline__ Mod64 mod64_of(unsigned long long n) { return Mod64{~0ull / n, n}; }
+__device__ __forceinline__ unsigned long long mod64(unsigned long long r, const Mod64 &d)
+{
+    unsigned long long x = r - __umul64hi(r, d.m) * d.n;
+    while (x >= d.n) x -= d.n;
+    return x;
+}
+
+// mn: modulus n, mn1: modulus n - 1 (n >= 2 staged pairs)
+__device__ __forceinline__ void sample_pair(unsigned long long seed, long long t, int h, const Mod64 &mn,
+                                            const Mod64 &mn1, int &i, int &j)
 {
     unsigned long long base = seed ^ ((unsigned long long)(unsigned)t << 32) ^ ((unsigned long long)(unsigned)h << 8);
     unsigned long long r0 = splitmix64(base), r1 = splitmix64(base ^ 1ull);
-    i = (int)(r0 % (unsigned long long)n);
-    int b = (int)(r1 % (unsigned long long)(n - 1));
+    i = (int)mod64(r0, mn);
+    int b = (int)mod64(r1, mn1);
     j = b >= i ? b + 1 : b;
 }
 
@@ -232,9 +246,10 @@ __device__ FitRes fit_model(const float2 *ss, const float2 *sd, int n, int rigid
     r.tx = r.ty = r.th = r.ls = r.rms = 0.f;
     r.inliers = 0;
     int best = -1, bh = 0x7fffffff;
+    const Mod64 mn = mod64_of((unsigned)n), mn1 = mod64_of((unsigned)(n - 1));
     for (int hh = wid; hh < D.H; hh += nwarps) {
         int i, j;
-        sample_pair(D.seed, t, hh, n, i, j);
+        sample_pair(D.seed, t, hh, mn, mn1, i, j);
         float m[4];
         int cnt = -1;
         if (two_point(ss[i], ss[j], sd[i], sd[j], rigid, m)) {
@@ -255,7 +270,7 @@ __device__ FitRes fit_model(const float2 *ss, const float2 *sd, int n, int rigid
     __syncthreads();
     if (sh.best < 2) return r;
     int i, j;
-    sample_pair(D.seed, t, sh.bh, n, i, j);
+    sample_pair(D.seed, t, sh.bh, mn, mn1, i, j);
     float m[4];
     two_point(ss[i], ss[j], sd[i], sd[j], rigid, m);
     float v[5] = {0.f, 0.f, 0.f, 0.f, 0.f};
@@ -378,7 +393,7 @@ __device__ __forceinline__ void sample_triple(unsigned long long seed, long long
                                               int &k)
 {
     unsigned long long base = seed ^ ((unsigned long long)(unsigned)t << 32) ^ ((unsigned long long)(unsigned)h << 8);
-    sample_pair(seed, t, h, n, i, j);
+    sample_pair(seed, t, h, mod64_of((unsigned)n), mod64_of((unsigned)(n - 1)), i, j);
     const int lo = min(i, j), hi = max(i, j);
     int c = (int)(splitmix64(base ^ 2ull) % (unsigned long long)(n - 2));
     if (c >= lo) ++c;
