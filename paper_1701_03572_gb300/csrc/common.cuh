@@ -62,6 +62,8 @@ struct StreamState {
     int err;              // first device error (stab_status), 0 if none
     long long iters;      // LK iterations of this step (statistic)
     long long tpl;        // LK template passes (feature x level x direction) of this step
+    unsigned long long fit_key[2];   // best hypothesis so far of the fit in flight, per fitted model
+    int fit_ticket;       // fit CTAs of this stream done (the last one refits and clears both)
     int n_det;            // corners of the last detection
     int n_above;          // candidates above the quality threshold (before the top-K cut)
     int hyb_rigid;        // hybrid mechanism: the model held since the last decision (1 rigid)

@@ -3,15 +3,17 @@
 // trajectory smoothing of Sec. 5.1 (offline over a clip, or streaming with a
 // W/2-frame lookahead, the GPU form of the paper's motion-compensation thread).
 //
-// The fit runs one CTA per stream.  Hypothesis h draws its two-point sample
-// from the SplitMix64 hash of (seed, t, h) and is scored by its inlier count;
-// model and residual use one fixed IEEE FP32 operation sequence (explicit
-// _rn intrinsics, no contraction), so counts and the winning hypothesis are
-// reproducible bit for bit.  The closed-form least-squares refit on the
-// winner's inliers uses fixed-order FP32 block reductions.  With the hybrid
-// mechanism (Sec. 4.1) a decision transition fits both models in the same CTA
-// and keeps the rigid one iff its RMS over its own inliers is strictly lower;
-// the choice is held in the stream state until the next decision.
+// The fit runs up to 8 CTAs per stream, each scoring a slice of the
+// hypotheses; the last to finish refits on the overall winner.  Hypothesis h
+// draws its two-point sample from the SplitMix64 hash of (seed, t, h) and is
+// scored by its inlier count; model and residual use one fixed IEEE FP32
+// operation sequence (explicit _rn intrinsics, no contraction), so counts and
+// the winning hypothesis are reproducible bit for bit.  The closed-form
+// least-squares refit on the winner's inliers uses fixed-order FP32 block
+// reductions.  With the hybrid mechanism (Sec. 4.1) a decision transition fits
+// both models in the same launch and keeps the rigid one iff its RMS over its
+// own inliers is strictly lower; the choice is held in the stream state until
+// the next decision.
 #include "kernels.cuh"
 
 namespace {
@@ -229,25 +231,27 @@ struct FitRes {
 };
 
 struct FitShared {
-    int wbs[16], wbh[16];
-    int best, bh;
+    unsigned long long key[16];   // per-warp best hypotheses (score_slice)
     float red[16][5];
 };
 
-// Robust fit of one model to the n staged centred pairs (every thread of the
-// block): hypotheses scored by inlier count, the first best kept, then the
-// closed-form least-squares refit on its inliers and their RMS residual.
-__device__ FitRes fit_model(const float2 *ss, const float2 *sd, int n, int rigid, const StreamDev &D, long long t,
-                            FitShared &sh)
+// Hypothesis scoring of one model for a slice of the hypotheses: warp g of
+// the stream's G scoring warps takes h = g, g + G, ...; a hypothesis scores its
+// inlier count (-1 when its two points are degenerate).  The block's best as
+// a key, larger = more inliers, then the lower h (the first best):
+// (count + 1) << 32 | ~h.  Every thread of the block returns it.
+__device__ __forceinline__ unsigned long long fit_key(int cnt, int h)
 {
-    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5, nwarps = blockDim.x >> 5;
-    FitRes r;
-    r.ok = false;
-    r.tx = r.ty = r.th = r.ls = r.rms = 0.f;
-    r.inliers = 0;
+    return ((unsigned long long)(unsigned)(cnt + 1) << 32) | (unsigned long long)(0xFFFFFFFFu - (unsigned)h);
+}
+
+__device__ unsigned long long score_slice(const float2 *ss, const float2 *sd, int n, int rigid, const StreamDev &D,
+                                          long long t, int g, int G, const Mod64 &mn, const Mod64 &mn1,
+                                          unsigned long long *skey)
+{
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
     int best = -1, bh = 0x7fffffff;
-    const Mod64 mn = mod64_of((unsigned)n), mn1 = mod64_of((unsigned)(n - 1));
-    for (int hh = wid; hh < D.H; hh += nwarps) {
+    for (int hh = g; hh < D.H; hh += G) {
         int i, j;
         sample_pair(D.seed, t, hh, mn, mn1, i, j);
         float m[4];
@@ -259,18 +263,29 @@ __device__ FitRes fit_model(const float2 *ss, const float2 *sd, int n, int rigid
         }
         if (cnt > best) { best = cnt; bh = hh; }
     }
-    if (lane == 0) { sh.wbs[wid] = best; sh.wbh[wid] = bh; }
+    __syncthreads();   // earlier readers of skey are done
+    if (lane == 0) skey[wid] = fit_key(best, bh);
     __syncthreads();
-    if (tid == 0) {
-        int b = -1, h = 0x7fffffff;
-        for (int k = 0; k < nwarps; ++k)
-            if (sh.wbs[k] > b || (sh.wbs[k] == b && sh.wbh[k] < h)) { b = sh.wbs[k]; h = sh.wbh[k]; }
-        sh.best = b; sh.bh = h;
-    }
-    __syncthreads();
-    if (sh.best < 2) return r;
+    unsigned long long k = 0;
+    for (int w = 0; w < nwarps; ++w) k = max(k, skey[w]);
+    return k;
+}
+
+// Least-squares refit of one model on the inliers of the winning hypothesis
+// (key from score_slice over all of the stream's hypotheses): the closed-form
+// similarity / rigid fit and the RMS residual of those inliers.
+__device__ FitRes refit(const float2 *ss, const float2 *sd, int n, int rigid, const StreamDev &D, long long t,
+                        unsigned long long key, const Mod64 &mn, const Mod64 &mn1, FitShared &sh)
+{
+    const int tid = threadIdx.x;
+    FitRes r;
+    r.ok = false;
+    r.tx = r.ty = r.th = r.ls = r.rms = 0.f;
+    r.inliers = 0;
+    const int best = (int)(unsigned)(key >> 32) - 1, bh = (int)(0xFFFFFFFFu - (unsigned)key);
+    if (best < 2) return r;
     int i, j;
-    sample_pair(D.seed, t, sh.bh, mn, mn1, i, j);
+    sample_pair(D.seed, t, bh, mn, mn1, i, j);
     float m[4];
     two_point(ss[i], ss[j], sd[i], sd[j], rigid, m);
     float v[5] = {0.f, 0.f, 0.f, 0.f, 0.f};
@@ -313,16 +328,22 @@ __device__ FitRes fit_model(const float2 *ss, const float2 *sd, int n, int rigid
     return r;
 }
 
+// Grid (streams, parts): the parts of a stream each stage its pairs and score
+// a slice of its hypotheses, folding their best into the stream's key with an
+// atomic maximum; the last part to finish (ticket) reads and clears the keys,
+// refits, decides and smooths.
 __global__ void __launch_bounds__(512) k_fit(const StreamDev *__restrict__ S, FitIO io, int streaming)
 {
     __shared__ float2 ss[STAB_MAXK], sd[STAB_MAXK];
     __shared__ FitShared sh;
+    __shared__ int s_last;
+    __shared__ unsigned long long s_keys[2];
     const StreamDev &D = S[blockIdx.x];
     StreamState *st = D.st;
-    const int tid = threadIdx.x;
+    const int tid = threadIdx.x, parts = gridDim.y, nwarps = blockDim.x >> 5;
     const long long t = io.src ? io.t : st->t - D.lag;   // transition tracked by this step
     if (!io.src && t < 0) {   // a batch's first step: no transition yet (nothing to record)
-        if (threadIdx.x == 0) st->out_frame[st->t & 1] = -1;
+        if (threadIdx.x == 0 && blockIdx.y == 0) st->out_frame[st->t & 1] = -1;
         return;
     }
     int n = io.src ? *io.n : (t >= 1 ? st->n_pairs : 0);
@@ -340,6 +361,31 @@ __global__ void __launch_bounds__(512) k_fit(const StreamDev *__restrict__ S, Fi
         sd[i] = make_float2(__fsub_rn(b.x, cx), __fsub_rn(b.y, cy));
     }
     __syncthreads();
+    const bool fitting = t >= 1 && n >= max(2, D.min_fit);
+    // models fitted: both (rigid first) on a decision transition, else the held one
+    const int nm = decide ? 2 : 1;
+    const Mod64 mn = mod64_of((unsigned)max(n, 2)), mn1 = mod64_of((unsigned)max(n - 1, 1));
+    if (fitting) {
+        const int g = blockIdx.y * nwarps + (tid >> 5), G = parts * nwarps;
+        for (int mi = 0; mi < nm; ++mi) {
+            const unsigned long long k = score_slice(ss, sd, n, decide ? 1 - mi : rigid, D, t, g, G, mn, mn1, sh.key);
+            if (tid == 0) atomicMax(&st->fit_key[mi], k);
+        }
+    }
+    __syncthreads();
+    if (tid == 0) {
+        __threadfence();
+        s_last = atomicAdd(&st->fit_ticket, 1) == parts - 1;
+    }
+    __syncthreads();
+    if (!s_last) return;
+    if (tid == 0) {
+        __threadfence();
+        s_keys[0] = atomicExch(&st->fit_key[0], 0ull);
+        s_keys[1] = atomicExch(&st->fit_key[1], 0ull);
+        st->fit_ticket = 0;
+    }
+    __syncthreads();
     stab_motion out;
     out.tx = out.ty = out.theta = out.log_scale = 0.f;
     out.inliers = 0;
@@ -350,17 +396,17 @@ __global__ void __launch_bounds__(512) k_fit(const StreamDev *__restrict__ S, Fi
     if (decide) out.flags |= STAB_FLAG_DECISION;
     FitRes res;
     res.ok = false;
-    if (t >= 1 && n >= max(2, D.min_fit)) {
+    if (fitting) {
         if (decide) {
-            const FitRes fr = fit_model(ss, sd, n, 1, D, t, sh);
-            const FitRes fs = fit_model(ss, sd, n, 0, D, t, sh);
+            const FitRes fr = refit(ss, sd, n, 1, D, t, s_keys[0], mn, mn1, sh);
+            const FitRes fs = refit(ss, sd, n, 0, D, t, s_keys[1], mn, mn1, sh);
             if (fr.ok) out.e_rigid = fr.rms;
             if (fs.ok) out.e_similarity = fs.rms;
             if (fr.ok && fs.ok) rigid = fr.rms < fs.rms;
             else if (fr.ok || fs.ok) rigid = fr.ok;
             res = rigid ? fr : fs;
         } else {
-            res = fit_model(ss, sd, n, rigid, D, t, sh);
+            res = refit(ss, sd, n, rigid, D, t, s_keys[0], mn, mn1, sh);
             if (res.ok) (rigid ? out.e_rigid : out.e_similarity) = res.rms;
         }
     }
@@ -577,9 +623,11 @@ void launch_compact(const Launch &L, const StreamDev *S, int n, CompactIO io)
     k_compact<<<n, 1024, 0, L.stream>>>(S, io);
 }
 
-void launch_fit(const Launch &L, const StreamDev *S, int n, FitIO io, int streaming)
+void launch_fit(const Launch &L, const StreamDev *S, int n, FitIO io, int streaming, int hmax)
 {
-    k_fit<<<n, 512, 0, L.stream>>>(S, io, streaming);
+    // one hypothesis or more per scoring warp (16 per CTA), at most 8 CTAs per stream
+    const int parts = hmax <= 16 ? 1 : hmax >= 8 * 16 ? 8 : (hmax + 15) / 16;
+    k_fit<<<dim3(n, parts), 512, 0, L.stream>>>(S, io, streaming);
 }
 
 void launch_fit_affine(const Launch &L, const StreamDev *S, AffineIO io)

@@ -98,7 +98,7 @@ int lk_variants();
 void launch_lk(const Launch &L, int prec, int rcode, int variant, const StreamDev *S, WorkList wl, LkIO io);
 
 void launch_compact(const Launch &L, const StreamDev *S, int n, CompactIO io);
-void launch_fit(const Launch &L, const StreamDev *S, int n, FitIO io, int streaming);
+void launch_fit(const Launch &L, const StreamDev *S, int n, FitIO io, int streaming, int hmax);
 void launch_fit_affine(const Launch &L, const StreamDev *S, AffineIO io);
 void launch_smooth_offline(const Launch &L, const stab_motion *m, int T, int W, int w, int h, float zoom,
                            float *mprime, float *Minv);

@@ -44,6 +44,7 @@ struct Pipeline {
     cudaEvent_t ev_in[2] = {}, ev_comp[4] = {}, ev_out[4] = {}, ev_join = nullptr;
     bool host_mode = false;   // the last step was a host-buffer step
     int wmax = 1;             // largest smoothing window of the batch
+    int hmax = 1;             // most fit hypotheses of a stream
 
     // Window radius for the tracker launch: the radius when every stream uses
     // the same one, its negative (the largest) when they differ.
@@ -139,6 +140,7 @@ stab_status build(Pipeline &pp, int n, const int *w, const int *h, const int *C,
         pp.rmax = std::max(pp.rmax, P[i].win_radius);
         pp.rmin = std::min(pp.rmin, P[i].win_radius);
         pp.Lmax = std::max(pp.Lmax, P[i].levels);
+        pp.hmax = std::max(pp.hmax, P[i].hypotheses);
     }
     cudaDeviceGetAttribute(&pp.sms, cudaDevAttrMultiProcessorCount, 0);
     int dev = 0;
@@ -313,7 +315,7 @@ void enqueue_step(Pipeline &pp, cudaStream_t s, Prof *pf = nullptr)
         mark("lk");
         launch_compact(L, pp.ds, pp.n, CompactIO{});
         mark("compact");
-        launch_fit(L, pp.ds, pp.n, FitIO{}, 1);
+        launch_fit(L, pp.ds, pp.n, FitIO{}, 1, pp.hmax);
         mark("fit");
         launch_warp(L, pp.ds, pp.wl_warp, WarpIO{});
         mark("warp");
@@ -333,7 +335,7 @@ void enqueue_step(Pipeline &pp, cudaStream_t s, Prof *pf = nullptr)
         launch_select(Ls, pp.ds, pp.n, DetIO{});
         launch_lk(Ls, pp.prec, pp.rcode(), pp.lk_variant, pp.ds, pp.wl_lk, LkIO{});
         launch_compact(Ls, pp.ds, pp.n, CompactIO{});
-        launch_fit(Ls, pp.ds, pp.n, FitIO{}, 1);
+        launch_fit(Ls, pp.ds, pp.n, FitIO{}, 1, pp.hmax);
         cudaEventRecord(pp.ev_det, pp.side);
         launch_level0(L, pp.prec, pp.ds, pp.wl_l0, FrameSrc{nullptr, 0, 0, 0});
         for (int l = 1; l < pp.Lmax; ++l) launch_pyr_down(L, pp.prec, pp.ds, pp.wl_pyr[l], l, -1);
@@ -524,7 +526,7 @@ stab_status stab_fit(stab_ctx *c, const float *src, const float *dst, const int 
     if (!c || !src || !dst || !n || !out || (model != STAB_RIGID && model != STAB_SIMILARITY && model != STAB_HYBRID))
         return STAB_ERR_INVALID_ARG;
     CTX_LAUNCH(c, stream);
-    launch_fit(L, pp.ds, 1, FitIO{(const float2 *)src, (const float2 *)dst, n, model, t, out}, 0);
+    launch_fit(L, pp.ds, 1, FitIO{(const float2 *)src, (const float2 *)dst, n, model, t, out}, 0, pp.hmax);
     return cuda_check(pp.err, "stab_fit");
 }
 
