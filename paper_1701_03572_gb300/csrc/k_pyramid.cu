@@ -185,12 +185,11 @@ __global__ void __launch_bounds__(L0_GROUPS) k_level0(const StreamDev *__restric
     }
 }
 
-// Level l >= 1 from level l-1 (REDUCE), as strips: a warp owns stab_pd_rows
-// output rows of STAB_PD_COLS columns, copies their input rows into its own
-// shared-memory region (all in flight at once), and a thread then walks down
-// 4 columns x .. x+3.  Per input row it reads the bytes 2x-2 .. 2x+8
-// (three aligned shared-memory loads inside the row; singly from global memory
-// with reflect-101 at the row ends) and forms the [1 4 6 4 1] row sums of columns 2x, 2x+2, 2x+4, 2x+6 as
+// Level l >= 1 from level l-1 (REDUCE), as barrier-free strips: a warp owns
+// stab_pd_rows output rows of STAB_PD_COLS columns, a thread 4 columns x ..
+// x+3, and walks down them.  Per input row it loads the bytes 2x-2 .. 2x+8
+// (three aligned loads inside the row; singly with reflect-101 at the row
+// ends) and forms the [1 4 6 4 1] row sums of columns 2x, 2x+2, 2x+4, 2x+6 as
 // two pairs of 16-bit lanes, so every add and multiply-add serves two outputs
 // (a lane's sum is at most 16 * 255 = 4080).  Five such rows give an output row
 // the same way (at most 65280 + 128 per lane), rounded and packed to bytes by
@@ -246,26 +245,9 @@ __device__ __forceinline__ unsigned pd_vsum(unsigned a0, unsigned a1, unsigned a
     return __byte_perm(va, vb, 0x7531);
 }
 
-// Shared-memory staging of a strip's input rows (one region per warp): row k
-// holds input row 2 rmin - 2 + k (reflected), bytes 2 xb - 16 .. 2 xb + 255 of it,
-// copied as 16-byte chunks with cp.async, all of the strip's rows in flight
-// together (a strip of R output rows needs at most 2 R + 7 input rows).
-constexpr int PD_SROW = 2 * STAB_PD_COLS + 32;        // 272 bytes = 17 chunks
-constexpr int PD_SROWS = 2 * 16 + 7;                  // tallest strip (16 rows)
-constexpr int PD_WARP_SMEM = PD_SROWS * PD_SROW;      // 10,608 bytes
-constexpr int PD_BLOCK_SMEM = 4 * PD_WARP_SMEM;
-
-__device__ __forceinline__ void pd_cp16(void *sdst, const void *gsrc)
-{
-    const unsigned d = (unsigned)__cvta_generic_to_shared(sdst);
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(d), "l"(gsrc) : "memory");
-}
-
 template <typename PT>
 __global__ void __launch_bounds__(128) k_pyr_down(const StreamDev *__restrict__ S, WorkList wl, int l, int slot_ov)
 {
-    extern __shared__ __align__(16) uint8_t pd_smem[];
-    uint8_t *sw = pd_smem + (threadIdx.x >> 5) * PD_WARP_SMEM;
     const int lane = threadIdx.x & 31;
     const int nwarps = gridDim.x * (blockDim.x >> 5);
     for (int item = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); item < wl.total; item += nwarps) {
@@ -277,46 +259,24 @@ __global__ void __launch_bounds__(128) k_pyr_down(const StreamDev *__restrict__ 
         const int wi = D.lw[l - 1], hi = D.lh[l - 1], pi = D.lp[l - 1];
         const int wo = D.lw[l], ho = D.lh[l];
         const int ncx = (wo + STAB_PD_COLS - 1) / STAB_PD_COLS, R = stab_pd_rows(ho);
-        const int xb = (local % ncx) * STAB_PD_COLS, x = xb + 4 * (lane - 1), y0 = (local / ncx) * R;
+        const int x = (local % ncx) * STAB_PD_COLS + 4 * (lane - 1), y0 = (local / ncx) * R;
         const int y1 = min(y0 + R, ho);
-        // output rows r = rmin .. rmin + nr - 1 are formed (the first is row y0 - 1
-        // or, at the top, row 0 itself); they read input rows 2 rmin - 2 .. + 2 nr + 2
-        const int rmin = max(y0 - 1, 0);
-        const int nr = 1 + (y0 > 0) + max(0, min(y1, ho - 1) - y0);
-        const int nk = 2 * nr + 3, g0 = 2 * xb - 16;
-        for (int e = lane; e < nk * (PD_SROW / 16); e += 32) {
-            const int k = e / (PD_SROW / 16), c = e - k * (PD_SROW / 16), gx = g0 + 16 * c;
-            if (gx >= 0 && gx + 16 <= pi)
-                pd_cp16(sw + k * PD_SROW + 16 * c, in + (size_t)reflect101(2 * rmin - 2 + k, hi) * pi + gx);
-        }
-        asm volatile("cp.async.wait_all;\n" ::: "memory");
-        __syncwarp();
-        // bytes 2x-4 .. 2x+11 lie inside the padded row (so in staged chunks) and
-        // 2x-2 .. 2x+8 inside the image row; other lanes read with reflection
+        // bytes 2x-4 .. 2x+11 lie inside the padded row and 2x-2 .. 2x+8 inside the image row
         const bool fast = x >= 4 && 2 * x + 8 <= wi - 1 && 2 * x + 12 <= pi;
-        auto words = [&](int k) -> PdWords {
-            if (fast) {
-                const uint8_t *q = sw + k * PD_SROW + 8 * lane + 4;   // byte 2x - 4
-                const uint2 m = *reinterpret_cast<const uint2 *>(q + 4);
-                return PdWords{*reinterpret_cast<const unsigned *>(q), m.x, m.y,
-                               *reinterpret_cast<const unsigned *>(q + 12)};
-            }
-            return pd_words(in + (size_t)reflect101(2 * rmin - 2 + k, hi) * pi, x, wi, false);
-        };
-        // row sums of staged rows k, k+1, k+2 = input rows 2r-2, 2r-1, 2r, where
-        // r is the next output row
-        int k = 0;
+        auto words = [&](int yy) { return pd_words(in + (size_t)reflect101(yy, hi) * pi, x, wi, fast); };
+        // row sums of input rows 2r-2, 2r-1, 2r, where r is the next output row
+        int r = max(y0 - 1, 0);
         unsigned a0, b0, a1, b1, a2, b2;
-        pd_hsum(words(0), a0, b0);
-        pd_hsum(words(1), a1, b1);
-        pd_hsum(words(2), a2, b2);
+        pd_hsum(words(2 * r - 2), a0, b0);
+        pd_hsum(words(2 * r - 1), a1, b1);
+        pd_hsum(words(2 * r), a2, b2);
         auto next_row = [&]() -> unsigned {
             unsigned a3, b3, a4, b4;
-            pd_hsum(words(k + 3), a3, b3);
-            pd_hsum(words(k + 4), a4, b4);
+            pd_hsum(words(2 * r + 1), a3, b3);
+            pd_hsum(words(2 * r + 2), a4, b4);
             const unsigned o = pd_vsum(a0, a1, a2, a3, a4, b0, b1, b2, b3, b4);
             a0 = a2; b0 = b2; a1 = a3; b1 = b3; a2 = a4; b2 = b4;
-            k += 2;
+            ++r;
             return o;
         };
         // rows y-1, y (replicated above row 0) and y+1 (replicated below row ho-1)
@@ -331,7 +291,6 @@ __global__ void __launch_bounds__(128) k_pyr_down(const StreamDev *__restrict__ 
             up = mid;
             mid = dn;
         }
-        __syncwarp();   // the staged rows are read; the next strip may overwrite them
     }
 }
 
@@ -364,8 +323,8 @@ void launch_pyr_down(const Launch &L, int prec, const StreamDev *S, WorkList wl,
 {
     // one warp per strip, four warps per block
     int g = grid_for(L, (wl.total + 3) / 4, prec ? occ_pyr_h() : occ_pyr_f());
-    if (prec) k_pyr_down<__half><<<g, 128, PD_BLOCK_SMEM, L.stream>>>(S, wl, l, slot_ov);
-    else k_pyr_down<float><<<g, 128, PD_BLOCK_SMEM, L.stream>>>(S, wl, l, slot_ov);
+    if (prec) k_pyr_down<__half><<<g, 128, 0, L.stream>>>(S, wl, l, slot_ov);
+    else k_pyr_down<float><<<g, 128, 0, L.stream>>>(S, wl, l, slot_ov);
 }
 
 void launch_plane_f32(const Launch &L, int prec, const StreamDev *S, int slot, int l, float *I, float *Ix, float *Iy)
@@ -386,16 +345,5 @@ void launch_plane_f32(const Launch &L, int prec, const StreamDev *S, int slot, i
     }
 OCC_FN128(occ_level0_f, k_level0<float>)
 OCC_FN128(occ_level0_h, k_level0<__half>)
-#define OCC_FN_PD(name, kern)                                                                           \
-    int name()                                                                                          \
-    {                                                                                                   \
-        static int v = 0;                                                                               \
-        if (!v) {                                                                                       \
-            if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, kern, 128, PD_BLOCK_SMEM) != cudaSuccess || \
-                v < 1)                                                                                  \
-                v = 1;                                                                                  \
-        }                                                                                               \
-        return v;                                                                                       \
-    }
-OCC_FN_PD(occ_pyr_f, k_pyr_down<float>)
-OCC_FN_PD(occ_pyr_h, k_pyr_down<__half>)
+OCC_FN128(occ_pyr_f, k_pyr_down<float>)
+OCC_FN128(occ_pyr_h, k_pyr_down<__half>)
