@@ -112,6 +112,9 @@ struct WorkList {
     const int *prefix;
     int n;
     int total;
+    // optional: items handed out by an atomic ticket (ctr[0]) instead of a
+    // fixed stride; ctr[1] counts finished groups, and the last resets both
+    unsigned *ctr = nullptr;
 };
 
 __device__ __forceinline__ int wl_stream(const WorkList &wl, int item)

@@ -367,7 +367,22 @@ __global__ void __launch_bounds__(128, MINB) k_lk(const StreamDev *__restrict__ 
     PT *sJ = reinterpret_cast<PT *>(base + 3 * bI);
     float *red = reinterpret_cast<float *>(base + 3 * bI + lk_bytes_J(rmax, ES));
     const int ngroups = (gridDim.x * blockDim.x) / NT;
-    for (int item = (blockIdx.x * blockDim.x + threadIdx.x) / NT; item < wl.total; item += ngroups) {
+    // The group's next item: a fixed stride, or with a ticket list the ticket
+    // thread 0 of the group drew (tk), broadcast to the group.
+    int tk = 0;
+    auto bcast = [&](int v) {
+        if (WPF == 1) return __shfl_sync(0xffffffffu, v, 0);
+        group_sync<WPF>(grp);
+        if (tig == 0) reinterpret_cast<int *>(red)[7] = v;
+        group_sync<WPF>(grp);
+        v = reinterpret_cast<const int *>(red)[7];
+        group_sync<WPF>(grp);
+        return v;
+    };
+    int first = (blockIdx.x * blockDim.x + threadIdx.x) / NT;
+    if (wl.ctr) first = bcast(tig == 0 ? (int)atomicAdd(wl.ctr, 1u) : 0);
+    for (int item = first; item < wl.total; item = wl.ctr ? bcast(tk) : item + ngroups) {
+        if (wl.ctr && tig == 0) tk = (int)atomicAdd(wl.ctr, 1u);   // drawn now, used after this item
         const int s = wl_stream(wl, item);
         const StreamDev &D = S[s];
         StreamState *st = D.st;
@@ -406,6 +421,11 @@ __global__ void __launch_bounds__(128, MINB) k_lk(const StreamDev *__restrict__ 
             atomicAdd((unsigned long long *)&st->iters, (unsigned long long)iters);
             atomicAdd((unsigned long long *)&st->tpl, (unsigned long long)tpl);
         }
+    }
+    // every group has drawn a ticket past the end; the last to finish resets the list
+    if (wl.ctr && tig == 0 && atomicAdd(wl.ctr + 1, 1u) == (unsigned)(ngroups - 1)) {
+        atomicExch(wl.ctr, 0u);
+        atomicExch(wl.ctr + 1, 0u);
     }
 }
 

@@ -248,6 +248,7 @@ stab_status build(Pipeline &pp, int n, const int *w, const int *h, const int *C,
     mk(&pp.wl_lk, [](const StreamDev &D) { return D.K; });
     mk(&pp.wl_warp, [](const StreamDev &D) { return ((D.w + STAB_TW - 1) / STAB_TW) * ((D.h + STAB_WTH - 1) / STAB_WTH); });
     for (auto &e : lists) all.insert(all.end(), e.second.begin(), e.second.end());
+    all.push_back(0); all.push_back(0);   // the tracker's ticket and finished-group counters
     if (cudaMalloc(&pp.prefix, all.size() * sizeof(int)) != cudaSuccess) return fail(pp.err, STAB_ERR_OOM, "cudaMalloc");
     cudaMemcpy(pp.prefix, all.data(), all.size() * sizeof(int), cudaMemcpyHostToDevice);
     size_t o = 0;
@@ -255,6 +256,8 @@ stab_status build(Pipeline &pp, int n, const int *w, const int *h, const int *C,
         e.first->prefix = pp.prefix + o;
         o += e.second.size();
     }
+    // features of unequal cost (iterations, lost tracks) go to whichever group is free
+    pp.wl_lk.ctr = reinterpret_cast<unsigned *>(pp.prefix + o);
     // kernel attributes and occupancy queries happen here, outside any capture
     occ_level0_f(); occ_level0_h(); occ_pyr_f(); occ_pyr_h();
     warm_detect(); warm_warp(); warm_lk();
