@@ -49,37 +49,26 @@ __device__ __forceinline__ float lambda32(int a, int b, int c)
     return __fdiv_rn(num, den);
 }
 
-// One block for all streams.  With use_cond (a captured batched step) it also
-// sets the condition of the graph node around detection: the response, filter
-// and selection run only when some stream detects (for the others they would
-// return at once).
-__global__ void k_begin(const StreamDev *__restrict__ S, int n, long long t_ov, int force_due,
-                        cudaGraphConditionalHandle cond, int use_cond)
+__global__ void k_begin(const StreamDev *__restrict__ S, int n, long long t_ov, int force_due)
 {
-    int any = 0;
-    for (int s = threadIdx.x; s < n; s += blockDim.x) {
-        const StreamDev &D = S[s];
-        StreamState *st = D.st;
-        long long t = t_ov >= 0 ? t_ov : st->t;
-        st->t = t;
-        const long long tb = t - D.lag;   // transition tracked by this step: frames tb-1 -> tb
-        int due;
-        if (force_due) due = 1;
-        else due = (tb >= 1) && (st->n_feat == 0 || ((tb - 1) % D.period) == 0 || st->n_feat < D.min_tracks);
-        st->due = due;
-        st->n_cand = 0;
-        st->n_sel = 0;
-        st->n_above = 0;
-        st->lam_max = 0;
-        st->blocks_done = 0;
-        st->iters = 0;
-        st->tpl = 0;
-        any |= due;
-    }
-    if (use_cond) {
-        any = __syncthreads_or(any);
-        if (threadIdx.x == 0) cudaGraphSetConditional(cond, any ? 1u : 0u);   // one caller only
-    }
+    int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= n) return;
+    const StreamDev &D = S[s];
+    StreamState *st = D.st;
+    long long t = t_ov >= 0 ? t_ov : st->t;
+    st->t = t;
+    const long long tb = t - D.lag;   // transition tracked by this step: frames tb-1 -> tb
+    int due;
+    if (force_due) due = 1;
+    else due = (tb >= 1) && (st->n_feat == 0 || ((tb - 1) % D.period) == 0 || st->n_feat < D.min_tracks);
+    st->due = due;
+    st->n_cand = 0;
+    st->n_sel = 0;
+    st->n_above = 0;
+    st->lam_max = 0;
+    st->blocks_done = 0;
+    st->iters = 0;
+    st->tpl = 0;
 }
 
 // One pixel row's bytes at columns x-3 .. x+6, clamped into the frame.  Inside
@@ -440,10 +429,9 @@ __global__ void __launch_bounds__(1024) k_select(const StreamDev *__restrict__ S
 
 }  // namespace
 
-void launch_begin(const Launch &L, const StreamDev *S, int n, long long t_ov, int force_due,
-                  cudaGraphConditionalHandle cond, int use_cond)
+void launch_begin(const Launch &L, const StreamDev *S, int n, long long t_ov, int force_due)
 {
-    k_begin<<<1, 256, 0, L.stream>>>(S, n, t_ov, force_due, cond, use_cond);
+    k_begin<<<(n + 63) / 64, 64, 0, L.stream>>>(S, n, t_ov, force_due);
 }
 
 static int occ_response()

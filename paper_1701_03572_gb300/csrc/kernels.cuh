@@ -87,8 +87,7 @@ void warm_detect();
 void warm_warp();
 void warm_lk();
 
-void launch_begin(const Launch &L, const StreamDev *S, int n, long long t_ov, int force_due,
-                  cudaGraphConditionalHandle cond = 0, int use_cond = 0);
+void launch_begin(const Launch &L, const StreamDev *S, int n, long long t_ov, int force_due);
 void launch_response(const Launch &L, const StreamDev *S, WorkList wl, DetIO io);
 void launch_filter(const Launch &L, const StreamDev *S, WorkList wl);
 void launch_select(const Launch &L, const StreamDev *S, int n, DetIO io);

@@ -40,8 +40,6 @@ struct Pipeline {
     cudaStream_t hs_in = nullptr, hs_comp = nullptr, hs_out = nullptr;
     // second branch of the step: detection runs beside the pyramid levels >= 1
     cudaStream_t side = nullptr, side2 = nullptr;
-    cudaStream_t condcap = nullptr;   // captures the body of the conditional detection node
-    cudaError_t cap_err = cudaSuccess;  // first error while building the conditional node
     cudaEvent_t ev_fork = nullptr, ev_det = nullptr, ev_warp = nullptr;
     cudaEvent_t ev_in[2] = {}, ev_comp[4] = {}, ev_out[4] = {}, ev_join = nullptr;
     bool host_mode = false;   // the last step was a host-buffer step
@@ -65,7 +63,7 @@ struct Pipeline {
         if (gexec) cudaGraphExecDestroy(gexec);
         if (graph) cudaGraphDestroy(graph);
         if (cap) cudaStreamDestroy(cap);
-        for (cudaStream_t x : {hs_in, hs_comp, hs_out, side, side2, condcap})
+        for (cudaStream_t x : {hs_in, hs_comp, hs_out, side, side2})
             if (x) cudaStreamDestroy(x);
         for (cudaEvent_t e : {ev_fork, ev_det, ev_warp})
             if (e) cudaEventDestroy(e);
@@ -294,56 +292,14 @@ struct Prof {
     }
 };
 
-// Detection (response, filter, select) on the side stream being captured, as
-// the body of a conditional IF node whose condition k_begin sets, so that the
-// steps where no stream detects skip the three launches.
-cudaError_t capture_detection_if(Pipeline &pp, cudaGraphConditionalHandle cond)
-{
-    cudaStreamCaptureStatus cs;
-    cudaGraph_t g;
-    const cudaGraphNode_t *deps = nullptr;
-    const cudaGraphEdgeData *edata = nullptr;
-    size_t nd = 0;
-    cudaError_t e = cudaStreamGetCaptureInfo(pp.side, &cs, nullptr, &g, &deps, &edata, &nd);
-    if (e != cudaSuccess) return e;
-    cudaGraphNodeParams cp = {};
-    cp.type = cudaGraphNodeTypeConditional;
-    cp.conditional.handle = cond;
-    cp.conditional.type = cudaGraphCondTypeIf;
-    cp.conditional.size = 1;
-    cudaGraphNode_t node;
-    if ((e = cudaGraphAddNode(&node, g, deps, edata, nd, &cp)) != cudaSuccess) return e;
-    cudaGraph_t body = cp.conditional.phGraph_out[0];
-    if ((e = cudaStreamBeginCaptureToGraph(pp.condcap, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal)) !=
-        cudaSuccess)
-        return e;
-    const Launch Lc{pp.condcap, pp.sms};
-    launch_response(Lc, pp.ds, pp.wl_resp, DetIO{});
-    launch_filter(Lc, pp.ds, pp.wl_filter);
-    launch_select(Lc, pp.ds, pp.n, DetIO{});
-    const cudaError_t el = cudaGetLastError();   // a failed launch; the body capture is ended either way
-    if ((e = cudaStreamEndCapture(pp.condcap, &body)) != cudaSuccess) return e;
-    if (el != cudaSuccess) return el;
-    return cudaStreamUpdateCaptureDependencies(pp.side, &node, nullptr, 1, cudaStreamSetCaptureDependencies);
-}
-
-// capture: the step is being captured into the batch's graph (stream s)
-void enqueue_step(Pipeline &pp, cudaStream_t s, Prof *pf = nullptr, bool capture = false)
+void enqueue_step(Pipeline &pp, cudaStream_t s, Prof *pf = nullptr)
 {
     Launch L{s, pp.sms};
     static const char *pyr_names[STAB_MAXL] = {"", "pyr_down_1", "pyr_down_2", "pyr_down_3", "pyr_down_4",
                                                 "pyr_down_5", "pyr_down_6", "pyr_down_7"};
     auto mark = [&](const char *n) { if (pf) pf->mark(n); };
     mark(nullptr);
-    cudaGraphConditionalHandle cond = 0;
-    if (capture) {
-        cudaStreamCaptureStatus cs;
-        cudaGraph_t g;
-        if (cudaStreamGetCaptureInfo(s, &cs, nullptr, &g, nullptr, nullptr, nullptr) != cudaSuccess ||
-            cudaGraphConditionalHandleCreate(&cond, g, 0, cudaGraphCondAssignDefault) != cudaSuccess)
-            capture = false;   // the error stays pending and fails the capture
-    }
-    launch_begin(L, pp.ds, pp.n, -1, 0, cond, capture ? 1 : 0);
+    launch_begin(L, pp.ds, pp.n, -1, 0);
     mark("begin");
     if (pf) {   // measured one kernel at a time
         launch_level0(L, pp.prec, pp.ds, pp.wl_l0, FrameSrc{nullptr, 0, 0, 0});
@@ -377,14 +333,9 @@ void enqueue_step(Pipeline &pp, cudaStream_t s, Prof *pf = nullptr, bool capture
         cudaStreamWaitEvent(pp.side2, pp.ev_fork, 0);
         launch_warp(Lw, pp.ds, pp.wl_warp, WarpIO{});
         cudaEventRecord(pp.ev_warp, pp.side2);
-        if (capture) {
-            const cudaError_t e = capture_detection_if(pp, cond);
-            if (e != cudaSuccess) pp.cap_err = e;   // reported once the capture has ended
-        } else {
-            launch_response(Ls, pp.ds, pp.wl_resp, DetIO{});
-            launch_filter(Ls, pp.ds, pp.wl_filter);
-            launch_select(Ls, pp.ds, pp.n, DetIO{});
-        }
+        launch_response(Ls, pp.ds, pp.wl_resp, DetIO{});
+        launch_filter(Ls, pp.ds, pp.wl_filter);
+        launch_select(Ls, pp.ds, pp.n, DetIO{});
         launch_lk(Ls, pp.prec, pp.rcode(), pp.lk_variant, pp.ds, pp.wl_lk, LkIO{});
         launch_compact(Ls, pp.ds, pp.n, CompactIO{});
         launch_fit(Ls, pp.ds, pp.n, FitIO{}, 1, pp.hmax);
@@ -639,7 +590,6 @@ stab_status stab_batch_create(int n, const stab_stream_desc *d, int ring, stab_b
     if (s == STAB_OK && (cudaStreamCreateWithFlags(&b->pp.cap, cudaStreamNonBlocking) != cudaSuccess ||
                          cudaStreamCreateWithFlags(&b->pp.side, cudaStreamNonBlocking) != cudaSuccess ||
                          cudaStreamCreateWithFlags(&b->pp.side2, cudaStreamNonBlocking) != cudaSuccess ||
-                         cudaStreamCreateWithFlags(&b->pp.condcap, cudaStreamNonBlocking) != cudaSuccess ||
                          cudaEventCreateWithFlags(&b->pp.ev_fork, cudaEventDisableTiming) != cudaSuccess ||
                          cudaEventCreateWithFlags(&b->pp.ev_det, cudaEventDisableTiming) != cudaSuccess ||
                          cudaEventCreateWithFlags(&b->pp.ev_warp, cudaEventDisableTiming) != cudaSuccess))
@@ -689,15 +639,8 @@ stab_status stab_batch_step(stab_batch *b, int use_graph, void *stream)
         if (!pp.gexec) {
             if (cudaStreamBeginCapture(pp.cap, cudaStreamCaptureModeThreadLocal) != cudaSuccess)
                 return cuda_check(pp.err, "begin capture");
-            pp.cap_err = cudaSuccess;
-            enqueue_step(pp, pp.cap, nullptr, true);
+            enqueue_step(pp, pp.cap);
             if (cudaStreamEndCapture(pp.cap, &pp.graph) != cudaSuccess) return cuda_check(pp.err, "end capture");
-            if (pp.cap_err != cudaSuccess) {
-                pp.err = std::string("conditional detection node: ") + cudaGetErrorString(pp.cap_err);
-                cudaGraphDestroy(pp.graph);
-                pp.graph = nullptr;
-                return STAB_ERR_CUDA;
-            }
             if (cudaGraphInstantiate(&pp.gexec, pp.graph, 0) != cudaSuccess) return cuda_check(pp.err, "instantiate");
         }
         if (cudaGraphLaunch(pp.gexec, s) != cudaSuccess) return cuda_check(pp.err, "graph launch");
