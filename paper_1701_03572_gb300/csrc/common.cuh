@@ -24,8 +24,7 @@ __host__ __device__ inline int stab_pslot(long long f) { return (int)(((f % STAB
 #define STAB_HBINS 4096      // response histogram: top 12 bits of the (non-negative) float score
 #define STAB_HSHIFT 19
 #define STAB_SEL_SMEM 12288  // selection keys held in shared memory
-#define STAB_TW 64           // image tile: 64 x 16 pixels, 256 threads x 4 pixels
-#define STAB_TH 16
+#define STAB_TW 64           // warp output tile width (pixels)
 // Corner response work: strips of 128 threads x 4 columns x 32 rows of the ROI.
 #define STAB_RS_THREADS 128
 #define STAB_RS_ROWS 32

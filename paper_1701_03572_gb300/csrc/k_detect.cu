@@ -2,13 +2,13 @@
 // (Sec. 3.1, Eq. 2) and exact top-K selection.
 //
 //  k_begin     per stream: frame index, whether detection is due, counters.
-//  k_response  64 x 16 ROI tiles staged in shared memory with a 3-px halo:
-//              Sobel 3x3 -> integer tensor over a 3x3 box -> FP32 min
+//  k_response  vertical strips of the ROI (a thread walks 4 columns down 32
+//              rows): Sobel 3x3 -> integer tensor over a 3x3 box -> FP32 min
 //              eigenvalue -> 3x3 non-maximum suppression.  Survivors are
 //              appended as 64-bit keys (score bits << 32 | ~raster index), so
 //              that "larger key" means "higher score, then lower index", and
 //              counted in a 4096-bin histogram of the score's top 12 bits.  The
-//              last tile of a stream to finish turns the histogram into the
+//              last strip of a stream to finish turns the histogram into the
 //              bin where the K-th key lives.
 //  k_filter    keeps keys at or above that bin and above q * max.
 //  k_select    one CTA per stream: radix select of the K-th largest key in
@@ -109,7 +109,7 @@ constexpr int RS_CAP = 1024;
 // products summed over 3 columns (x-1 .. x+4) are kept for two rows more; three
 // such rows give the 3x3 structure tensor and the score two rows back, and
 // three score rows give the NMS of the row before.  Integer sums are exact;
-// the score is lambda32 of them, as in the tile form.
+// the score is lambda32 of them.
 __global__ void __launch_bounds__(STAB_RS_THREADS) k_response(const StreamDev *__restrict__ S, WorkList wl, DetIO io)
 {
     __shared__ unsigned smax;
@@ -255,7 +255,7 @@ __global__ void __launch_bounds__(STAB_RS_THREADS) k_response(const StreamDev *_
         }
         __syncthreads();
         if (s_last) {
-            // This is the stream's last tile: every append and histogram count is
+            // This is the stream's last strip: every append and histogram count is
             // visible (they were made before each tile's fence and ticket).
             __threadfence();
             unsigned lm = __ldcg(&st->lam_max);
