@@ -256,7 +256,7 @@ __global__ void __launch_bounds__(STAB_RS_THREADS) k_response(const StreamDev *_
         __syncthreads();
         if (s_last) {
             // This is the stream's last strip: every append and histogram count is
-            // visible (they were made before each tile's fence and ticket).
+            // visible (they were made before each strip's fence and ticket).
             __threadfence();
             unsigned lm = __ldcg(&st->lam_max);
             float thr = __fmul_rn(D.quality, __uint_as_float(lm));
