@@ -48,7 +48,7 @@ LK_FLOP_TEMPLATE, LK_FLOP_ITER = 27, 12
 # (profiles/lk_dram_16x1080p.md: dram__bytes_read.sum + dram__bytes_write.sum
 # of one launch on this workload, 16 streams); used only while the kernel
 # source is unchanged.
-TRAFFIC = {"lk": {"file": "k_lk.cu", "sha": "8e5fe466ad942f07", "bytes_per_launch": 190478592 + 3550208}}
+TRAFFIC = {"lk": {"file": "k_lk.cu", "sha": "ff90049d60006f6b", "bytes_per_launch": 190591744 + 3222784}}
 
 
 def config_dict(streams):
