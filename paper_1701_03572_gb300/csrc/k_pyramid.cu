@@ -60,6 +60,37 @@ __device__ __forceinline__ unsigned luma1(const uint8_t *p, int C)
     return C == 1 ? (unsigned)__ldg(p) : (77u * __ldg(p) + 150u * __ldg(p + 1) + 29u * __ldg(p + 2) + 128u) >> 8;
 }
 
+// The aligned words of one row that the fast path reads: RGB bytes 3x-4 ..
+// 3x+15 (five words), gray bytes x-4 .. x+7 (three).
+struct L0Words { unsigned w[5]; };
+
+__device__ __forceinline__ L0Words l0_words(const uint8_t *__restrict__ src, int pitch, int C, int x, int yy)
+{
+    const uint8_t *row = src + (size_t)yy * pitch;
+    const unsigned *q = reinterpret_cast<const unsigned *>(row + C * x) - 1;
+    L0Words v;
+#pragma unroll
+    for (int k = 0; k < 5; ++k) v.w[k] = (C == 3 || k < 3) ? __ldg(q + k) : 0u;
+    return v;
+}
+
+// Luma of columns x-1 (byte 0 of lo), x..x+3 (mid), x+4 (byte 0 of hi) from a
+// row's fast-path words.
+__device__ __forceinline__ void luma_words(const L0Words &v, int C, unsigned &lo, unsigned &mid, unsigned &hi)
+{
+    if (C == 3) {
+        const unsigned wl = v.w[0], wr = v.w[4];
+        mid = luma4(v.w[1], v.w[2], v.w[3]);
+        // x-1: bytes 1..3 of the word before; x+4: bytes 0..2 of the word after
+        lo = (77u * ((wl >> 8) & 255u) + 150u * ((wl >> 16) & 255u) + 29u * (wl >> 24) + 128u) >> 8;
+        hi = (77u * (wr & 255u) + 150u * ((wr >> 8) & 255u) + 29u * ((wr >> 16) & 255u) + 128u) >> 8;
+    } else {
+        lo = v.w[0] >> 24;
+        mid = v.w[1];
+        hi = v.w[2] & 255u;
+    }
+}
+
 // Luma of columns x-1 (byte 0 of lo), x..x+3 (mid), x+4 (byte 0 of hi) of row yy.
 __device__ __forceinline__ void luma_row(const uint8_t *__restrict__ src, int pitch, int C, int w, int x, int yy,
                                         bool fast, unsigned &lo, unsigned &mid, unsigned &hi)
@@ -175,9 +206,19 @@ __global__ void __launch_bounds__(L0_GROUPS) k_level0(const StreamDev *__restric
         luma_row(src, pitch, C, w, x, max(y0 - 1, 0), fast, dummy0, pmid, dummy1);
         luma_row(src, pitch, C, w, x, y0, fast, clo, cmid, chi);
         (void)plo; (void)phi;
+        // fast path: the words of row y + 2 are in flight while row y + 1's luma
+        // and row y's planes are formed
+        L0Words nw{};
+        if (fast) nw = l0_words(src, pitch, C, x, min(y0 + 1, h - 1));
         for (int y = y0; y < y1; ++y) {
             unsigned nlo, nmid, nhi;
-            luma_row(src, pitch, C, w, x, min(y + 1, h - 1), fast, nlo, nmid, nhi);
+            if (fast) {
+                const L0Words cw = nw;
+                if (y + 1 < y1) nw = l0_words(src, pitch, C, x, min(y + 2, h - 1));
+                luma_words(cw, C, nlo, nmid, nhi);
+            } else {
+                luma_row(src, pitch, C, w, x, min(y + 1, h - 1), false, nlo, nmid, nhi);
+            }
             emit_row<PT>(D, slot, 0, x, y, w, pmid, clo, cmid, chi, nmid);
             pmid = cmid;
             clo = nlo; cmid = nmid; chi = nhi;
