@@ -42,7 +42,7 @@ def _cuda(a):
 
 # ----------------------------------------------------------------- pyramid --
 @pytest.mark.parametrize("w,h,L,prec", [(320, 240, 3, 0), (640, 480, 4, 1), (333, 257, 4, 0), (17, 16, 1, 1),
-                                        (131, 67, 5, 0)])
+                                        (131, 67, 5, 0), (1001, 803, 3, 1)])
 def test_pyramid_and_planes_bit_exact(w, h, L, prec):
     rng = np.random.default_rng(w * 7 + h)
     img = rng.integers(0, 256, (h, w), dtype=np.uint8)
@@ -59,14 +59,22 @@ def test_pyramid_and_planes_bit_exact(w, h, L, prec):
     assert ctx.sync() == 0
 
 
-def test_pyramid_rgb_luma_1080p():
+@pytest.mark.parametrize("prec", [0, 1])
+def test_pyramid_rgb_luma_1080p(prec):
+    # level 1 (960 x 540) takes the tallest REDUCE strips and eight column chunks,
+    # level 2 the 4-row strips, levels 3-4 the 2-row ones
     clip = _clip(2, 1, 2)
     rgb = clip["frames"][0].numpy()
-    ctx = S.Context(1920, 1080, _params(levels=5))
+    ctx = S.Context(1920, 1080, _params(levels=5, precision=prec))
     levels = ctx.pyramid(_cuda(rgb))
     ref = O.pyramid(O.luma(rgb), 5)
     for l in range(5):
         assert np.array_equal(levels[l].cpu().numpy(), ref[l]), f"level {l}"
+        I, Ix, Iy = ctx.planes(l)
+        rI, rIx, rIy = O.grad_planes(ref[l])
+        assert np.array_equal(I.cpu().numpy(), rI), f"I, level {l}"
+        assert np.array_equal(Ix.cpu().numpy(), rIx) and np.array_equal(Iy.cpu().numpy(), rIy), f"grad, level {l}"
+    assert ctx.sync() == 0
 
 
 # ---------------------------------------------------------------- corners --
