@@ -71,7 +71,7 @@ __global__ void k_begin(const StreamDev *__restrict__ S, int n, long long t_ov, 
     st->tpl = 0;
 }
 
-// One pixel row's bytes at columns x-3 .. x+6, clamped into the frame.  Inside
+// One pixel row's bytes at columns x-1 .. x+4, clamped into the frame.  Inside
 // the row they come from three aligned words (columns x-4 .. x+7), which the
 // caller loads one row ahead (rs_words); near a border they are read singly.
 struct RsWords { unsigned w0, w1, w2; };
@@ -83,16 +83,16 @@ __device__ __forceinline__ RsWords rs_words(const uint8_t *__restrict__ g, int p
 }
 
 __device__ __forceinline__ void rs_pixels(const uint8_t *__restrict__ g, int pitch, int w, int h, int x, int yy,
-                                          bool fast, RsWords v, int (&p)[10])
+                                          bool fast, RsWords v, int (&p)[6])
 {
     if (fast) {
-        p[0] = (v.w0 >> 8) & 255u; p[1] = (v.w0 >> 16) & 255u; p[2] = v.w0 >> 24;
-        p[3] = v.w1 & 255u; p[4] = (v.w1 >> 8) & 255u; p[5] = (v.w1 >> 16) & 255u; p[6] = v.w1 >> 24;
-        p[7] = v.w2 & 255u; p[8] = (v.w2 >> 8) & 255u; p[9] = (v.w2 >> 16) & 255u;
+        p[0] = v.w0 >> 24;
+        p[1] = v.w1 & 255u; p[2] = (v.w1 >> 8) & 255u; p[3] = (v.w1 >> 16) & 255u; p[4] = v.w1 >> 24;
+        p[5] = v.w2 & 255u;
     } else {
         const uint8_t *row = g + (size_t)clampi(yy, 0, h - 1) * pitch;
 #pragma unroll
-        for (int k = 0; k < 10; ++k) p[k] = __ldg(row + clampi(x - 3 + k, 0, w - 1));
+        for (int k = 0; k < 6; ++k) p[k] = __ldg(row + clampi(x - 1 + k, 0, w - 1));
     }
 }
 
@@ -104,12 +104,14 @@ constexpr int RS_CAP = 1024;
 // Corner response (Eq. 2), NMS and candidate list as barrier-free vertical
 // strips: a thread owns ROI columns x .. x+3 of a 32-row strip and walks its
 // pixel rows once.  Per pixel row it forms the separable Sobel parts
-// (horizontal difference and [1 2 1] smoothing) of columns x-2 .. x+5 and
-// keeps two rows of them; three rows give gx, gy of the previous row, whose
-// products summed over 3 columns (x-1 .. x+4) are kept for two rows more; three
-// such rows give the 3x3 structure tensor and the score two rows back, and
-// three score rows give the NMS of the row before.  Integer sums are exact;
-// the score is lambda32 of them.
+// (horizontal difference and [1 2 1] smoothing) of its 4 columns and keeps two
+// rows of them; three rows give gx, gy of the previous row, whose products are
+// summed over 3 columns (the products of columns x-1 and x+4 come from the
+// neighbouring lanes) and kept for two rows more; three such rows give the 3x3
+// structure tensor and the score two rows back, and three score rows (the
+// neighbours' outer scores again by shuffle) give the NMS of the row before.
+// Lanes 0 and 31 of a warp compute their columns only for lanes 1 and 30 and
+// emit nothing.  Integer sums are exact; the score is lambda32 of them.
 __global__ void __launch_bounds__(STAB_RS_THREADS) k_response(const StreamDev *__restrict__ S, WorkList wl, DetIO io)
 {
     __shared__ unsigned smax;
@@ -130,16 +132,18 @@ __global__ void __launch_bounds__(STAB_RS_THREADS) k_response(const StreamDev *_
         else { g = D.u8[stab_pslot(st->t - D.lag - 1)][0]; pitch = D.lp[0]; }
         const int w = D.w, h = D.h;
         const int rx1 = D.roi_x1, ry1 = D.roi_y1;
-        const int ngx = (rx1 - D.roi_x0 + 4 * STAB_RS_THREADS - 1) / (4 * STAB_RS_THREADS);
-        const int x = D.roi_x0 + ((local % ngx) * STAB_RS_THREADS + tid) * 4;
+        const int ngx = (rx1 - D.roi_x0 + STAB_RS_COLS - 1) / STAB_RS_COLS;
+        const int x = D.roi_x0 + (local % ngx) * STAB_RS_COLS + (tid >> 5) * 120 + 4 * (lane - 1);
+        const bool owner = lane >= 1 && lane <= 30;   // lanes 0 and 31 only supply neighbours
         const int y0 = D.roi_y0 + (local / ngx) * STAB_RS_ROWS;
         const int nrows = min(STAB_RS_ROWS, ry1 - y0);
         const bool fast = x >= 4 && x + 8 <= w && ((x | pitch) & 3) == 0 && (reinterpret_cast<uintptr_t>(g) & 3) == 0;
         if (tid == 0) { smax = 0; s_n = 0; s_valid = RS_CAP; }
         __syncthreads();
-        int d1[8] = {0}, d2[8] = {0}, s1[8] = {0}, s2[8] = {0};      // Sobel parts of pixel rows py-1, py-2
-        int ha1[6] = {0}, hb1[6] = {0}, hc1[6] = {0};                // tensor row sums of row py-2
-        int ha2[6] = {0}, hb2[6] = {0}, hc2[6] = {0};                // ... of row py-3
+        // own columns x .. x+3; the scores also hold columns x-1 (index 0) and x+4 (5)
+        int d1[4] = {0}, d2[4] = {0}, s1[4] = {0}, s2[4] = {0};      // Sobel parts of pixel rows py-1, py-2
+        int ha1[4] = {0}, hb1[4] = {0}, hc1[4] = {0};                // tensor row sums of row py-2
+        int ha2[4] = {0}, hb2[4] = {0}, hc2[4] = {0};                // ... of row py-3
         float l1[6] = {0.f}, l2[6] = {0.f};                          // scores of rows py-3, py-4
         unsigned lmax = 0;
         RsWords nxt = fast ? rs_words(g, pitch, h, x, y0 - 3) : RsWords{0u, 0u, 0u};
@@ -147,33 +151,39 @@ __global__ void __launch_bounds__(STAB_RS_THREADS) k_response(const StreamDev *_
             const int py = y0 - 3 + k;
             const RsWords cur = nxt;
             if (fast && k + 1 < nrows + 6) nxt = rs_words(g, pitch, h, x, py + 1);   // next row in flight
-            int p[10];
+            int p[6];
             rs_pixels(g, pitch, w, h, x, py, fast, cur, p);
-            int d0[8], s0[8];
+            int d0[4], s0[4];
 #pragma unroll
-            for (int j = 0; j < 8; ++j) {
+            for (int j = 0; j < 4; ++j) {
                 d0[j] = p[j + 2] - p[j];
                 s0[j] = p[j] + 2 * p[j + 1] + p[j + 2];
             }
-            // gx, gy of row py-1 at columns x-2 .. x+5; products summed over 3 columns
-            int A[8], B[8], C[8];
+            // gx, gy of row py-1 at columns x .. x+3 (index 1 .. 4); the products of
+            // columns x-1 and x+4 come from the neighbouring lanes
+            int A[6], B[6], C[6];
 #pragma unroll
-            for (int j = 0; j < 8; ++j) {
+            for (int j = 0; j < 4; ++j) {
                 const int gx = d2[j] + 2 * d1[j] + d0[j], gy = s0[j] - s2[j];
-                A[j] = gx * gx; B[j] = gx * gy; C[j] = gy * gy;
+                A[j + 1] = gx * gx; B[j + 1] = gx * gy; C[j + 1] = gy * gy;
             }
-            int ha0[6], hb0[6], hc0[6];
+            A[0] = __shfl_up_sync(0xffffffffu, A[4], 1); A[5] = __shfl_down_sync(0xffffffffu, A[1], 1);
+            B[0] = __shfl_up_sync(0xffffffffu, B[4], 1); B[5] = __shfl_down_sync(0xffffffffu, B[1], 1);
+            C[0] = __shfl_up_sync(0xffffffffu, C[4], 1); C[5] = __shfl_down_sync(0xffffffffu, C[1], 1);
+            int ha0[4], hb0[4], hc0[4];
 #pragma unroll
-            for (int i = 0; i < 6; ++i) {
+            for (int i = 0; i < 4; ++i) {
                 ha0[i] = A[i] + A[i + 1] + A[i + 2];
                 hb0[i] = B[i] + B[i + 1] + B[i + 2];
                 hc0[i] = C[i] + C[i + 1] + C[i + 2];
             }
-            // score of row py-2 at columns x-1 .. x+4
+            // score of row py-2 at columns x .. x+3, and of x-1, x+4 from the neighbours
             float l0[6];
 #pragma unroll
-            for (int i = 0; i < 6; ++i)
-                l0[i] = lambda32(ha2[i] + ha1[i] + ha0[i], hb2[i] + hb1[i] + hb0[i], hc2[i] + hc1[i] + hc0[i]);
+            for (int i = 0; i < 4; ++i)
+                l0[i + 1] = lambda32(ha2[i] + ha1[i] + ha0[i], hb2[i] + hb1[i] + hb0[i], hc2[i] + hc1[i] + hc0[i]);
+            l0[0] = __shfl_up_sync(0xffffffffu, l0[4], 1);
+            l0[5] = __shfl_down_sync(0xffffffffu, l0[1], 1);
             // NMS of row py-3 (scores l2 = row py-4, l1 = py-3, l0 = py-2)
             unsigned long long keys[2];
             int nk = 0;
@@ -181,7 +191,7 @@ __global__ void __launch_bounds__(STAB_RS_THREADS) k_response(const StreamDev *_
             if (k >= 6) {
 #pragma unroll
                 for (int c = 0; c < 4; ++c) {
-                    if (x + c < rx1) {
+                    if (owner && x + c < rx1) {
                         const float v = l1[c + 1];
                         lmax = max(lmax, __float_as_uint(v));
                         // strict maximum over the 3x3 neighbourhood; a tie goes to the lower raster index
@@ -226,12 +236,13 @@ __global__ void __launch_bounds__(STAB_RS_THREADS) k_response(const StreamDev *_
             }
             // shift the row windows
 #pragma unroll
-            for (int j = 0; j < 8; ++j) { d2[j] = d1[j]; d1[j] = d0[j]; s2[j] = s1[j]; s1[j] = s0[j]; }
+            for (int j = 0; j < 4; ++j) { d2[j] = d1[j]; d1[j] = d0[j]; s2[j] = s1[j]; s1[j] = s0[j]; }
 #pragma unroll
-            for (int i = 0; i < 6; ++i) {
+            for (int i = 0; i < 4; ++i) {
                 ha2[i] = ha1[i]; ha1[i] = ha0[i]; hb2[i] = hb1[i]; hb1[i] = hb0[i]; hc2[i] = hc1[i]; hc1[i] = hc0[i];
-                l2[i] = l1[i]; l1[i] = l0[i];
             }
+#pragma unroll
+            for (int i = 0; i < 6; ++i) { l2[i] = l1[i]; l1[i] = l0[i]; }
         }
         // block max of the score; the buffered candidates go out with one atomic
         for (int o = 16; o; o >>= 1) lmax = max(lmax, __shfl_xor_sync(0xffffffffu, lmax, o));
