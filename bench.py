@@ -237,7 +237,10 @@ def run_ours(args):
            "warmup": args.warmup, "ms_per_step": round(total_ms / args.steps, 4), "higher_is_better": True,
            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "storage": "u8 frames, f16 I/Ix/Iy planes",
            "data": "synthetic", "config": config_dict(B),
-           "latency_ms": {"p50": round(p50, 4), "p99": round(p99, 4), "per": "batch step (16 frames)"},
+           "latency_ms": {"p50": round(p50, 4), "p99": round(p99, 4), "per": "batch step (16 frames)",
+                          # not in the step latency: the step that ingests frame t emits frame
+                          # t - (BATCH_OUT_LAG + 1 + W/2), of which W/2 is the smoother's lookahead
+                          "output_delay_frames": S.BATCH_OUT_LAG + 1 + A, "smoothing_lookahead_frames": A},
            "plain": plain, "e2e": e2e, "roofline": roof,
            "kernels_ms": {k: round(v, 4) for k, v in kavg.items()},
            "gpu_launches": n_k * args.steps, "clocks": clk, "wall_s": round(wall, 3), "autotune": tuned,
