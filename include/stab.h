@@ -257,13 +257,12 @@ stab_status stab_warp(stab_ctx *ctx, const uint8_t *src_dev, int src_pitch, uint
 /* Batched multi-stream pipeline (one CUDA-graph launch per frame step).
  * Stream i has its own size, channel count and parameters.  The step that
  * takes frame t of every stream from its input ring slot (t % ring) builds
- * frame t's pyramid and, as a parallel branch of the same graph, tracks the
+ * frame t's pyramid and, as parallel branches of the same graph, tracks the
  * previous transition (frames t-2 -> t-1: detection when due, tracker, fit,
- * smoothing); after the pyramid it composes the frame whose smoothed map the
- * previous step produced and writes the stabilised frame u = t - 3 - W_i/2 of
- * stream i to its output buffer (when u >= 0).  The motions it reports are
- * those of the transition t-1; the results equal those of the single-stream
- * calls. */
+ * smoothing) and composes the frame whose smoothed map the previous step
+ * produced, writing the stabilised frame u = t - 3 - W_i/2 of stream i to its
+ * output buffer (when u >= 0).  The motions it reports are those of the
+ * transition t-1; the results equal those of the single-stream calls. */
 typedef struct {
     int w, h, channels;
     stab_params params;
