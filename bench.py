@@ -44,10 +44,9 @@ FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
 # (3 x 7 flop) + G accumulation (3 FMA = 6 flop) = 27; iteration = bilinear J
 # (7) + residual (1) + b accumulation (2 FMA = 4) = 12.
 LK_FLOP_TEMPLATE, LK_FLOP_ITER = 27, 12
-# DRAM traffic per launch of the dominant kernel from an ncu capture
-# (profiles/lk_dram_16x1080p.md: dram__bytes_read.sum + dram__bytes_write.sum
-# of one launch on this workload, 16 streams); used only while the kernel
-# source is unchanged.
+# DRAM traffic per launch of the dominant kernel from one ncu capture
+# (dram__bytes_read.sum + dram__bytes_write.sum of one launch on this workload,
+# 16 streams); used only while the kernel source is unchanged.
 TRAFFIC = {"lk": {"file": "k_lk.cu", "sha": "ff90049d60006f6b", "bytes_per_launch": 190591744 + 3222784}}
 
 

@@ -299,6 +299,17 @@ stab_status stab_batch_step_host(stab_batch *b, const uint8_t *const *frames_hos
  * *variant (may be NULL) receives the choice; ms_out (may be NULL, one float
  * per variant) the measured mean ms per launch (-1 when taken from the cache). */
 stab_status stab_batch_autotune(stab_batch *b, const char *cache_path, int *variant, float *ms_out, void *stream);
+/* Bound the candidate list of corner detection (the NMS survivors kept
+ * before the top-K selection, Sec. 3.1) of every stream of a context or batch
+ * to `cap` keys; cap = 0 restores the capacity sized at creation (every
+ * possible survivor of the ROI), larger values are clipped to it.  A
+ * detection with more survivors keeps `cap` of them (its corner list is then
+ * not the exact top K) and latches STAB_ERR_CAPACITY in the device error word,
+ * which the next stab_sync / stab_batch_sync returns and clears.  For callers
+ * that bound the scratch a detection may fill, and the test hook of the
+ * latched-error path.  Synchronous: waits for the context's last stream. */
+stab_status stab_set_candidate_capacity(stab_ctx *ctx, int cap);
+stab_status stab_batch_set_candidate_capacity(stab_batch *b, int cap);
 /* Force a tracker variant (0..3) for a batch or a single-stream context. */
 stab_status stab_batch_set_lk_variant(stab_batch *b, int variant);
 stab_status stab_set_lk_variant(stab_ctx *ctx, int variant);

@@ -79,7 +79,7 @@ def _declare(L):
     L.or_detect.restype = C.c_int
     L.or_track.argtypes = [C.POINTER(_u8p), C.POINTER(_u8p), _i32p, _i32p, _i32p, C.c_int, _f32p, C.c_int,
                            C.c_int, C.c_int, C.c_double, C.c_double, C.c_double, _f64p, _f64p, _f64p, _u8p, _u8p,
-                           _i32p]
+                           _i32p, _f64p]
     L.or_track.restype = C.c_int
     L.or_grad_planes.argtypes = [_u8p, C.c_int, C.c_int, C.c_int, _f64p, _f64p, _f64p]
     L.or_splitmix64.argtypes = [C.c_uint64]
@@ -199,11 +199,12 @@ def track(pyrI: list, pyrJ: list, pts: np.ndarray, win_r=10, max_iters=30, eps=0
     pts = _c(pts, np.float32).reshape(-1, 2)
     n = pts.shape[0]
     fwd = np.zeros((n, 2)); back = np.zeros((n, 2)); fb = np.zeros(n)
-    st = np.zeros(n, np.uint8); stf = np.zeros(n, np.uint8); it = np.zeros(1, np.int32)
+    st = np.zeros(n, np.uint8); stf = np.zeros(n, np.uint8); it = np.zeros(1, np.int32); lm = np.zeros((n, 2))
     lib().or_track(PI, PJ, _p(lw, _i32p), _p(lh, _i32p), _p(lw, _i32p), L, _p(pts, _f32p), n, win_r, max_iters,
                    eps, min_eig, fb_thresh, _p(fwd, _f64p), _p(back, _f64p), _p(fb, _f64p), _p(st, _u8p),
-                   _p(stf, _u8p), _p(it, _i32p))
-    return dict(fwd=fwd, back=back, fb_err=fb, status=st, status_fwd=stf, iters=int(it[0]))
+                   _p(stf, _u8p), _p(it, _i32p), _p(lm, _f64p))
+    return dict(fwd=fwd, back=back, fb_err=fb, status=st, status_fwd=stf, iters=int(it[0]), lam_min=lm[:, 0].copy(),
+                lam_trace=lm[:, 1].copy())
 
 
 # -------------------------------------------------------------------- fit --

@@ -254,7 +254,7 @@ static double bilin(const plane_t *P, double (*f)(const plane_t *, int, int), do
 
 /* Track u from pyramid I to pyramid J.  Returns 1 if tracked. */
 static int lk_one(const plane_t *I, const plane_t *J, int L, double ux, double uy, int r, int max_iters,
-                  double eps, double min_eig, double *vx, double *vy, int *iters)
+                  double eps, double min_eig, double *vx, double *vy, int *iters, double *lam_min)
 {
     int n = (2 * r + 1) * (2 * r + 1);
     double *T = (double *)malloc(sizeof(double) * 3 * (size_t)n);
@@ -274,6 +274,7 @@ static int lk_one(const plane_t *I, const plane_t *J, int L, double ux, double u
             }
         double lam = 0.5 * ((Gxx + Gyy) - sqrt((Gxx - Gyy) * (Gxx - Gyy) + 4.0 * Gxy * Gxy));
         double D = Gxx * Gyy - Gxy * Gxy;
+        if (lam_min && lam / n < lam_min[0]) { lam_min[0] = lam / n; lam_min[1] = (Gxx + Gyy) / n; }
         if (!(lam / n >= min_eig) || !(D > 0)) { ok = 0; break; }
         double nx = 0.0, ny = 0.0;
         for (int it = 0; it < max_iters; ++it) {
@@ -308,11 +309,16 @@ static int lk_one(const plane_t *I, const plane_t *J, int L, double ux, double u
  * result with a zero guess; a pair is kept when both passes track and the
  * round trip ends within fb_thresh of the start.
  * Outputs (n each): fwd xy (2n), back xy (2n), fb error, status (1 kept),
- * status of the forward pass alone. Returns the number kept. */
+ * status of the forward pass alone, and (when lam_min is not NULL, 2n) the
+ * smallest normalised eigenvalue lambda_min(G) / (2r+1)^2 met at any level of
+ * either pass -- the quantity the loss test compares with min_eig -- with the
+ * normalised trace of that G, reported so that a caller can tell a decision
+ * taken close to that threshold and how finely the eigenvalue is resolved.
+ * Returns the number kept. */
 int or_track(const uint8_t *const *pyrI, const uint8_t *const *pyrJ, const int *lw, const int *lh,
              const int *lp, int L, const float *pts, int n, int r, int max_iters, double eps, double min_eig,
              double fb_thresh, double *fwd, double *back, double *fb_err, uint8_t *status, uint8_t *status_fwd,
-             int *iters)
+             int *iters, double *lam_min)
 {
     plane_t I[16], J[16];
     if (L < 1 || L > 16) return -1;
@@ -324,8 +330,10 @@ int or_track(const uint8_t *const *pyrI, const uint8_t *const *pyrJ, const int *
     if (iters) *iters = 0;
     for (int k = 0; k < n; ++k) {
         double ux = pts[2 * k], uy = pts[2 * k + 1], vx, vy, bx, by;
-        int s1 = lk_one(I, J, L, ux, uy, r, max_iters, eps, min_eig, &vx, &vy, iters);
-        int s2 = s1 ? lk_one(J, I, L, vx, vy, r, max_iters, eps, min_eig, &bx, &by, iters) : 0;
+        double *lm = lam_min ? &lam_min[2 * k] : NULL;
+        if (lm) { lm[0] = HUGE_VAL; lm[1] = 0.0; }
+        int s1 = lk_one(I, J, L, ux, uy, r, max_iters, eps, min_eig, &vx, &vy, iters, lm);
+        int s2 = s1 ? lk_one(J, I, L, vx, vy, r, max_iters, eps, min_eig, &bx, &by, iters, lm) : 0;
         if (!s1) { bx = ux; by = uy; }
         double e = sqrt((bx - ux) * (bx - ux) + (by - uy) * (by - uy));
         fwd[2 * k] = vx; fwd[2 * k + 1] = vy;

@@ -447,20 +447,25 @@ void launch_begin(const Launch &L, const StreamDev *S, int n, long long t_ov, in
 
 static int occ_response()
 {
-    static int occ = 0;
-    if (!occ && (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_response, STAB_RS_THREADS, 0) != cudaSuccess ||
-                 occ < 1))
-        occ = 1;
-    return occ;
+    static DevCache c;
+    return c.get([] {
+        int occ = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_response, STAB_RS_THREADS, 0) != cudaSuccess ||
+            occ < 1)
+            occ = 1;
+        return occ;
+    });
 }
 
+// k_select's dynamic shared memory exceeds the default limit: the attribute is
+// set once on every device the selection runs on.
 static void select_attr()
 {
-    static bool attr = false;
-    if (!attr) {
+    static DevCache c;
+    c.get([] {
         cudaFuncSetAttribute(k_select, cudaFuncAttributeMaxDynamicSharedMemorySize, STAB_SEL_SMEM * 8);
-        attr = true;
-    }
+        return 1;
+    });
 }
 
 void warm_detect()

@@ -432,17 +432,20 @@ __global__ void __launch_bounds__(128, MINB) k_lk(const StreamDev *__restrict__ 
 template <typename PT, int NS, int RC, int WPF, int MINB>
 struct LkKernel {
     static int smem(int rmax) { return (128 / (32 * WPF)) * lk_group_bytes(rmax, (int)sizeof(PT)); }
+    // sets the kernel's shared-memory attribute and queries its occupancy, once
+    // per device and radius
     static int occ(int rmax)
     {
-        static int v[STAB_MAXR + 1] = {0};
-        if (!v[rmax]) {
+        static DevCache c[STAB_MAXR + 1];
+        return c[rmax].get([rmax] {
+            int v = 0;
             cudaFuncSetAttribute(k_lk<PT, NS, RC, WPF, MINB>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem(rmax));
-            if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v[rmax], k_lk<PT, NS, RC, WPF, MINB>, 128,
-                                                              smem(rmax)) != cudaSuccess ||
-                v[rmax] < 1)
-                v[rmax] = 1;
-        }
-        return v[rmax];
+            if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, k_lk<PT, NS, RC, WPF, MINB>, 128, smem(rmax)) !=
+                    cudaSuccess ||
+                v < 1)
+                v = 1;
+            return v;
+        });
     }
     static void run(const Launch &L, const StreamDev *S, WorkList wl, LkIO io, int rmax)
     {

@@ -377,12 +377,13 @@ void launch_plane_f32(const Launch &L, int prec, const StreamDev *S, int slot, i
 #define OCC_FN128(name, kern)                                                                  \
     int name()                                                                                 \
     {                                                                                          \
-        static int v = 0;                                                                      \
-        if (!v) {                                                                              \
+        static DevCache c;                                                                     \
+        return c.get([] {                                                                      \
+            int v = 0;                                                                         \
             if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, kern, L0_GROUPS, 0) != cudaSuccess || v < 1) \
                 v = 1;                                                                         \
-        }                                                                                      \
-        return v;                                                                              \
+            return v;                                                                          \
+        });                                                                                    \
     }
 OCC_FN128(occ_level0_f, k_level0<float>)
 OCC_FN128(occ_level0_h, k_level0<__half>)

@@ -406,10 +406,12 @@ __global__ void __launch_bounds__(256, 4) k_warp(const StreamDev *__restrict__ S
 
 static int occ_warp()
 {
-    static int occ = 0;
-    if (!occ && (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_warp, 256, 0) != cudaSuccess || occ < 1))
-        occ = 1;
-    return occ;
+    static DevCache c;
+    return c.get([] {
+        int occ = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_warp, 256, 0) != cudaSuccess || occ < 1) occ = 1;
+        return occ;
+    });
 }
 
 void warm_warp() { occ_warp(); }

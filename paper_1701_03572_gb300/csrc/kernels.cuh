@@ -1,11 +1,38 @@
 // kernels.cuh -- launch interface between the host runtime and the kernels.
 #pragma once
 
+#include <mutex>
+
 #include "common.cuh"
 
 struct Launch {
     cudaStream_t stream;
     int sms;
+};
+
+// Once-per-device values (occupancy, kernel attributes).  A function attribute
+// set with cudaFuncSetAttribute and an occupancy query apply to the device that
+// is current at the time, so each cache keeps one entry per device, filled on
+// the first use on that device under a mutex (host threads may drive different
+// devices at once).  0 means "not yet computed"; compute() returns >= 1.
+constexpr int kMaxDevices = 64;
+static inline int current_device()
+{
+    int d = 0;
+    return cudaGetDevice(&d) == cudaSuccess ? d : -1;
+}
+struct DevCache {
+    std::mutex mu;
+    int v[kMaxDevices] = {};
+    template <class F>
+    int get(F &&compute)
+    {
+        const int d = current_device();
+        if (d < 0 || d >= kMaxDevices) return compute();
+        std::lock_guard<std::mutex> g(mu);
+        if (!v[d]) v[d] = compute();
+        return v[d];
+    }
 };
 
 static inline int grid_for(const Launch &L, int total, int occ)

@@ -43,6 +43,7 @@ struct Pipeline {
     cudaEvent_t ev_fork = nullptr, ev_det = nullptr, ev_warp = nullptr;
     cudaEvent_t ev_in[2] = {}, ev_comp[4] = {}, ev_out[4] = {}, ev_join = nullptr;
     bool host_mode = false;   // the last step was a host-buffer step
+    std::vector<int> cand_cap0;   // candidate capacity of each stream as sized at creation
     int wmax = 1;             // largest smoothing window of the batch
     int hmax = 1;             // most fit hypotheses of a stream
 
@@ -226,6 +227,7 @@ stab_status build(Pipeline &pp, int n, const int *w, const int *h, const int *C,
             if (cudaMemset(pp.arena, 0, off) != cudaSuccess) return cuda_check(pp.err, "cudaMemset");
         }
     }
+    for (int i = 0; i < n; ++i) pp.cand_cap0.push_back(pp.hs[i].cand_cap);
     if (cudaMalloc(&pp.ds, sizeof(StreamDev) * n) != cudaSuccess) return fail(pp.err, STAB_ERR_OOM, "cudaMalloc");
     if (cudaMemcpy(pp.ds, pp.hs.data(), sizeof(StreamDev) * n, cudaMemcpyHostToDevice) != cudaSuccess)
         return cuda_check(pp.err, "cudaMemcpy");
@@ -347,6 +349,23 @@ void enqueue_step(Pipeline &pp, cudaStream_t s, Prof *pf = nullptr)
     }
     launch_advance(L, pp.ds, pp.n);
     mark("advance");
+}
+
+// Bound every stream's candidate list to cap keys (0: the capacity sized at
+// creation).  Waits for the pipeline's last stream, then rewrites the field of
+// each device descriptor; kernels read it at run time, so a captured graph
+// stays valid.
+stab_status set_cand_cap(Pipeline &pp, int cap)
+{
+    if (cap < 0) return fail(pp.err, STAB_ERR_INVALID_ARG, "negative candidate capacity");
+    if (cudaStreamSynchronize(pp.last) != cudaSuccess) return cuda_check(pp.err, "stream synchronize");
+    for (int i = 0; i < pp.n; ++i) {
+        const int c = cap == 0 ? pp.cand_cap0[i] : std::min(cap, pp.cand_cap0[i]);
+        pp.hs[i].cand_cap = c;
+        if (cudaMemcpy(&pp.ds[i].cand_cap, &c, sizeof(int), cudaMemcpyHostToDevice) != cudaSuccess)
+            return cuda_check(pp.err, "candidate capacity");
+    }
+    return STAB_OK;
 }
 
 stab_status read_err(Pipeline &pp)
@@ -699,6 +718,18 @@ stab_status stab_batch_lk_work(stab_batch *b, int64_t *iterations, int64_t *temp
     return cuda_check(pp.err, "stab_batch_lk_work");
 }
 
+stab_status stab_set_candidate_capacity(stab_ctx *c, int cap)
+{
+    if (!c) return STAB_ERR_INVALID_ARG;
+    return set_cand_cap(c->pp, cap);
+}
+
+stab_status stab_batch_set_candidate_capacity(stab_batch *b, int cap)
+{
+    if (!b) return STAB_ERR_INVALID_ARG;
+    return set_cand_cap(b->pp, cap);
+}
+
 stab_status stab_set_lk_variant(stab_ctx *c, int v)
 {
     if (!c || v < 0 || v >= lk_variants()) return STAB_ERR_INVALID_ARG;
@@ -932,12 +963,12 @@ static stab_status charb_args(const float *It, const float *Ip, int w, int h, in
 
 static Launch plain_launch(void *stream)
 {
-    static int sms = 0;
-    if (!sms) {
-        int dev = 0;
-        cudaGetDevice(&dev);
-        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    }
+    static DevCache c;
+    const int sms = c.get([] {
+        int n = 0;
+        cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, current_device());
+        return n > 0 ? n : 1;
+    });
     return Launch{(cudaStream_t)stream, sms};
 }
 

@@ -103,6 +103,8 @@ def lib():
             "stab_batch_autotune": ([_vp, C.c_char_p, C.POINTER(_i), _vp, _vp], _i),
             "stab_batch_set_lk_variant": ([_vp, _i], _i),
             "stab_set_lk_variant": ([_vp, _i], _i),
+            "stab_set_candidate_capacity": ([_vp, _i], _i),
+            "stab_batch_set_candidate_capacity": ([_vp, _i], _i),
             "stab_batch_step_profiled": ([_vp, _vp, _vp, _i, C.POINTER(_i)], _i),
             "stab_batch_kernel_name": ([_vp, _i], C.c_char_p),
             "stab_batch_lk_work": ([_vp, C.POINTER(_i64), C.POINTER(_i64)], _i),
@@ -125,6 +127,15 @@ def _p(t):
     if not t.is_cuda:
         raise ValueError("expected a CUDA tensor")
     return _vp(t.data_ptr())
+
+
+def _rows(img: torch.Tensor):
+    """A 2-D uint8 image with unit column stride as (tensor, pitch in bytes);
+    other layouts are made contiguous."""
+    if img.dim() == 2 and img.stride(1) == 1 and img.stride(0) >= img.shape[1]:
+        return img, img.stride(0)
+    img = img.contiguous()
+    return img, img.shape[1]
 
 
 def _s(stream=None):
@@ -190,8 +201,15 @@ class Context:
     def sync(self):
         return self._chk(lib().stab_sync(self._h), "stab_sync")
 
+    def sync_status(self) -> int:
+        """stab_sync's status as an int (device errors are returned, not raised)."""
+        return int(lib().stab_sync(self._h))
+
     def set_lk_variant(self, v: int):
         self._chk(lib().stab_set_lk_variant(self._h, v), "stab_set_lk_variant")
+
+    def set_candidate_capacity(self, cap: int):
+        self._chk(lib().stab_set_candidate_capacity(self._h, cap), "stab_set_candidate_capacity")
 
     def pyramid(self, frame: torch.Tensor):
         ch = 1 if frame.dim() == 2 else frame.shape[2]
@@ -212,12 +230,14 @@ class Context:
         return I, Ix, Iy
 
     def detect(self, gray: torch.Tensor):
-        gray = gray.contiguous()
+        """Corners of a gray frame: a (h, w) uint8 tensor whose rows may be
+        strided (row stride = pitch, any base address)."""
+        gray, pitch = _rows(gray)
         dev = gray.device
         pts = torch.zeros((self.K, 2), dtype=torch.float32, device=dev)
         lam = torch.zeros(self.K, dtype=torch.float32, device=dev)
         n = torch.zeros(2, dtype=torch.int32, device=dev)
-        self._chk(lib().stab_detect(self._h, _p(gray), self.w, _p(pts), _p(lam), _p(n[0:1]), _p(n[1:2]), _s()),
+        self._chk(lib().stab_detect(self._h, _p(gray), pitch, _p(pts), _p(lam), _p(n[0:1]), _p(n[1:2]), _s()),
                   "stab_detect")
         return pts, lam, n
 
@@ -380,6 +400,13 @@ class Batch:
     def set_lk_variant(self, v: int):
         self._chk(lib().stab_batch_set_lk_variant(self._h, v), "stab_batch_set_lk_variant")
 
+    def set_candidate_capacity(self, cap: int):
+        self._chk(lib().stab_batch_set_candidate_capacity(self._h, cap), "stab_batch_set_candidate_capacity")
+
+    def sync_status(self) -> int:
+        """stab_batch_sync's status as an int (device errors are returned, not raised)."""
+        return int(lib().stab_batch_sync(self._h))
+
     def features(self, i: int):
         K = self.descs[i][3].max_corners
         pts = torch.zeros((K, 2), dtype=torch.float32)
@@ -390,15 +417,16 @@ class Batch:
 
 def detect_noalloc(gray: torch.Tensor, roi, quality: float, max_corners: int, pts=None, lam=None, n=None):
     """stab_detect_noalloc: corners without a context or any allocation inside
-    the library (outputs are allocated here unless given).  Returns
+    the library (outputs are allocated here unless given).  gray: (h, w) uint8
+    whose rows may be strided (row stride = pitch, any base address).  Returns
     (status, pts (K, 2), lam (K,), counts [n, n_above_threshold])."""
-    gray = gray.contiguous()
+    gray, pitch = _rows(gray)
     h, w = gray.shape
     dev = gray.device
     pts = pts if pts is not None else torch.zeros((max_corners, 2), dtype=torch.float32, device=dev)
     lam = lam if lam is not None else torch.zeros(max_corners, dtype=torch.float32, device=dev)
     n = n if n is not None else torch.zeros(2, dtype=torch.int32, device=dev)
-    st = lib().stab_detect_noalloc(_p(gray), w, h, w, roi[0], roi[1], roi[2], roi[3], quality, max_corners,
+    st = lib().stab_detect_noalloc(_p(gray), w, h, pitch, roi[0], roi[1], roi[2], roi[3], quality, max_corners,
                                    _p(pts), _p(lam), _p(n[0:1]), _p(n[1:2]), _s())
     return st, pts, lam, n
 

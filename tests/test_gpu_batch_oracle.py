@@ -1,0 +1,115 @@
+"""The batched CUDA-graph step against the oracle's whole-clip run.
+
+The batched step (stab_batch_step: one graph launch per frame step serving
+every stream of a batch, FP16 plane storage) is the path the throughput
+figures come from.  Here it runs the per-frame method of Sec. 3-5 (detection
+when due, pyramidal LK with the forward-backward check, robust fit, streaming
+trajectory smoothing, compensating warp) on
+
+  * two 1920x1080 RGB streams (1000 corners, 5 levels, 100 hypotheses,
+    similarity), and
+  * one stream of each resolution of the mixed 64-stream workload (320x240,
+    640x480, 1280x720, 1920x1080 gray; 200 / 292 / 538 / 1000 corners in
+    proportion to area; 3 / 4 / 5 / 5 levels),
+
+and every reported motion and every composed frame is compared with
+oracle.run_clip on the same clip.  Step t of a batch ingests frame t, reports
+the transition t-2 -> t-1 (run_clip's increment t - BATCH_LAG) and composes
+frame t - BATCH_OUT_LAG - 1 - W/2.  Bars (the whole-path bars of the
+single-stream test): angle and log-scale within 2e-4, translation within
+0.05 px; the detection schedule identical; tracked-pair and inlier counts
+within 1 % (a pair whose status sits near a threshold may fall either way);
+composed frames differ by more than 1 LSB on < 2 % of pixels, mean |d| < 0.3.
+"""
+import dataclasses
+
+import numpy as np
+import pytest
+import torch
+
+from oracle import oracle as O
+from paper_1701_03572_gb300 import stab as S
+from paper_1701_03572_gb300.synth import CONFIG_SPECS, ClipSpec, make_clip
+
+pytestmark = pytest.mark.gpu
+
+DEV = "cuda"
+W = 15          # smoothing window
+T = 16          # frames per clip: composed frames from step 3 + W/2 = 10 on
+
+
+def _cuda(a):
+    return torch.as_tensor(np.ascontiguousarray(a)).to(DEV)
+
+
+def _run_batch(clips, params):
+    descs = [(f.shape[2], f.shape[1], 1 if f.ndim == 3 else f.shape[3], p) for f, p in zip(clips, params)]
+    b = S.Batch(descs)
+    motions = [[None] * T for _ in clips]
+    outs = [{} for _ in clips]
+    for t in range(T):
+        for i, f in enumerate(clips):
+            b.input_slot(i, t % b.ring).copy_(_cuda(f[t]))
+        b.step(use_graph=True)
+        torch.cuda.synchronize()
+        mot = b.motions()
+        for i in range(len(clips)):
+            motions[i][t] = mot[i]
+            k = t - S.BATCH_OUT_LAG - 1 - W // 2
+            if k >= 0:
+                outs[i][k] = b.output(i).cpu().numpy().copy()
+    assert b.sync() == 0
+    return motions, outs
+
+
+def _check_stream(frames, motions, outs, op, what):
+    ref = O.run_clip(frames, op)
+    checked = 0
+    for t in range(1 + S.BATCH_LAG, T):
+        tt = t - S.BATCH_LAG
+        g = motions[t]
+        m = np.array(g["m"], np.float64)
+        assert not g["flags"] & S.STAB_FLAG_SKIPPED and ref["flags"][tt] == 0, (what, tt)
+        assert bool(g["flags"] & S.STAB_FLAG_DETECTED) == bool(ref["detected"][tt - 1]), (what, tt)
+        assert np.abs(m[2:] - ref["incs"][tt, 2:]).max() < 2e-4, (what, tt, m, ref["incs"][tt])
+        assert np.abs(m[:2] - ref["incs"][tt, :2]).max() < 0.05, (what, tt, m, ref["incs"][tt])
+        nt, ni = ref["n_tracked"][tt], ref["n_inliers"][tt]
+        assert abs(g["n_tracks"] - nt) <= max(2, 0.01 * nt), (what, tt, g["n_tracks"], nt)
+        assert abs(g["inliers"] - ni) <= max(2, 0.01 * ni), (what, tt, g["inliers"], ni)
+        checked += 1
+    assert checked == T - 1 - S.BATCH_LAG
+    assert len(outs) == T - S.BATCH_OUT_LAG - 1 - W // 2
+    for k, frame in outs.items():
+        d = np.abs(frame.astype(int) - ref["out"][k].astype(int))
+        assert (d > 1).mean() < 0.02 and d.mean() < 0.3, (what, k, (d > 1).mean(), d.mean())
+
+
+def test_batch_1080p_rgb_vs_oracle():
+    """Two 1920x1080 RGB streams, the benchmark's per-stream settings (window
+    15 here, so that composed frames come out within the clip)."""
+    spec = dataclasses.replace(CONFIG_SPECS[2], frames=T)
+    clips = [make_clip(spec, 4100 + s, device=DEV)["frames"].cpu().numpy() for s in range(2)]
+    p = S.default_params(max_corners=1000, levels=5, hypotheses=100, smooth_window=W, model=S.STAB_SIMILARITY,
+                         precision=S.STAB_FP16_STORAGE)
+    motions, outs = _run_batch(clips, [p, p])
+    op = O.Params(max_corners=1000, levels=5, hypotheses=100, smooth_window=W, rigid=False)
+    for i, f in enumerate(clips):
+        _check_stream(f, motions[i], outs[i], op, f"1080p stream {i}")
+
+
+MIXED = [(320, 240, 200, 3), (640, 480, 292, 4), (1280, 720, 538, 5), (1920, 1080, 1000, 5)]
+
+
+def test_batch_mixed_resolutions_vs_oracle():
+    """One stream of each resolution of the 64-stream mixed workload in one
+    batch: uneven work lists (strips, features, tiles) across streams, five
+    levels next to three, one graph launch per step."""
+    clips, params, ops = [], [], []
+    for k, (w, h, K, L) in enumerate(MIXED):
+        clips.append(make_clip(ClipSpec(w, h, T), 4200 + k, device=DEV)["frames"].cpu().numpy())
+        params.append(S.default_params(max_corners=K, levels=L, hypotheses=100, smooth_window=W,
+                                       precision=S.STAB_FP16_STORAGE))
+        ops.append(O.Params(max_corners=K, levels=L, hypotheses=100, smooth_window=W, rigid=False))
+    motions, outs = _run_batch(clips, params)
+    for i, f in enumerate(clips):
+        _check_stream(f, motions[i], outs[i], ops[i], f"{MIXED[i][0]}x{MIXED[i][1]}")

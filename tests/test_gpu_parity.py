@@ -7,8 +7,9 @@ attributable to that step alone.  Bars:
     decisions taken with one fixed operation order on both sides);
   * robust fit: identical inlier counts and winning sample; parameters within
     1e-4 (angle, log-scale) and 0.02 px (translation);
-  * tracker: positions within 0.01 px where both sides keep the point, status
-    agreement >= 99 %;
+  * tracker: positions within 0.01 px where both sides keep the point; every
+    status disagreement explained by a decision near a threshold (tau_fb,
+    min_eig, the image edge), at most 1 % of features;
   * smoothing: FP32 vs FP64 within the bounds derived in each test.
 """
 import dataclasses
@@ -141,42 +142,98 @@ def _lk_case(cfg, seed, K, L):
     return f0, f1, pts, w, h
 
 
+def _lk_gpu(f0, f1, pts, w, h, K, L, variant=1, prec=0, **kw):
+    ctx = S.Context(w, h, _params(max_corners=K, levels=L, precision=prec, **kw))
+    ctx.set_lk_variant(variant)
+    r = ctx.lk(_cuda(f0), _cuda(f1), _cuda(pts))
+    torch.cuda.synchronize()
+    return {k: v.cpu().numpy() for k, v in r.items()}
+
+
+def _unexplained_status(g, ref, w, h, tau, min_eig, m_fb, m_eig, m_b):
+    """Features whose status differs between the GPU and the oracle for a
+    reason other than a decision taken near one of its thresholds:
+      * the round trip ends within m_fb px of tau_fb on the oracle's side
+        (both sides tracked both passes);
+      * the smallest normalised eigenvalue of G met on the oracle's side lies
+        within m_eig x its normalised trace of min_eig (the FP32 sums resolve
+        the eigenvalue to a few units in the last place of the trace);
+      * a final position (either side, either pass) lies within m_b px of the
+        image's edge, where the level-0 bounds test decides.
+    Returns a list of (index, reason data) of the rest."""
+    bad = []
+    for k in np.flatnonzero(g["status"] != ref["status"]):
+        both_ran = g["status_fwd"][k] == 1 and ref["status_fwd"][k] == 1 and g["fb_err"][k] >= 0 and ref["fb_err"][k] >= 0
+        near_fb = both_ran and abs(ref["fb_err"][k] - tau) <= m_fb
+        near_eig = abs(ref["lam_min"][k] - min_eig) <= m_eig * ref["lam_trace"][k]
+        pos = np.array([g["fwd"][k], g["back"][k], ref["fwd"][k], ref["back"][k]], np.float64)
+        near_b = bool(((pos[:, 0] < m_b) | (pos[:, 0] > w - 1 - m_b) | (pos[:, 1] < m_b) |
+                       (pos[:, 1] > h - 1 - m_b)).any())
+        if not (near_fb or near_eig or near_b):
+            bad.append((int(k), dict(gpu=(int(g["status_fwd"][k]), float(g["fb_err"][k])),
+                                     oracle=(int(ref["status_fwd"][k]), float(ref["fb_err"][k])),
+                                     lam_min=float(ref["lam_min"][k]), trace=float(ref["lam_trace"][k]))))
+    return bad
+
+
+# Parity runs take eps = 0 and a fixed iteration count on both sides (the
+# convergence test would otherwise stop FP32 and FP64 at different iterations
+# near |eta| = eps and move the positions by up to eps); every status
+# disagreement must then sit within 1e-3 px of tau_fb, within the eigenvalue's
+# FP32 resolution of min_eig, or within 1e-3 px of the image edge.
+PARITY_ITERS = 20
+
+
 @pytest.mark.parametrize("cfg,K,L,variant", [(0, 200, 3, 0), (0, 200, 3, 1), (0, 200, 3, 2), (0, 200, 3, 3),
                                               (1, 500, 4, 1), (2, 1000, 5, 1), (2, 1000, 5, 3)])
 def test_lk_parity(cfg, K, L, variant):
     f0, f1, pts, w, h = _lk_case(cfg, 20 + cfg, K, L)
-    ref = O.track(O.pyramid(f0, L), O.pyramid(f1, L), pts)
-    res = {}
-    for prec in (0, 1):
-        ctx = S.Context(w, h, _params(max_corners=K, levels=L, precision=prec))
-        ctx.set_lk_variant(variant)
-        r = ctx.lk(_cuda(f0), _cuda(f1), _cuda(pts))
-        torch.cuda.synchronize()
-        res[prec] = {k: v.cpu().numpy() for k, v in r.items()}
+    ref = O.track(O.pyramid(f0, L), O.pyramid(f1, L), pts, max_iters=PARITY_ITERS, eps=0.0)
+    res = {prec: _lk_gpu(f0, f1, pts, w, h, K, L, variant, prec, eps=0.0, max_iters=PARITY_ITERS)
+           for prec in (0, 1)}
     # FP16 storage holds the same plane values: identical results
     for k in res[0]:
         assert np.array_equal(res[0][k], res[1][k]), k
     g = res[0]
-    agree = (g["status"] == ref["status"]).mean()
-    assert agree >= 0.99
+    bad = _unexplained_status(g, ref, w, h, 1.0, 0.01, 1e-3, 1e-5, 1e-3)
+    assert not bad, bad[:10]
     both = (g["status"] == 1) & (ref["status"] == 1)
     assert both.sum() >= 0.8 * len(pts)
+    assert (g["status"] != ref["status"]).mean() <= 0.01
     d = np.hypot(*(g["fwd"][both] - ref["fwd"][both]).T)
     assert d.max() < 0.01, d.max()
     db = np.hypot(*(g["back"][both] - ref["back"][both]).T)
     assert db.max() < 0.02
 
 
+@pytest.mark.parametrize("cfg,K,L", [(0, 200, 3), (2, 1000, 5)])
+def test_lk_production_settings(cfg, K, L):
+    """With the production stopping rule (eps = 0.01 px, up to 30 iterations)
+    the two sides may stop one iteration apart: positions agree within
+    0.01 px forward and 0.02 px after the backward pass, so the round-trip
+    error of the two sides differs by up to 0.03 px; status disagreements must
+    sit within that of tau_fb, within 2 % of the trace of min_eig (a start
+    point moved by 0.01 px moves G by well under 1 %), or within 0.03 px of
+    the edge."""
+    f0, f1, pts, w, h = _lk_case(cfg, 120 + cfg, K, L)
+    ref = O.track(O.pyramid(f0, L), O.pyramid(f1, L), pts)
+    g = _lk_gpu(f0, f1, pts, w, h, K, L, 1, 1)
+    bad = _unexplained_status(g, ref, w, h, 1.0, 0.01, 0.03, 2e-2, 0.03)
+    assert not bad, bad[:10]
+    assert (g["status"] != ref["status"]).mean() <= 0.01
+    both = (g["status"] == 1) & (ref["status"] == 1)
+    assert np.hypot(*(g["fwd"][both] - ref["fwd"][both]).T).max() < 0.01
+    assert np.hypot(*(g["back"][both] - ref["back"][both]).T).max() < 0.02
+
+
 @pytest.mark.parametrize("r", [4, 12])
 def test_lk_parity_other_window_radii(r):
     f0, f1, pts, w, h = _lk_case(0, 25, 150, 3)
-    ref = O.track(O.pyramid(f0, 3), O.pyramid(f1, 3), pts, win_r=r)
-    ctx = S.Context(w, h, _params(max_corners=150, levels=3, win_radius=r))
-    g = {k: v.cpu().numpy() for k, v in ctx.lk(_cuda(f0), _cuda(f1), _cuda(pts)).items()}
-    # a 9 x 9 window sums 5x fewer samples than 21 x 21: its G and b are noisier
-    # and more decisions land near the thresholds
-    differ = g["status"] != ref["status"]
-    assert differ.mean() <= (0.01 if r >= 10 else 0.03), (ref["fb_err"][differ], g["fb_err"][differ])
+    ref = O.track(O.pyramid(f0, 3), O.pyramid(f1, 3), pts, win_r=r, max_iters=PARITY_ITERS, eps=0.0)
+    g = _lk_gpu(f0, f1, pts, w, h, 150, 3, 0, 0, win_radius=r, eps=0.0, max_iters=PARITY_ITERS)
+    bad = _unexplained_status(g, ref, w, h, 1.0, 0.01, 1e-3, 1e-5, 1e-3)
+    assert not bad, bad[:10]
+    assert (g["status"] != ref["status"]).mean() <= 0.01
     both = (g["status"] == 1) & (ref["status"] == 1)
     assert both.sum() >= 0.7 * len(pts)
     assert np.hypot(*(g["fwd"][both] - ref["fwd"][both]).T).max() < 0.01

@@ -33,6 +33,8 @@ MUTATIONS = [
     ("LK 2x2 solve transposed", "double ex = (Gyy * bx - Gxy * by) / D;", "double ex = (Gxx * bx - Gxy * by) / D;"),
     ("bilinear weight", "(1 - ax) * ay * f(P, x0, y0 + 1)", "ax * ay * f(P, x0, y0 + 1)"),
     ("level scaling", "double px = ldexp(ux, -l), py = ldexp(uy, -l);", "double px = ldexp(ux, -l), py = ldexp(uy, 1 - l);"),
+    ("reported min eigenvalue not normalised", "if (lam_min && lam / n < lam_min[0]) { lam_min[0] = lam / n;",
+     "if (lam_min && lam < lam_min[0]) { lam_min[0] = lam;"),
     ("backward check skipped", "status[k] = (uint8_t)(s1 && s2 && e <= fb_thresh);", "status[k] = (uint8_t)(s1);"),
     ("splitmix constant", "z = (z ^ (z >> 27)) * 0x94D049BB133111EBULL;", "z = (z ^ (z >> 27)) * 0x94D049BB133111EAULL;"),
     ("rotation cross sign", "B += x0 * y1 - x1 * y0;", "B += x1 * y0 - x0 * y1;"),
@@ -80,6 +82,7 @@ PINS = [
     (P.test_lk_zero_motion_is_exact, {}), (P.test_lk_integer_translation, dict(dx=-7, dy=5)),
     (P.test_lk_subpixel_translation_of_smooth_texture, {}), (P.test_lk_first_iteration_is_the_newton_step, {}),
     (P.test_lk_backward_check_rejects_inconsistent_track, {}),
+    (P.test_lk_reported_min_eigenvalue_is_that_of_the_window_tensor, {}),
     (P.test_splitmix64_published_outputs, {}),
     (P.test_ls_closed_form_exact_pairs, dict(rigid=False)), (P.test_ls_matches_svd_procrustes, dict(rigid=False)),
     (P.test_fit_recovers_model_with_outliers, dict(rigid=False)),

@@ -313,6 +313,35 @@ def test_lk_flat_window_is_lost():
     assert r["status"][0] == 0 and r["status_fwd"][0] == 0
 
 
+def test_lk_reported_min_eigenvalue_is_that_of_the_window_tensor():
+    """lam_min = smallest eigenvalue of G = sum over the window of the gradient
+    outer products, divided by the window's sample count, minimised over the
+    levels of both passes.  Zero motion at even integer positions samples
+    every level at integer pixels, so G is a plain sum over numpy's central
+    differences (replicated border) and numpy's eigvalsh gives the truth."""
+    img = np.clip(smooth_texture(96, 128, 31, sigma=2.5), 0, 255).astype(np.uint8)
+    pyr = O.pyramid(img, 2)
+    pts = np.array([[40.0, 36.0], [64.0, 50.0], [90.0, 60.0]], np.float32)
+    r = O.track(pyr, pyr, pts, win_r=7)
+    n = 15 * 15
+    for k, (x, y) in enumerate(pts.astype(int)):
+        lams = []
+        for l in range(2):
+            I, Ix, Iy = O.grad_planes(pyr[l])
+            xs, ys = x >> l, y >> l
+            gx = Ix[ys - 7:ys + 8, xs - 7:xs + 8].ravel()
+            gy = Iy[ys - 7:ys + 8, xs - 7:xs + 8].ravel()
+            G = np.array([[gx @ gx, gx @ gy], [gx @ gy, gy @ gy]])
+            lams.append((np.linalg.eigvalsh(G)[0] / n, np.trace(G) / n))
+        lo = min(lams)
+        assert r["status"][k] == 1
+        assert abs(r["lam_min"][k] - lo[0]) <= 1e-9 * lo[0]
+        assert abs(r["lam_trace"][k] - lo[1]) <= 1e-9 * lo[1]
+    flat = np.full((64, 64), 100, np.uint8)
+    rf = O.track(O.pyramid(flat, 2), O.pyramid(flat, 2), np.array([[32.0, 32.0]], np.float32))
+    assert rf["lam_min"][0] == 0.0
+
+
 def test_lk_backward_check_rejects_inconsistent_track():
     """A point on a patch that vanishes from the next frame cannot round-trip."""
     I = np.clip(smooth_texture(96, 128, 21, sigma=1.5), 0, 255).astype(np.uint8)
