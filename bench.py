@@ -13,8 +13,9 @@ path for one stream through the single-stream calls with FP32 planes;
 stabilised frames out.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-Under torchrun each rank runs its own batch on its own GPU (independent
-videos: no exchange), and rank 0 prints one JSON line.
+Under torchrun the job is N x 16 independent videos dealt round-robin to the
+ranks (16 per GPU; no exchange between them), each rank runs its share as one
+batch on its own GPU, and rank 0 prints one JSON line.
 """
 from __future__ import annotations
 
@@ -44,6 +45,9 @@ FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
 # (3 x 7 flop) + G accumulation (3 FMA = 6 flop) = 27; iteration = bilinear J
 # (7) + residual (1) + b accumulation (2 FMA = 4) = 12.
 LK_FLOP_TEMPLATE, LK_FLOP_ITER = 27, 12
+# The hot-path survey's rough estimate of the same counts (6.6 k and 3.1 k per
+# 441-sample window, i.e. about 15 and 7 per sample), reported beside ours.
+LK_FLOP_SURVEY = (15, 7)
 # DRAM traffic per launch of the dominant kernel from one ncu capture
 # (dram__bytes_read.sum + dram__bytes_write.sum of one launch on this workload,
 # 16 streams); used only while the kernel source is unchanged.
@@ -70,6 +74,14 @@ def dist_env():
 def partition_streams(total: int, world: int, rank: int) -> list:
     """Stream indices of `rank` (round-robin): independent videos, no exchange."""
     return list(range(rank, total, world))
+
+
+def partition_by_area(sizes: list, world: int, rank: int) -> list:
+    """Indices of `rank`'s streams when streams of unequal size are spread over
+    `world` GPUs: streams sorted by pixel area (largest first, ties by index)
+    and dealt round-robin, so every rank gets a like mix of sizes."""
+    order = sorted(range(len(sizes)), key=lambda i: (-sizes[i][0] * sizes[i][1], i))
+    return sorted(order[k] for k in range(rank, len(order), world))
 
 
 def max_over_ranks(x: float, device=None) -> float:
@@ -134,6 +146,99 @@ class ClockSampler:
                 "reasons": reasons, "samples": len(rows)}
 
 
+class NvmlClockSampler:
+    """SM clock and clock-event reasons sampled through NVML every few ms by a
+    separate process (this file run with --clock-sampler), so that even a timed
+    region of a few ms holds several samples; only reads the GPU's state."""
+    REASONS = {0x4: "sw_power_cap", 0x8: "hw_slowdown", 0x20: "sw_thermal_slowdown", 0x40: "hw_thermal_slowdown",
+               0x80: "hw_power_brake_slowdown"}
+
+    def __init__(self, device_index: int, uuid: str | None, period_ms: float = 2.0):
+        self.index, self.uuid, self.period = device_index, uuid, period_ms
+        self.proc, self.path = None, None
+
+    def start(self):
+        try:
+            import tempfile
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            cmd = [sys.executable, os.path.abspath(__file__), "--clock-sampler", self.path, "--clock-index",
+                   str(self.index), "--clock-period-ms", str(self.period)]
+            if self.uuid:
+                cmd += ["--clock-uuid", self.uuid]
+            self.proc = subprocess.Popen(cmd, stdout=subprocess.DEVNULL, stderr=subprocess.DEVNULL)
+            deadline = time.time() + 10
+            while time.time() < deadline and os.path.getsize(self.path) == 0 and self.proc.poll() is None:
+                time.sleep(0.01)
+        except Exception:
+            self.proc = None
+
+    def stop(self, t0: float, t1: float):
+        """Stats of the samples taken in [t0, t1] (time.time() seconds)."""
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        rows = []
+        for line in open(self.path):
+            f = line.strip().split(",")
+            if len(f) == 4:
+                try:
+                    rows.append((float(f[0]), float(f[1]), float(f[2]), int(f[3])))
+                except ValueError:
+                    pass
+        os.unlink(self.path)
+        inside = [r for r in rows if t0 <= r[0] <= t1]
+        if not inside:
+            return None
+        reasons = sorted({name for r in inside for bit, name in self.REASONS.items() if r[3] & bit})
+        return {"sm_mhz": statistics.median(r[1] for r in inside), "sm_max_mhz": max(r[2] for r in inside),
+                "sm_mhz_min": min(r[1] for r in inside), "reasons": reasons, "samples": len(inside),
+                "period_ms": self.period, "source": "NVML, samples inside the timed region"}
+
+
+def clock_sampler_main(path: str, index: int, uuid: str | None, period_ms: float):
+    import signal
+    L = C.CDLL("libnvidia-ml.so.1")
+    if L.nvmlInit_v2() != 0:
+        return
+    h = C.c_void_p()
+    ok = False
+    if uuid:
+        u = uuid if uuid.startswith("GPU-") else "GPU-" + uuid
+        ok = L.nvmlDeviceGetHandleByUUID(u.encode(), C.byref(h)) == 0
+    if not ok and L.nvmlDeviceGetHandleByIndex_v2(index, C.byref(h)) != 0:
+        return
+    try:
+        reasons_fn = L.nvmlDeviceGetCurrentClocksEventReasons
+    except AttributeError:
+        reasons_fn = L.nvmlDeviceGetCurrentClocksThrottleReasons
+    stop = []
+    signal.signal(signal.SIGTERM, lambda *a: stop.append(1))
+    clk, mx, rs = C.c_uint(), C.c_uint(), C.c_ulonglong()
+    L.nvmlDeviceGetMaxClockInfo(h, 1, C.byref(mx))          # 1 = NVML_CLOCK_SM
+    with open(path, "w") as f:
+        while not stop:
+            t = time.time()
+            if L.nvmlDeviceGetClockInfo(h, 1, C.byref(clk)) == 0 and reasons_fn(h, C.byref(rs)) == 0:
+                f.write(f"{t:.6f},{clk.value},{mx.value},{rs.value}\n")
+                f.flush()
+            time.sleep(period_ms / 1e3)
+    L.nvmlShutdown()
+
+
+def device_uuid(dev) -> str | None:
+    try:
+        import torch
+        u = getattr(torch.cuda.get_device_properties(dev), "uuid", None)
+        return str(u) if u is not None else None
+    except Exception:
+        return None
+
+
 # ------------------------------------------------------------------ frames --
 def make_frames(n_clips: int, ring: int, device: str):
     """n_clips seeded 1080p RGB clips of `ring` frames that retrace their path
@@ -163,13 +268,18 @@ def run_ours(args):
     B = args.streams
     A = PARAMS["smooth_window"] // 2
     ring = RING
-    clips = make_frames(min(args.clips, B), ring, dev)
+    # the job: ws x B independent videos dealt round-robin to the ranks; video g
+    # shows seeded clip g % n_clips starting 3 (g // n_clips) frames in
+    mine = partition_streams(ws * B, ws, rank)
+    n_clips = min(args.clips, B)
+    clips = make_frames(n_clips, ring, dev)
     p16 = S.default_params(**PARAMS, precision=S.STAB_FP16_STORAGE)
-    batch = S.Batch([(W, H, CH, p16) for _ in range(B)], ring=ring)
-    offs = [(i // len(clips)) * 3 % ring for i in range(B)]
-    for i in range(B):
+    batch = S.Batch([(W, H, CH, p16) for _ in mine], ring=ring)
+    src_clip = [g % n_clips for g in mine]
+    offs = [(g // n_clips) * 3 % ring for g in mine]
+    for i in range(len(mine)):
         for s in range(ring):
-            batch.input_slot(i, s).copy_(clips[i % len(clips)][(s + offs[i]) % ring])
+            batch.input_slot(i, s).copy_(clips[src_clip[i]][(s + offs[i]) % ring])
     stream = torch.cuda.current_stream()
     # prime the smoother's lookahead (no composed frame before step A + 3: the
     # step tracks one frame behind the frame it ingests and composes one step
@@ -190,26 +300,33 @@ def run_ours(args):
     # ---- timed region: K graph steps
     ev = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps + 1)]
     clocks = ClockSampler(local)
+    nvml = NvmlClockSampler(local, device_uuid(dev))
     clocks.start()
+    nvml.start()
     barrier()
     torch.cuda.synchronize()
     t0 = time.perf_counter()
+    tw0 = time.time()
     ev[0].record(stream)
     for k in range(args.steps):
         batch.step(True)
         ev[k + 1].record(stream)
     torch.cuda.synchronize()
+    tw1 = time.time()
     wall = time.perf_counter() - t0
     barrier()
-    clk = clocks.stop()
+    clk_smi = clocks.stop()
+    clk = nvml.stop(tw0, tw1) or clk_smi
     assert batch.sync() == 0
     step_ms = [ev[k].elapsed_time(ev[k + 1]) for k in range(args.steps)]
     total_ms = ev[0].elapsed_time(ev[-1])
     total_ms = max_over_ranks(total_ms, dev)
     value = ws * B * args.steps / (total_ms / 1e3)
-    lat = sorted(step_ms)
-    p50 = lat[len(lat) // 2]
-    p99 = lat[min(len(lat) - 1, int(math.ceil(0.99 * len(lat))) - 1)]
+
+    # ---- per-step latency: each step launched alone on an idle GPU, events
+    # around it, over a fixed count of steps independent of --steps
+    lat = latency_loop(batch, stream, args.lat_steps, args.lat_warmup) if args.lat_steps > 0 else None
+    gaps = sorted(step_ms)
 
     # ---- per-kernel times (event-bracketed steps without a graph)
     kt, lkw = {}, []
@@ -226,9 +343,9 @@ def run_ours(args):
     plain = run_plain(S, clips[0], ring, args.plain_steps, dev) if args.plain_steps > 0 else None
 
     # ---- end to end through host buffers
-    e2e = run_e2e(S, batch, clips, offs, ring, args.e2e_steps, B) if args.e2e_steps > 0 else None
+    e2e = run_e2e(S, batch, clips, src_clip, offs, ring, args.e2e_steps, ws, dev) if args.e2e_steps > 0 else None
 
-    mixed = run_mixed(S, dev, args.mixed_steps, args.warmup) if args.mixed_steps > 0 else None
+    mixed = run_mixed(S, dev, args.mixed_steps, args.warmup, ws, rank) if args.mixed_steps > 0 else None
     gn = run_gn(S, dev, args.gn_pairs) if args.gn_pairs > 0 else None
     fits = run_fits(S, dev, args.fit_reps) if args.fit_reps > 0 else None
 
@@ -236,13 +353,16 @@ def run_ours(args):
            "warmup": args.warmup, "ms_per_step": round(total_ms / args.steps, 4), "higher_is_better": True,
            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "storage": "u8 frames, f16 I/Ix/Iy planes",
            "data": "synthetic", "config": config_dict(B),
-           "latency_ms": {"p50": round(p50, 4), "p99": round(p99, 4), "per": "batch step (16 frames)",
-                          # not in the step latency: the step that ingests frame t emits frame
-                          # t - (BATCH_OUT_LAG + 1 + W/2), of which W/2 is the smoother's lookahead
-                          "output_delay_frames": S.BATCH_OUT_LAG + 1 + A, "smoothing_lookahead_frames": A},
+           "latency_ms": dict(lat or {}, per="batch step (16 frames)",
+                              # not in the step latency: the step that ingests frame t emits frame
+                              # t - (BATCH_OUT_LAG + 1 + W/2), of which W/2 is the smoother's lookahead
+                              output_delay_frames=S.BATCH_OUT_LAG + 1 + A, smoothing_lookahead_frames=A),
+           "step_interval_ms": {"p50": round(gaps[len(gaps) // 2], 4), "max": round(gaps[-1], 4),
+                                "of": f"event gaps between the {args.steps} back-to-back timed steps"},
            "plain": plain, "e2e": e2e, "roofline": roof,
            "kernels_ms": {k: round(v, 4) for k, v in kavg.items()},
-           "gpu_launches": n_k * args.steps, "clocks": clk, "wall_s": round(wall, 3), "autotune": tuned,
+           "gpu_launches": n_k * args.steps, "clocks": clk, "clocks_nvidia_smi": clk_smi, "wall_s": round(wall, 3),
+           "autotune": tuned, "streams_per_rank": len(mine),
            "mixed_64_streams": mixed, "photometric_gn": gn, "fits": fits}
     if ws == 1 and rank == 0 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(clips[0].cpu().numpy(), args.cpu_frames)
@@ -251,6 +371,28 @@ def run_ours(args):
     if ws > 1:
         import torch.distributed as dist
         dist.destroy_process_group()
+
+
+def latency_loop(batch, stream, steps: int, warm: int) -> dict:
+    """p50 / p99 / max of the device time of one batched step launched with the
+    GPU idle (CUDA events around the graph launch, a synchronisation after
+    each), over `steps` steps after `warm` untimed ones; one step in five
+    detects corners, so the p99 is a detection step."""
+    import torch
+    a = torch.cuda.Event(enable_timing=True)
+    b = torch.cuda.Event(enable_timing=True)
+    ms = []
+    for k in range(warm + steps):
+        a.record(stream)
+        batch.step(True)
+        b.record(stream)
+        b.synchronize()
+        if k >= warm:
+            ms.append(a.elapsed_time(b))
+    ms.sort()
+    q = lambda f: ms[min(len(ms) - 1, int(math.ceil(f * len(ms))) - 1)]
+    return {"p50": round(q(0.5), 4), "p99": round(q(0.99), 4), "max": round(ms[-1], 4), "steps": steps,
+            "warmup": warm, "how": "each step alone on an idle GPU, CUDA events around the graph launch"}
 
 
 def kernel_source_sha(name: str) -> str:
@@ -295,9 +437,13 @@ def roofline(kavg: dict, lkw: list, B: int) -> dict:
     lk_flop = tp * n_win * LK_FLOP_TEMPLATE + it * n_win * LK_FLOP_ITER
     if kavg.get("lk", 0) > 0:
         tf = lk_flop / (kavg["lk"] / 1e3) / 1e12
+        tf_s = (tp * n_win * LK_FLOP_SURVEY[0] + it * n_win * LK_FLOP_SURVEY[1]) / (kavg["lk"] / 1e3) / 1e12
         kernels["lk"] = {"bound": "alu", "achieved": round(tf, 3), "unit": "TFLOP/s",
                          "frac": round(tf / FP32_PEAK_TFLOPS, 4), "ms": round(kavg["lk"], 4),
-                         "iterations": int(it), "template_passes": int(tp)}
+                         "iterations": int(it), "template_passes": int(tp),
+                         "flop_per_sample": {"template": LK_FLOP_TEMPLATE, "iteration": LK_FLOP_ITER},
+                         "frac_at_survey_estimate": {"flop_per_sample": list(LK_FLOP_SURVEY),
+                                                     "frac": round(tf_s / FP32_PEAK_TFLOPS, 4)}}
     if dom in kernels:
         d = kernels[dom]
         traffic = None
@@ -392,15 +538,16 @@ def run_plain(S, clip, ring, steps, dev):
             "lk_variant": best, "lk_variant_frame_ms": {str(k): round(v, 4) for k, v in tune.items()}}
 
 
-def run_e2e(S, batch, clips, offs, ring, steps, B):
+def run_e2e(S, batch, clips, src_clip, offs, ring, steps, ws, dev):
     import torch
+    B = batch.n
     host = [c.cpu().pin_memory() for c in clips]
     outs = [torch.empty((H, W, CH), dtype=torch.uint8).pin_memory() for _ in range(B)]
     stream = torch.cuda.current_stream()
     t0 = batch.frame
 
     def one(t):
-        frames = [host[i % len(host)][(t + offs[i]) % ring] for i in range(B)]
+        frames = [host[src_clip[i]][(t + offs[i]) % ring] for i in range(B)]
         batch.step_host(frames, outs)
 
     for k in range(3):
@@ -408,14 +555,15 @@ def run_e2e(S, batch, clips, offs, ring, steps, B):
     torch.cuda.synchronize()
     t0 = batch.frame
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    barrier()
     e0.record(stream)
     for k in range(steps):
         one(t0 + k)
     e1.record(stream)
     torch.cuda.synchronize()
     assert batch.sync() == 0
-    ms = e0.elapsed_time(e1)
-    return {"value": round(B * steps / (ms / 1e3), 1), "unit": "frames/s",
+    ms = max_over_ranks(e0.elapsed_time(e1), dev)
+    return {"value": round(ws * B * steps / (ms / 1e3), 1), "unit": "frames/s",
             "h2d_bytes_per_step": B * W * H * CH, "d2h_bytes_per_step": B * W * H * CH,
             "api": "stab_batch_step_host (pinned host frames in, stabilised frames out)", "steps": steps}
 
@@ -424,9 +572,11 @@ def run_e2e(S, batch, clips, offs, ring, steps, B):
 MIXED = [(320, 240, 200, 3), (640, 480, 292, 4), (1280, 720, 538, 5), (1920, 1080, 1000, 5)]
 
 
-def run_mixed(S, dev, steps, warmup):
+def run_mixed(S, dev, steps, warmup, ws=1, rank=0):
     """64 gray streams, 16 each of 320x240, 640x480, 1280x720, 1920x1080, with
-    200-1000 corners in proportion to area; one graph launch per frame step."""
+    200-1000 corners in proportion to area; one graph launch per frame step.
+    With several ranks the 64 streams are spread by pixel area (each rank a
+    like mix of sizes) and the value counts every rank's frames."""
     import dataclasses
 
     import torch
@@ -442,6 +592,9 @@ def run_mixed(S, dev, steps, warmup):
         for i in range(16):
             descs.append((w, h, 1, p))
             src.append((k, (3 * i) % ring))
+    mine = partition_by_area([(d[0], d[1]) for d in descs], ws, rank)
+    descs = [descs[i] for i in mine]
+    src = [src[i] for i in mine]
     b = S.Batch(descs, ring=ring)
     for i, (k, off) in enumerate(src):
         for sl in range(ring):
@@ -454,6 +607,7 @@ def run_mixed(S, dev, steps, warmup):
     torch.cuda.synchronize()
     stream = torch.cuda.current_stream()
     ev = [torch.cuda.Event(enable_timing=True) for _ in range(steps + 1)]
+    barrier()
     ev[0].record(stream)
     for k in range(steps):
         b.step(True)
@@ -461,14 +615,15 @@ def run_mixed(S, dev, steps, warmup):
     torch.cuda.synchronize()
     assert b.sync() == 0
     ms = sorted(ev[k].elapsed_time(ev[k + 1]) for k in range(steps))
-    tot = ev[0].elapsed_time(ev[-1])
+    tot = max_over_ranks(ev[0].elapsed_time(ev[-1]), dev)
     area = sum(16 * w * h for w, h, _, _ in MIXED)
     return {"streams": 64, "resolutions": "16 x each of 320x240, 640x480, 1280x720, 1920x1080 (gray)",
             "corners": [k for _, _, k, _ in MIXED], "value": round(64 * steps / (tot / 1e3), 1), "unit": "frames/s",
             "equiv_1080p_frames_per_s": round(steps * area / (W * H) / (tot / 1e3), 1),
             "step_ms_p50": round(ms[len(ms) // 2], 4),
             "step_ms_p99": round(ms[min(len(ms) - 1, int(math.ceil(0.99 * len(ms))) - 1)], 4),
-            "lk_variant": v, "steps": steps}
+            "lk_variant": v, "steps": steps, "streams_per_rank": len(mine),
+            "scaling": "strong (the 64 streams spread over the ranks by area)" if ws > 1 else None}
 
 
 # ----------------------------------------------- photometric Gauss-Newton --
@@ -601,11 +756,73 @@ def oracle_stream(frames, n_frames, warm=0):
     return counted, time.perf_counter() - t_start
 
 
+def cpu_info() -> dict:
+    """Host CPU: model name and the cores this process may run on."""
+    model = None
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.lower().startswith("model name"):
+                model = line.split(":", 1)[1].strip()
+                break
+    except Exception:
+        pass
+    if not model:
+        try:
+            for line in open("/proc/cpuinfo"):
+                if line.lower().startswith(("model name", "cpu part")):
+                    model = line.split(":", 1)[1].strip()
+                    break
+        except OSError:
+            pass
+    try:
+        usable = len(os.sched_getaffinity(0))
+    except AttributeError:
+        usable = os.cpu_count()
+    return {"cpu_model": model, "nproc": usable, "cpu_count": os.cpu_count()}
+
+
+def oracle_all_cores():
+    """Point the oracle at its OpenMP build with one thread per usable core;
+    returns (restore handle, threads) or (None, 1) if that build fails."""
+    from oracle import oracle as O
+    try:
+        path = O.build_omp()
+    except Exception:
+        return None, 1
+    prev = O.use_library(path)
+    n = cpu_info()["nproc"] or 1
+    try:
+        O.lib().omp_set_num_threads(n)
+        threads = int(O.lib().omp_get_max_threads())
+    except AttributeError:
+        threads = n
+    return prev, threads
+
+
 def cpu_baseline(frames, n):
-    cnt, sec = oracle_stream(frames, n)
-    return {"value": round(cnt / sec, 4), "unit": "frames/s", "cores": 1, "kind": "oracle",
+    """The oracle timed on one 1080p RGB stream: single-threaded (the build the
+    tests use) and on all usable host cores (its OpenMP build over rows and
+    features).  `value` / `cores` are the all-core run's."""
+    from oracle import oracle as O
+    info = cpu_info()
+    cnt1, sec1 = oracle_stream(frames, n)
+    single = {"value": round(cnt1 / sec1, 4), "unit": "frames/s", "cores": 1, "frames": cnt1,
+              "seconds": round(sec1, 2)}
+    prev, threads = oracle_all_cores()
+    if prev is None:
+        return dict(single, kind="oracle", single_thread=single, **info,
+                    sample=f"{cnt1} consecutive frames of one 1920x1080 RGB stream, single thread (the OpenMP "
+                           f"build failed)")
+    try:
+        cnt, sec = oracle_stream(frames, n)
+    finally:
+        O.restore_library(prev)
+    return {"value": round(cnt / sec, 4), "unit": "frames/s", "cores": threads, "kind": "oracle",
             "sample": f"{cnt} consecutive frames of one 1920x1080 RGB stream (luma, pyramid, detection when due, "
-                      f"LK fwd+bwd, fit, streaming smoothing, RGB warp); {sec:.1f} s"}
+                      f"LK fwd+bwd, fit, streaming smoothing, RGB warp) on {threads} threads, {sec:.1f} s; "
+                      f"single thread: {cnt1} frames, {sec1:.1f} s",
+            "single_thread": single, **info}
 
 
 def run_reference(args):
@@ -619,15 +836,22 @@ def run_reference(args):
     spec = dataclasses.replace(CONFIG_SPECS[2], frames=ring, pingpong=True)
     frames = make_clip(spec, 2000, device="cpu", dtype=torch.float32,
                        frames=range(min(ring, args.warmup + args.steps + 1)))["frames"].numpy()
-    cnt, sec = oracle_stream(frames, args.steps, warm=args.warmup)
+    from oracle import oracle as O
+    prev, threads = oracle_all_cores()
+    try:
+        cnt, sec = oracle_stream(frames, args.steps, warm=args.warmup)
+    finally:
+        if prev is not None:
+            O.restore_library(prev)
     v = cnt / sec
     print(json.dumps({"impl": "reference", "metric": METRIC, "value": round(v, 4), "unit": "frames/s",
                       "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
                       "ms_per_step": round(1e3 * sec / cnt, 2), "higher_is_better": True, "scaling": "weak",
                       "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": config_dict(STREAMS),
-                      "cpu_baseline": {"value": round(v, 4), "unit": "frames/s", "cores": 1, "kind": "oracle",
+                      "cpu_baseline": {"value": round(v, 4), "unit": "frames/s", "cores": threads, "kind": "oracle",
                                        "sample": f"one step = one 1920x1080 RGB frame of one stream through the "
-                                                 f"FP64 C oracle (single thread); {cnt} steps"},
+                                                 f"FP64 C oracle on {threads} threads; {cnt} steps",
+                                       **cpu_info()},
                       "e2e": {"value": round(v, 4), "unit": "frames/s", "h2d_bytes_per_step": 0,
                               "d2h_bytes_per_step": 0}}))
 
@@ -642,7 +866,13 @@ def main():
     ap.add_argument("--prof-steps", type=int, default=10)
     ap.add_argument("--plain-steps", type=int, default=60)
     ap.add_argument("--e2e-steps", type=int, default=20)
-    ap.add_argument("--cpu-frames", type=int, default=8)
+    ap.add_argument("--cpu-frames", type=int, default=16)
+    ap.add_argument("--lat-steps", type=int, default=300, help="steps of the latency loop (0 = skip)")
+    ap.add_argument("--lat-warmup", type=int, default=20)
+    ap.add_argument("--clock-sampler", default=None, help=argparse.SUPPRESS)
+    ap.add_argument("--clock-index", type=int, default=0, help=argparse.SUPPRESS)
+    ap.add_argument("--clock-uuid", default=None, help=argparse.SUPPRESS)
+    ap.add_argument("--clock-period-ms", type=float, default=2.0, help=argparse.SUPPRESS)
     ap.add_argument("--mixed-steps", type=int, default=30, help="steps of the 64-stream mixed batch (0 = skip)")
     ap.add_argument("--gn-pairs", type=int, default=256, help="frame pairs of the photometric refinement (0 = skip)")
     ap.add_argument("--fit-reps", type=int, default=200, help="timed calls per fit model (0 = skip)")
@@ -650,6 +880,9 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-autotune", action="store_true")
     args = ap.parse_args()
+    if args.clock_sampler:
+        clock_sampler_main(args.clock_sampler, args.clock_index, args.clock_uuid, args.clock_period_ms)
+        return
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
     if args.impl == "reference":

@@ -20,19 +20,31 @@ import numpy as np
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "stab_oracle.c")
 _LIB = os.path.join(_HERE, "_build", "libstab_oracle.so")
+_LIB_OMP = os.path.join(_HERE, "_build", "libstab_oracle_omp.so")
 _lib = None
+
+
+def _compile(out: str, extra: list, force: bool) -> str:
+    if force or not os.path.exists(out) or os.path.getmtime(out) < os.path.getmtime(_SRC):
+        os.makedirs(os.path.dirname(out), exist_ok=True)
+        tmp = out + f".{os.getpid()}.tmp"
+        subprocess.check_call(["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fPIC", "-shared", *extra,
+                               "-o", tmp, _SRC, "-lm"])
+        os.replace(tmp, out)
+    return out
 
 
 def build(force: bool = False) -> str:
     """Compile the oracle with gcc (no contraction of a*b+c: decisions taken in
-    FP32 must reproduce the stated operation order)."""
-    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
-        os.makedirs(os.path.dirname(_LIB), exist_ok=True)
-        tmp = _LIB + f".{os.getpid()}.tmp"
-        subprocess.check_call(["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fPIC", "-shared",
-                               "-o", tmp, _SRC, "-lm"])
-        os.replace(tmp, _LIB)
-    return _LIB
+    FP32 must reproduce the stated operation order).  Single-threaded."""
+    return _compile(_LIB, [], force)
+
+
+def build_omp(force: bool = False) -> str:
+    """The same source built with OpenMP, for timing the oracle on all host
+    cores (loops over rows and features run in parallel; same results).  The
+    tests never load it."""
+    return _compile(_LIB_OMP, ["-fopenmp"], force)
 
 
 def lib():

@@ -17,6 +17,13 @@
  * Every loop follows the definition in the order the paper states it; no
  * blocking, fusion or reordering.  Readings of silent or ambiguous passages are
  * stated where they are used.
+ *
+ * Threads: the library the tests load is built without OpenMP and runs on one
+ * thread.  Loops whose iterations are independent (image rows, features) carry
+ * an OpenMP pragma that takes effect only in the separate timing build
+ * (-fopenmp), which the benchmark uses to time the oracle on all host cores;
+ * each iteration computes exactly what it computes alone, so both builds give
+ * the same bits.
  */
 #include <math.h>
 #include <stdint.h>
@@ -41,6 +48,7 @@ static int clampi(int i, int lo, int hi) { return i < lo ? lo : (i > hi ? hi : i
  * rounded half up. */
 void or_luma(const uint8_t *rgb, int w, int h, int pitch, uint8_t *out, int out_pitch)
 {
+#pragma omp parallel for
     for (int y = 0; y < h; ++y)
         for (int x = 0; x < w; ++x) {
             const uint8_t *p = rgb + (size_t)y * pitch + 3 * x;
@@ -58,6 +66,7 @@ void or_pyr_down(const uint8_t *src, int w, int h, int sp, uint8_t *dst, int dp)
 {
     static const int k5[5] = {1, 4, 6, 4, 1};
     int w2 = (w + 1) / 2, h2 = (h + 1) / 2;
+#pragma omp parallel for
     for (int y = 0; y < h2; ++y)
         for (int x = 0; x < w2; ++x) {
             long s = 0;
@@ -131,6 +140,7 @@ double or_lambda64(int32_t a, int32_t b, int32_t c)
 /* Response map over a rectangle (for tests): lam[(y-y0)*(x1-x0) + (x-x0)]. */
 void or_response(const uint8_t *I, int pitch, int x0, int y0, int x1, int y1, float *lam32, double *lam64)
 {
+#pragma omp parallel for
     for (int y = y0; y < y1; ++y)
         for (int x = x0; x < x1; ++x) {
             int32_t t[3];
@@ -328,12 +338,18 @@ int or_track(const uint8_t *const *pyrI, const uint8_t *const *pyrJ, const int *
     }
     int kept = 0;
     if (iters) *iters = 0;
+#pragma omp parallel for schedule(dynamic, 4) reduction(+ : kept)
     for (int k = 0; k < n; ++k) {
         double ux = pts[2 * k], uy = pts[2 * k + 1], vx, vy, bx, by;
         double *lm = lam_min ? &lam_min[2 * k] : NULL;
+        int itk = 0;
         if (lm) { lm[0] = HUGE_VAL; lm[1] = 0.0; }
-        int s1 = lk_one(I, J, L, ux, uy, r, max_iters, eps, min_eig, &vx, &vy, iters, lm);
-        int s2 = s1 ? lk_one(J, I, L, vx, vy, r, max_iters, eps, min_eig, &bx, &by, iters, lm) : 0;
+        int s1 = lk_one(I, J, L, ux, uy, r, max_iters, eps, min_eig, &vx, &vy, &itk, lm);
+        int s2 = s1 ? lk_one(J, I, L, vx, vy, r, max_iters, eps, min_eig, &bx, &by, &itk, lm) : 0;
+        if (iters) {
+#pragma omp atomic
+            *iters += itk;
+        }
         if (!s1) { bx = ux; by = uy; }
         double e = sqrt((bx - ux) * (bx - ux) + (by - uy) * (by - uy));
         fwd[2 * k] = vx; fwd[2 * k + 1] = vy;
@@ -705,6 +721,7 @@ void or_warp_inverse(const double m[4], int w, int h, double zoom, float Minv[6]
  * then one in y, each fma(f, hi - lo, lo). */
 void or_warp(const uint8_t *src, int w, int h, int C, int sp, const float M[6], uint8_t *dst, int dp)
 {
+#pragma omp parallel for
     for (int y = 0; y < h; ++y)
         for (int x = 0; x < w; ++x) {
             float xf = (float)x, yf = (float)y;

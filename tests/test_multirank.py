@@ -1,6 +1,7 @@
 """Host logic of the multi-GPU benchmark (one process per GPU, independent
-streams per rank, max-over-ranks timing) exercised with world_size-2 gloo
-process groups on the CPU."""
+streams dealt to the ranks, max-over-ranks timing) exercised with
+world_size-2 gloo process groups on the CPU: the functions bench.run_ours and
+bench.run_mixed call to split their streams and time the job."""
 import os
 import socket
 
@@ -9,6 +10,8 @@ import torch.distributed as dist
 import torch.multiprocessing as mp
 
 import bench
+
+MIXED_SIZES = [(w, h) for w, h, _, _ in bench.MIXED for _ in range(16)]
 
 
 def _free_port():
@@ -25,11 +28,12 @@ def _worker(rank, world, port, q):
     dist.init_process_group("gloo", init_method="env://", rank=rank, world_size=world)
     try:
         ws, r, local = bench.dist_env()
-        mine = bench.partition_streams(16, ws, r)
+        mine = bench.partition_streams(ws * bench.STREAMS, ws, r)     # the headline job: 16 videos per rank
+        mixed = bench.partition_by_area(MIXED_SIZES, ws, r)           # the mixed batch spread by area
         t = 10.0 + 5.0 * r                         # per-rank elapsed ms
         bench.barrier()
         worst = bench.max_over_ranks(t)
-        q.put((r, ws, local, mine, worst))
+        q.put((r, ws, local, mine, mixed, worst))
     finally:
         dist.destroy_process_group()
 
@@ -45,13 +49,28 @@ def test_two_rank_partition_and_max_over_ranks():
     for p in procs:
         p.join(timeout=60)
         assert p.exitcode == 0
-    (r0, ws0, l0, m0, w0), (r1, ws1, l1, m1, w1) = res
+    (r0, ws0, l0, m0, x0, w0), (r1, ws1, l1, m1, x1, w1) = res
     assert ws0 == ws1 == 2 and (r0, r1) == (0, 1) and (l0, l1) == (0, 1)
-    # every stream on exactly one rank, no exchange between ranks
-    assert sorted(m0 + m1) == list(range(16)) and not set(m0) & set(m1)
+    # every video on exactly one rank, 16 per rank, no exchange between ranks
+    assert sorted(m0 + m1) == list(range(32)) and not set(m0) & set(m1)
+    assert len(m0) == len(m1) == bench.STREAMS
+    # the mixed streams: each once, and each rank gets 8 of every resolution
+    assert sorted(x0 + x1) == list(range(64)) and not set(x0) & set(x1)
+    for xs in (x0, x1):
+        per_size = {}
+        for i in xs:
+            per_size[MIXED_SIZES[i]] = per_size.get(MIXED_SIZES[i], 0) + 1
+        assert sorted(per_size.values()) == [8, 8, 8, 8]
     assert w0 == w1 == 15.0
 
 
 def test_single_process_helpers():
     assert bench.partition_streams(5, 1, 0) == [0, 1, 2, 3, 4]
+    assert bench.partition_by_area(MIXED_SIZES, 1, 0) == list(range(64))
+    # three ranks: pixel areas within one largest stream of each other
+    areas = []
+    for r in range(3):
+        xs = bench.partition_by_area(MIXED_SIZES, 3, r)
+        areas.append(sum(MIXED_SIZES[i][0] * MIXED_SIZES[i][1] for i in xs))
+    assert max(areas) - min(areas) <= 1920 * 1080
     assert bench.max_over_ranks(3.5) == 3.5

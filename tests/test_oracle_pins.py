@@ -789,3 +789,32 @@ def test_affine_collinear_points_are_skipped():
     src = np.stack([x, 0.5 * x + 10], 1).astype(np.float32)
     f = O.fit_affine(src, src + 1, 320, 240, 100, 0, 1)
     assert f["flags"] == 1 and np.array_equal(f["m"], [1, 0, 0, 1, 0, 0])
+
+
+# ------------------------------------------------------- OpenMP timing build --
+def test_openmp_timing_build_gives_the_same_bits():
+    """The timing build (loops over rows and features in parallel) computes
+    the same values as the single-threaded library the tests use."""
+    import dataclasses
+
+    from paper_1701_03572_gb300.synth import CONFIG_SPECS, make_clip
+    frames = make_clip(dataclasses.replace(CONFIG_SPECS[0], frames=4), 3)["frames"].numpy()
+    rgb = np.random.default_rng(4).integers(0, 256, (37, 53, 3), dtype=np.uint8)
+    p = O.Params(max_corners=200, levels=3, smooth_window=3)
+
+    def run():
+        out = [O.luma(rgb), O.pyramid(frames[0], 3)[2]]
+        pts, lam, _ = O.detect(frames[0], O.roi_of(320, 240), 200)
+        tr = O.track(O.pyramid(frames[0], 3), O.pyramid(frames[1], 3), pts)
+        rc = O.run_clip(frames, p)
+        return out + [pts, lam, tr["fwd"], tr["back"], tr["status"], tr["iters"], tr["lam_min"], rc["incs"],
+                      rc["out"]]
+
+    ref = run()
+    prev = O.use_library(O.build_omp())
+    try:
+        got = run()
+    finally:
+        O.restore_library(prev)
+    for a, b in zip(ref, got):
+        assert np.array_equal(np.asarray(a), np.asarray(b))

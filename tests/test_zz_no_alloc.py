@@ -61,16 +61,16 @@ def test_noalloc_detect_matches_oracle_and_context_detect_on_consecutive_calls(c
 
 
 def test_noalloc_detect_on_a_strided_view_at_an_odd_address():
-    """Rows 3 bytes into a wider buffer (pitch = w + 37, base address odd): the
+    """Rows 2 bytes into a wider buffer (pitch = w + 37, base address odd): the
     byte-wise path of the response kernel, bit-equal to stab_detect on the
     same view and to the oracle."""
     clip = make_clip(dataclasses.replace(CONFIG_SPECS[0], frames=1), 77)
     img = clip["frames"][0].numpy()
     h, w = img.shape
     big = np.zeros((h + 2, w + 37), np.uint8)
-    big[1:h + 1, 3:w + 3] = img
+    big[1:h + 1, 2:w + 2] = img
     gbig = torch.as_tensor(big).cuda()
-    view = gbig[1:h + 1, 3:w + 3]
+    view = gbig[1:h + 1, 2:w + 2]
     assert view.stride(0) == w + 37 and view.data_ptr() % 2 == 1
     rp, rl, nc = O.detect(img, _roi(w, h), 200)
     for _ in range(2):
