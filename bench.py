@@ -508,7 +508,7 @@ def run_plain(S, clip, ring, steps, dev):
     # warps per feature), timing a few frames of each
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     tune = {}
-    for v in range(4):
+    for v in range(S.LK_VARIANTS):
         ctx.set_lk_variant(v)
         frame_step(t)
         t += 1

@@ -310,7 +310,12 @@ stab_status stab_batch_autotune(stab_batch *b, const char *cache_path, int *vari
  * latched-error path.  Synchronous: waits for the context's last stream. */
 stab_status stab_set_candidate_capacity(stab_ctx *ctx, int cap);
 stab_status stab_batch_set_candidate_capacity(stab_batch *b, int cap);
-/* Force a tracker variant (0..3) for a batch or a single-stream context. */
+/* Force a tracker variant (0..4) for a batch or a single-stream context:
+ * 0 / 1: one warp per feature, template in registers, register budgets of
+ * 128 / 168; 2 / 3: two warps per feature, budgets of 80 / 128; 4: one warp
+ * per feature, template in shared memory, budget of 96 (more resident warps).
+ * The one-warp variants (0, 1, 4) give identical results; the two-warp ones
+ * sum the window in another order (FP32 rounding differences only). */
 stab_status stab_batch_set_lk_variant(stab_batch *b, int variant);
 stab_status stab_set_lk_variant(stab_ctx *ctx, int variant);
 /* Copy the motions of the last step (n entries) to host memory (synchronous). */

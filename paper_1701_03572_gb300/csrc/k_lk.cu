@@ -127,11 +127,15 @@ __device__ __forceinline__ float lerpf(float a, float b, float f) { return fmaf(
 // Track one feature from pyramid slot sa to slot sb.  RC = compile-time
 // radius (0: runtime D.r).  sI: pw rows of I, sG: pw rows of (Ix, Iy), sJ:
 // pw + 2 LK_MARGIN rows of the next frame's I (plane precision), red: 3 * WPF.
+// TS: the template (T, Tx, Ty per sample pair) lives in shared memory at sT
+// (3 NS / 2 packed pairs per thread, thread-interleaved so a warp's accesses
+// are conflict-free) instead of 3 NS registers, for a register budget that
+// lets more warps reside; otherwise sT is unused.
 // Not inlined: the kernel calls it for the forward and the backward track, and
 // one copy of its unrolled body keeps the instruction working set small.
-template <typename PT, int NS, int RC, int WPF>
+template <typename PT, int NS, int RC, int WPF, bool TS>
 __device__ __noinline__ bool lk_track(const StreamDev &D, int sa, int sb, float ux, float uy, float &vx, float &vy, int &iters,
-                         int &tpl, PT *sI, typename Plane2<PT>::type *sG, PT *sJ, float *red, int tig, int grp)
+                         int &tpl, PT *sI, typename Plane2<PT>::type *sG, PT *sJ, float *red, fx2 *sT, int tig, int grp)
 {
     typedef typename Plane2<PT>::type PT2;
     constexpr int NT = 32 * WPF;
@@ -162,8 +166,24 @@ __device__ __noinline__ bool lk_track(const StreamDev &D, int sa, int sb, float 
     // in the two lanes of packed f32x2 arithmetic); T, Tx, Ty are kept as pairs.
     constexpr bool PAIR = Q % 2 == 0;
     constexpr int NP = PAIR ? NS / 2 : 1;
+    static_assert(!TS || (PAIR && WPF == 1), "the shared template is laid out for pairs and one warp");
     float T[PAIR ? 1 : NS], TX[PAIR ? 1 : NS], TY[PAIR ? 1 : NS];
-    fx2 TT[NP], TTX[NP], TTY[NP];
+    fx2 TT[(PAIR && !TS) ? NP : 1], TTX[(PAIR && !TS) ? NP : 1], TTY[(PAIR && !TS) ? NP : 1];
+    // template pair m, component k (0: T, 1: Tx, 2: Ty) of this thread
+    auto tref = [&](int m, int k) -> fx2 & {
+        if constexpr (TS) return sT[(3 * m + k) * 32 + tig];
+        else return k == 0 ? TT[m] : (k == 1 ? TTX[m] : TTY[m]);
+    };
+    // EXACT windows: a segment without samples (past the window) still reads
+    // staged, finite values, so its samples are not masked one by one; its
+    // lane's share of every sum (G and b) is dropped once, after accumulating.
+    constexpr bool MASK_END = EXACT && Q == 2;
+    auto psum = [&](fx2 v, int pp) {
+        float u0, u1;
+        upk(v, u0, u1);
+        if constexpr (MASK_END) return (sv[2 * pp] ? u0 : 0.f) + (sv[2 * pp + 1] ? u1 : 0.f);
+        else return u0 + u1;
+    };
     for (int l = D.L - 1; l >= 0; --l) {
         const PT *Ia = reinterpret_cast<const PT *>(D.pI[sa][l]);
         const PT2 *Ga = reinterpret_cast<const PT2 *>(D.pG[sa][l]);
@@ -214,20 +234,22 @@ __device__ __noinline__ bool lk_track(const StreamDev &D, int sa, int sb, float 
                     const fx2 hX1 = fma2(AX, sub2(a1, a0), a0);
                     a0 = pk(ga0.y, gb0.y); a1 = pk(ga1.y, gb1.y);
                     const fx2 hY1 = fma2(AX, sub2(a1, a0), a0);
-                    // samples past the window's last row weigh 0
-                    const fx2 ok = pk(sok(qa, e) ? 1.f : 0.f, sok(qb, e) ? 1.f : 0.f), zero = pk(0.f, 0.f);
                     const int m = pp * SEG + e;
-                    TT[m] = fma2(ok, fma2(AY, sub2(hI1, hI), hI), zero);
-                    TTX[m] = fma2(ok, fma2(AY, sub2(hX1, hX), hX), zero);
-                    TTY[m] = fma2(ok, fma2(AY, sub2(hY1, hY), hY), zero);
-                    sxx = fma2(TTX[m], TTX[m], sxx); sxy = fma2(TTX[m], TTY[m], sxy); syy = fma2(TTY[m], TTY[m], syy);
+                    fx2 t = fma2(AY, sub2(hI1, hI), hI), tx = fma2(AY, sub2(hX1, hX), hX);
+                    fx2 ty = fma2(AY, sub2(hY1, hY), hY);
+                    if constexpr (!MASK_END) {
+                        // samples past the window's last row weigh 0
+                        const fx2 ok = pk(sok(qa, e) ? 1.f : 0.f, sok(qb, e) ? 1.f : 0.f), zero = pk(0.f, 0.f);
+                        t = fma2(ok, t, zero); tx = fma2(ok, tx, zero); ty = fma2(ok, ty, zero);
+                    }
+                    tref(m, 0) = t; tref(m, 1) = tx; tref(m, 2) = ty;
+                    sxx = fma2(tx, tx, sxx); sxy = fma2(tx, ty, sxy); syy = fma2(ty, ty, syy);
                     hI = hI1; hX = hX1; hY = hY1;
                 }
             }
-            float u0, u1;
-            upk(sxx, u0, u1); gxx = u0 + u1;
-            upk(sxy, u0, u1); gxy = u0 + u1;
-            upk(syy, u0, u1); gyy = u0 + u1;
+            gxx = psum(sxx, 0);
+            gxy = psum(sxy, 0);
+            gyy = psum(syy, 0);
         } else {
     #pragma unroll
             for (int q = 0; q < Q; ++q) {
@@ -298,15 +320,14 @@ __device__ __noinline__ bool lk_track(const StreamDev &D, int sa, int sb, float 
                         a0 = pk(f1(pJa[oa]), f1(pJb[ob])); a1 = pk(f1(pJa[oa + 1]), f1(pJb[ob + 1]));
                         const fx2 h1 = fma2(CX, sub2(a1, a0), a0);
                         const int m = pp * SEG + e;
-                        const fx2 err = sub2(TT[m], fma2(CY, sub2(h1, h), h));   // outside the window Tx = Ty = 0
-                        ax2 = fma2(err, TTX[m], ax2);
-                        ay2 = fma2(err, TTY[m], ay2);
+                        const fx2 err = sub2(tref(m, 0), fma2(CY, sub2(h1, h), h));   // outside the window Tx = Ty = 0
+                        ax2 = fma2(err, tref(m, 1), ax2);
+                        ay2 = fma2(err, tref(m, 2), ay2);
                         h = h1;
                     }
                 }
-                float u0, u1;
-                upk(ax2, u0, u1); bxs = u0 + u1;
-                upk(ay2, u0, u1); bys = u0 + u1;
+                bxs = psum(ax2, 0);
+                bys = psum(ay2, 0);
             } else {
     #pragma unroll
                 for (int q = 0; q < Q; ++q) {
@@ -350,22 +371,28 @@ __host__ __device__ constexpr int lk_bytes_J(int r, int es)
 {
     return lk_al16((2 * r + 2 + 2 * LK_MARGIN) * lk_sw(2 * r + 2 + 2 * LK_MARGIN) * es);
 }
-__host__ __device__ constexpr int lk_group_bytes(int r, int es) { return 3 * lk_bytes_I(r, es) + lk_bytes_J(r, es) + 32; }
+// The shared template of a TS group: 3 NS / 2 packed pairs per thread, 32 threads.
+__host__ __device__ constexpr int lk_bytes_T(int ns) { return 3 * (ns / 2) * 32 * 8; }
+__host__ __device__ constexpr int lk_group_bytes(int r, int es, int tbytes = 0)
+{
+    return 3 * lk_bytes_I(r, es) + lk_bytes_J(r, es) + 32 + tbytes;
+}
 
-template <typename PT, int NS, int RC, int WPF, int MINB>
+template <typename PT, int NS, int RC, int WPF, int MINB, bool TS>
 __global__ void __launch_bounds__(128, MINB) k_lk(const StreamDev *__restrict__ S, WorkList wl, LkIO io, int rmax)
 {
     typedef typename Plane2<PT>::type PT2;
     extern __shared__ __align__(16) unsigned char lk_smem[];
-    constexpr int NT = 32 * WPF, ES = (int)sizeof(PT);
+    constexpr int NT = 32 * WPF, ES = (int)sizeof(PT), TB = TS ? lk_bytes_T(NS) : 0;
     const int grp = threadIdx.x / NT, tig = threadIdx.x - grp * NT;
-    unsigned char *base = lk_smem + grp * lk_group_bytes(rmax, ES);
+    unsigned char *base = lk_smem + grp * lk_group_bytes(rmax, ES, TB);
     // regions sized for rmax; a stream with a smaller radius uses a prefix
     const int bI = lk_bytes_I(rmax, ES);
     PT *sI = reinterpret_cast<PT *>(base);
     PT2 *sG = reinterpret_cast<PT2 *>(base + bI);
     PT *sJ = reinterpret_cast<PT *>(base + 3 * bI);
     float *red = reinterpret_cast<float *>(base + 3 * bI + lk_bytes_J(rmax, ES));
+    fx2 *sT = reinterpret_cast<fx2 *>(base + 3 * bI + lk_bytes_J(rmax, ES) + 32);
     const int ngroups = (gridDim.x * blockDim.x) / NT;
     // The group's next item: a fixed stride, or with a ticket list the ticket
     // thread 0 of the group drew (tk), broadcast to the group.
@@ -399,11 +426,11 @@ __global__ void __launch_bounds__(128, MINB) k_lk(const StreamDev *__restrict__ 
         const float2 u = pts[f];
         int iters = 0, tpl = 0;
         float vx, vy, bx = u.x, by = u.y;
-        const bool ok1 = lk_track<PT, NS, RC, WPF>(D, sp, sn, u.x, u.y, vx, vy, iters, tpl, sI, sG, sJ, red, tig,
-                                                   grp);
+        const bool ok1 = lk_track<PT, NS, RC, WPF, TS>(D, sp, sn, u.x, u.y, vx, vy, iters, tpl, sI, sG, sJ, red,
+                                                       sT, tig, grp);
         bool ok2 = false;
-        if (ok1) ok2 = lk_track<PT, NS, RC, WPF>(D, sn, sp, vx, vy, bx, by, iters, tpl, sI, sG, sJ, red, tig,
-                                                    grp);
+        if (ok1) ok2 = lk_track<PT, NS, RC, WPF, TS>(D, sn, sp, vx, vy, bx, by, iters, tpl, sI, sG, sJ, red, sT,
+                                                     tig, grp);
         if (!ok1) { bx = u.x; by = u.y; }
         const float ex = bx - u.x, ey = by - u.y;
         const float e2 = ex * ex + ey * ey;
@@ -429,9 +456,12 @@ __global__ void __launch_bounds__(128, MINB) k_lk(const StreamDev *__restrict__ 
     }
 }
 
-template <typename PT, int NS, int RC, int WPF, int MINB>
+template <typename PT, int NS, int RC, int WPF, int MINB, bool TS = false>
 struct LkKernel {
-    static int smem(int rmax) { return (128 / (32 * WPF)) * lk_group_bytes(rmax, (int)sizeof(PT)); }
+    static int smem(int rmax)
+    {
+        return (128 / (32 * WPF)) * lk_group_bytes(rmax, (int)sizeof(PT), TS ? lk_bytes_T(NS) : 0);
+    }
     // sets the kernel's shared-memory attribute and queries its occupancy, once
     // per device and radius
     static int occ(int rmax)
@@ -439,8 +469,8 @@ struct LkKernel {
         static DevCache c[STAB_MAXR + 1];
         return c[rmax].get([rmax] {
             int v = 0;
-            cudaFuncSetAttribute(k_lk<PT, NS, RC, WPF, MINB>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem(rmax));
-            if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, k_lk<PT, NS, RC, WPF, MINB>, 128, smem(rmax)) !=
+            cudaFuncSetAttribute(k_lk<PT, NS, RC, WPF, MINB, TS>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem(rmax));
+            if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, k_lk<PT, NS, RC, WPF, MINB, TS>, 128, smem(rmax)) !=
                     cudaSuccess ||
                 v < 1)
                 v = 1;
@@ -451,7 +481,7 @@ struct LkKernel {
     {
         const int groups_per_block = 128 / (32 * WPF);
         const int blocks = (wl.total + groups_per_block - 1) / groups_per_block;
-        k_lk<PT, NS, RC, WPF, MINB><<<grid_for(L, blocks, occ(rmax)), 128, smem(rmax), L.stream>>>(S, wl, io, rmax);
+        k_lk<PT, NS, RC, WPF, MINB, TS><<<grid_for(L, blocks, occ(rmax)), 128, smem(rmax), L.stream>>>(S, wl, io, rmax);
     }
 };
 
@@ -460,6 +490,8 @@ struct LkKernel {
 //   1: one warp per feature, <= 168 registers (3 blocks / SM)
 //   2: two warps per feature, <= 80 registers (6 blocks / SM)
 //   3: two warps per feature, <= 128 registers (4 blocks / SM)
+//   4: one warp per feature, template in shared memory, <= 96 registers
+//      (5 blocks / SM with FP16 planes: 10.5 KB of shared memory per warp)
 // Other radii use the runtime-radius build of variant 0.
 // rcode: the window radius shared by every stream, or minus the largest
 // radius when streams differ (then the runtime-radius build, sized for it).
@@ -471,6 +503,7 @@ void run_variant(int v, const Launch &L, const StreamDev *S, WorkList wl, LkIO i
         case 1: LkKernel<PT, 14, 10, 1, 3>::run(L, S, wl, io, 10); return;
         case 2: LkKernel<PT, 7, 10, 2, 6>::run(L, S, wl, io, 10); return;
         case 3: LkKernel<PT, 7, 10, 2, 4>::run(L, S, wl, io, 10); return;
+        case 4: LkKernel<PT, 14, 10, 1, 5, true>::run(L, S, wl, io, 10); return;
         default: LkKernel<PT, 14, 10, 1, 4>::run(L, S, wl, io, 10); return;
         }
     }
@@ -486,6 +519,7 @@ void warm_all()
         if (r == 10) {
             LkKernel<PT, 14, 10, 1, 4>::occ(r); LkKernel<PT, 14, 10, 1, 3>::occ(r);
             LkKernel<PT, 7, 10, 2, 6>::occ(r); LkKernel<PT, 7, 10, 2, 4>::occ(r);
+            LkKernel<PT, 14, 10, 1, 5, true>::occ(r);
             LkKernel<PT, 14, 0, 1, 4>::occ(r);
         } else if (r < 10) {
             LkKernel<PT, 14, 0, 1, 4>::occ(r);
@@ -497,7 +531,7 @@ void warm_all()
 
 }  // namespace
 
-int lk_variants() { return 4; }
+int lk_variants() { return 5; }
 
 void warm_lk()
 {

@@ -185,7 +185,8 @@ PARITY_ITERS = 20
 
 
 @pytest.mark.parametrize("cfg,K,L,variant", [(0, 200, 3, 0), (0, 200, 3, 1), (0, 200, 3, 2), (0, 200, 3, 3),
-                                              (1, 500, 4, 1), (2, 1000, 5, 1), (2, 1000, 5, 3)])
+                                              (0, 200, 3, 4), (1, 500, 4, 1), (2, 1000, 5, 1), (2, 1000, 5, 3),
+                                              (2, 1000, 5, 4)])
 def test_lk_parity(cfg, K, L, variant):
     f0, f1, pts, w, h = _lk_case(cfg, 20 + cfg, K, L)
     ref = O.track(O.pyramid(f0, L), O.pyramid(f1, L), pts, max_iters=PARITY_ITERS, eps=0.0)
@@ -438,7 +439,7 @@ def test_autotuner_picks_a_variant_and_caches_it(tmp_path):
         b.step()
         if t == 2:
             v, ms = b.autotune(cache)
-            assert 0 <= v < 4 and len(ms) == 4 and all(x > 0 for x in ms.values())
+            assert 0 <= v < S.LK_VARIANTS and len(ms) == S.LK_VARIANTS and all(x > 0 for x in ms.values())
             v2, ms2 = b.autotune(cache)          # second call: from the cache, no timing
             assert v2 == v and ms2 == {}
     assert b.sync() == 0
