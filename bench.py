@@ -294,9 +294,9 @@ def run_ours(args):
     for _ in range(args.warmup):
         batch.step(True)
     torch.cuda.synchronize()
-    # kernels per step: begin, level 0, REDUCE levels 1 .. L-1, response, filter, select,
-    # tracker, compaction, fit (with the smoothing step), warp, advance
-    n_k = 10 + (PARAMS["levels"] - 1)
+    # kernels per step: begin, level 0, REDUCE level 1, the fused launch of levels 2-4,
+    # response, filter, select, tracker, compaction, fit (with the smoothing step), warp, advance
+    n_k = 12
     # ---- timed region: K graph steps
     ev = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps + 1)]
     clocks = ClockSampler(local)
@@ -425,6 +425,10 @@ def roofline(kavg: dict, lkw: list, B: int) -> dict:
         pw, ph = sizes[l - 1]
         w_, h_ = sizes[l]
         alg_bytes[f"pyr_down_{l}"] = B * (pw * ph + w_ * h_ * (1 + 6))
+    # the fused launch of levels l0 .. l0+2: level l0-1 read once, each level written once
+    for l0 in range(2, L, 3):
+        pw, ph = sizes[l0 - 1]
+        alg_bytes[f"pyr_tail_{l0}"] = B * (pw * ph + sum(w_ * h_ * (1 + 6) for w_, h_ in sizes[l0:l0 + 3]))
     kernels = {}
     for k, ms in kavg.items():
         if k in alg_bytes and ms > 0:

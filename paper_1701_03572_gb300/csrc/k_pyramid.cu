@@ -335,6 +335,205 @@ __global__ void __launch_bounds__(128) k_pyr_down(const StreamDev *__restrict__ 
     }
 }
 
+// Levels l0 .. l0 + D - 1 (D <= 3) of a stream in one launch, from level
+// l0 - 1 in global memory.  A block owns a PT_TH x PT_TW tile of the stream's
+// last fused level lt = l0 + D - 1 and the tiles 2^k times larger of level
+// lt - k.  It stages the rows and columns of level l0 - 1 those tiles need
+// (their own pixels, the halos of the later levels and the neighbours of the
+// planes) into shared memory with 16-byte cp.async, then builds each fused
+// level's region in shared memory from the region of the level above it
+// (the same packed 16-bit REDUCE sums as the strip kernel), and emits each
+// level's own tile (u8, I, Ix, Iy).  Out-of-image taps are reflect-101
+// indices into the level above, so every region only ever holds pixels of the
+// image; the regions of the levels are derived from the last one:
+//   B0 (level lt): rows [Y0 - 1, Y1 + 1), columns [X0 - 4, X1 + 1) (quads)
+//   B(k+1): rows [2 ys_k - 2, 2 ye_k + 1), columns [2 xs_k - 4, 2 xe_k + 4)
+// which covers the five-tap inputs of every quad of B(k) and the one-pixel
+// neighbourhood of level k + 1's own tile.
+constexpr int PT_TH = 8, PT_TW = 32, PT_THREADS = 256, PT_MAXD = 3;
+
+struct PtRegion {
+    int ys, ye, xs, xe;   // rows [ys, ye), columns [xs, xe) of the level (unclipped); xs % 4 == 0
+    int stride;           // bytes per buffer row
+    int off;              // byte offset of the buffer in shared memory
+};
+
+// Regions and buffer offsets of a tile whose last level's tile starts at
+// (X0, Y0); k = 0 is the last fused level, k = D the staged input level.
+__host__ __device__ inline int pt_regions(int D, int X0, int Y0, int X1, int Y1, PtRegion *R)
+{
+    R[0].ys = Y0 - 1; R[0].ye = Y1 + 1;
+    R[0].xs = (X0 - 4) & ~3;
+    R[0].xe = (X1 + 1 + 3) & ~3;
+    for (int k = 0; k < D; ++k) {
+        R[k + 1].ys = 2 * R[k].ys - 2;
+        R[k + 1].ye = 2 * R[k].ye + 1;
+        R[k + 1].xs = 2 * R[k].xs - 4;
+        R[k + 1].xe = 2 * R[k].xe + 4;
+    }
+    // the staged level starts on a 16-byte column for the copies
+    R[D].xs = R[D].xs & ~15;
+    int off = 0;
+    for (int k = 0; k <= D; ++k) {
+        R[k].stride = ((R[k].xe - R[k].xs) + 8 + 15) & ~15;   // + the hi byte and a word of slack
+        R[k].off = off;
+        off += R[k].stride * (R[k].ye - R[k].ys);
+    }
+    return off;
+}
+
+// Largest shared-memory footprint of a tile (interior tile, D = PT_MAXD).
+__host__ __device__ inline int pt_smem_bytes()
+{
+    PtRegion R[PT_MAXD + 1];
+    return pt_regions(PT_MAXD, 64, 64, 64 + PT_TW, 64 + PT_TH, R) + 64;
+}
+
+// Walks e = first, first + PT_THREADS, ... over n items of rows of `per`
+// items as (row, column) pairs without a division per step.
+struct PtWalk {
+    int r, c, dr, dc, per;
+    __device__ PtWalk(int first, int per_) : per(per_)
+    {
+        r = first / per; c = first - r * per;
+        dr = PT_THREADS / per; dc = PT_THREADS - dr * per;
+    }
+    __device__ void next()
+    {
+        r += dr; c += dc;
+        if (c >= per) { c -= per; ++r; }
+    }
+};
+
+// REDUCE sums of the five-tap row of input row gy for the quad at column x
+// (packed 16-bit lanes, see pd_hsum); `fast` quads read four aligned words.
+__device__ __forceinline__ void pt_hrow(const unsigned char *row, int x, int wi, int xs, bool fast, unsigned &a,
+                                        unsigned &b)
+{
+    PdWords v;
+    if (fast) {
+        const unsigned *q = reinterpret_cast<const unsigned *>(row + (2 * x - 4 - xs));
+        v.wl = q[0]; v.w0 = q[1]; v.w1 = q[2]; v.wr = q[3];
+    } else {
+        unsigned bb[11];
+#pragma unroll
+        for (int i = 0; i < 11; ++i) bb[i] = row[reflect101(2 * x - 2 + i, wi) - xs];
+        v.wl = (bb[0] << 16) | (bb[1] << 24);
+        v.w0 = bb[2] | (bb[3] << 8) | (bb[4] << 16) | (bb[5] << 24);
+        v.w1 = bb[6] | (bb[7] << 8) | (bb[8] << 16) | (bb[9] << 24);
+        v.wr = bb[10];
+    }
+    pd_hsum(v, a, b);
+}
+
+template <typename PT>
+__global__ void __launch_bounds__(PT_THREADS, 4) k_pyr_tail(const StreamDev *__restrict__ S, WorkList wl, int l0,
+                                                         int l1, int slot_ov)
+{
+    extern __shared__ __align__(16) unsigned char pt_smem[];
+    __shared__ PtRegion sreg[PT_MAXD + 1];
+    const int tid = threadIdx.x;
+    for (int item = blockIdx.x; item < wl.total; item += gridDim.x) {
+        const int s = wl_stream(wl, item);
+        const StreamDev &D = S[s];
+        const int local = item - __ldg(&wl.prefix[s]);
+        const int slot = slot_ov >= 0 ? slot_ov : stab_pslot(D.st->t);
+        const int lt = min(l1, D.L) - 1, nd = lt - l0 + 1;   // fused levels of this stream
+        const int ntx = (D.lw[lt] + PT_TW - 1) / PT_TW;
+        const int X0 = (local % ntx) * PT_TW, Y0 = (local / ntx) * PT_TH;
+        if (tid == 0) pt_regions(nd, X0, Y0, X0 + PT_TW, Y0 + PT_TH, sreg);
+        __syncthreads();
+        // ---- stage level l0 - 1: the clipped region, whole 16-byte chunks of the rows
+        {
+            const int li = l0 - 1, wi = D.lw[li], hi = D.lh[li], pi = D.lp[li];
+            const PtRegion Q = sreg[nd];
+            const int r0 = max(Q.ys, 0), r1 = min(Q.ye, hi);
+            const int c0 = max(Q.xs, 0), c1 = min(Q.xe, wi);   // c0 % 16 == 0
+            const int nch = c1 > c0 ? (c1 - c0 + 15) >> 4 : 0, n = (r1 - r0) * nch;
+            const uint8_t *src = D.u8[slot][li];
+            unsigned char *dst = pt_smem + Q.off;
+            if (n > 0) {
+                PtWalk wk(tid, nch);
+                for (int e = tid; e < n; e += PT_THREADS, wk.next()) {
+                    const int gy = r0 + wk.r, gx = c0 + 16 * wk.c;   // gx + 16 <= pitch: the chunk stays in the row
+                    const unsigned d =
+                        (unsigned)__cvta_generic_to_shared(dst + (gy - Q.ys) * Q.stride + (gx - Q.xs));
+                    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(d),
+                                 "l"(src + (size_t)gy * pi + gx) : "memory");
+                }
+            }
+            asm volatile("cp.async.wait_all;\n" ::: "memory");
+            __syncthreads();
+        }
+        // ---- levels l0 .. lt: build region k from region k + 1, emit the tile of k + 1
+        for (int k = nd - 1; k >= -1; --k) {
+            // emit the own tile of the level of region k + 1 (if it is a fused level)
+            if (k + 1 < nd) {
+                const int l = lt - (k + 1);
+                const int w = D.lw[l], h = D.lh[l];
+                const PtRegion Q = sreg[k + 1];
+                const unsigned char *b = pt_smem + Q.off;
+                const int oy0 = Y0 << (k + 1), oy1 = min((Y0 + PT_TH) << (k + 1), h);
+                const int ox0 = X0 << (k + 1), ox1 = min((X0 + PT_TW) << (k + 1), w);
+                const int nq = (ox1 - ox0 + 3) >> 2, n = (oy1 - oy0) * nq;
+                if (n > 0) {
+                    PtWalk wk(tid, nq);
+                    for (int e = tid; e < n; e += PT_THREADS, wk.next()) {
+                        const int x = ox0 + 4 * wk.c, y = oy0 + wk.r;
+                        const unsigned char *row = b + (y - Q.ys) * Q.stride + (x - Q.xs);
+                        const unsigned mid = *reinterpret_cast<const unsigned *>(row);
+                        const unsigned up = y > 0 ? *reinterpret_cast<const unsigned *>(row - Q.stride) : mid;
+                        const unsigned dn = y + 1 < h ? *reinterpret_cast<const unsigned *>(row + Q.stride) : mid;
+                        const unsigned lo = x > 0 ? row[-1] : (mid & 255u);
+                        emit_row<PT>(D, slot, l, x, y, w, up, lo, mid, row[4], dn);
+                    }
+                }
+            }
+            if (k < 0) break;
+            // build region k (level lt - k) from region k + 1 (level lt - k - 1): a
+            // thread walks a band of rows down one quad column, five input row sums in
+            // flight (two new ones per output row)
+            {
+                const int l = lt - k, li = l - 1;
+                const int w = D.lw[l], h = D.lh[l], wi = D.lw[li], hi = D.lh[li];
+                const PtRegion Q = sreg[k], P = sreg[k + 1];
+                const unsigned char *bi = pt_smem + P.off;
+                unsigned char *bo = pt_smem + Q.off;
+                const int r0 = max(Q.ys, 0), r1 = min(Q.ye, h);
+                const int x0 = max(Q.xs, 0), x1 = min(Q.xe, w);
+                const int nq = x1 > x0 ? (x1 - x0 + 3) >> 2 : 0, nr = r1 - r0;
+                if (nq > 0 && nr > 0) {
+                    const int nb = min(max(PT_THREADS / nq, 1), nr);          // bands
+                    const int bh = (nr + nb - 1) / nb;                          // rows per band
+                    for (int task = tid; task < nq * nb; task += PT_THREADS) {
+                        const int band = task / nq, x = x0 + 4 * (task - band * nq);
+                        const int ya = r0 + band * bh, yb = min(ya + bh, r1);
+                        if (ya >= yb) continue;
+                        const bool fast = x >= 1 && 2 * x + 8 <= wi - 1;
+                        auto hrow = [&](int v, unsigned &a, unsigned &c) {
+                            pt_hrow(bi + (reflect101(v, hi) - P.ys) * P.stride, x, wi, P.xs, fast, a, c);
+                        };
+                        unsigned a0, c0, a1, c1, a2, c2;
+                        hrow(2 * ya - 2, a0, c0);
+                        hrow(2 * ya - 1, a1, c1);
+                        hrow(2 * ya, a2, c2);
+                        unsigned char *o = bo + (ya - Q.ys) * Q.stride + (x - Q.xs);
+                        for (int y = ya; y < yb; ++y, o += Q.stride) {
+                            unsigned a3, c3, a4, c4;
+                            hrow(2 * y + 1, a3, c3);
+                            hrow(2 * y + 2, a4, c4);
+                            *reinterpret_cast<unsigned *>(o) = pd_vsum(a0, a1, a2, a3, a4, c0, c1, c2, c3, c4);
+                            a0 = a2; c0 = c2; a1 = a3; c1 = c3; a2 = a4; c2 = c4;
+                        }
+                    }
+                }
+            }
+            __syncthreads();
+        }
+        __syncthreads();   // the buffers and the region table are refilled for the next item
+    }
+}
+
 template <typename PT>
 __global__ void k_plane_f32(const StreamDev *__restrict__ S, int slot, int l, float *I, float *Ix, float *Iy)
 {
@@ -366,6 +565,36 @@ void launch_pyr_down(const Launch &L, int prec, const StreamDev *S, WorkList wl,
     int g = grid_for(L, (wl.total + 3) / 4, prec ? occ_pyr_h() : occ_pyr_f());
     if (prec) k_pyr_down<__half><<<g, 128, 0, L.stream>>>(S, wl, l, slot_ov);
     else k_pyr_down<float><<<g, 128, 0, L.stream>>>(S, wl, l, slot_ov);
+}
+
+static int occ_tail(int prec)
+{
+    static DevCache c[2];
+    return c[prec ? 1 : 0].get([prec] {
+        int v = 0;
+        const int smem = pt_smem_bytes();
+        cudaError_t e;
+        if (prec) {
+            cudaFuncSetAttribute(k_pyr_tail<__half>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, k_pyr_tail<__half>, PT_THREADS, smem);
+        } else {
+            cudaFuncSetAttribute(k_pyr_tail<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, k_pyr_tail<float>, PT_THREADS, smem);
+        }
+        return (e != cudaSuccess || v < 1) ? 1 : v;
+    });
+}
+
+int pyr_tail_tile_w() { return PT_TW; }
+int pyr_tail_tile_h() { return PT_TH; }
+int pyr_tail_levels() { return PT_MAXD; }
+void warm_pyr_tail() { occ_tail(0); occ_tail(1); }
+
+void launch_pyr_tail(const Launch &L, int prec, const StreamDev *S, WorkList wl, int l0, int l1, int slot_ov)
+{
+    const int g = grid_for(L, wl.total, occ_tail(prec)), smem = pt_smem_bytes();
+    if (prec) k_pyr_tail<__half><<<g, PT_THREADS, smem, L.stream>>>(S, wl, l0, l1, slot_ov);
+    else k_pyr_tail<float><<<g, PT_THREADS, smem, L.stream>>>(S, wl, l0, l1, slot_ov);
 }
 
 void launch_plane_f32(const Launch &L, int prec, const StreamDev *S, int slot, int l, float *I, float *Ix, float *Iy)

@@ -102,6 +102,14 @@ struct WarpIO {
 
 void launch_level0(const Launch &L, int prec, const StreamDev *S, WorkList wl, FrameSrc ov);
 void launch_pyr_down(const Launch &L, int prec, const StreamDev *S, WorkList wl, int l, int slot_ov);
+// Levels l0 .. l1-1 (at most pyr_tail_levels()) in one launch; work items are
+// tiles of pyr_tail_tile_w() x pyr_tail_tile_h() pixels of each stream's last
+// level below l1 (none for a stream with l0 levels or fewer).
+void launch_pyr_tail(const Launch &L, int prec, const StreamDev *S, WorkList wl, int l0, int l1, int slot_ov);
+int pyr_tail_tile_w();
+int pyr_tail_tile_h();
+int pyr_tail_levels();
+void warm_pyr_tail();
 void launch_plane_f32(const Launch &L, int prec, const StreamDev *S, int slot, int l, float *I, float *Ix,
                       float *Iy);
 int occ_level0_f();

@@ -27,7 +27,7 @@ struct Pipeline {
     char *arena = nullptr;
     size_t arena_bytes = 0;
     int *prefix = nullptr;
-    WorkList wl_l0{}, wl_pyr[STAB_MAXL]{}, wl_resp{}, wl_filter{}, wl_lk{}, wl_warp{};
+    WorkList wl_l0{}, wl_pyr[STAB_MAXL]{}, wl_tail[STAB_MAXL]{}, wl_resp{}, wl_filter{}, wl_lk{}, wl_warp{};
     std::string err;
     cudaStream_t last = nullptr;
     cudaStream_t cap = nullptr;
@@ -245,6 +245,15 @@ stab_status build(Pipeline &pp, int n, const int *w, const int *h, const int *C,
     mk(&pp.wl_l0, [](const StreamDev &D) { return ((D.w + 511) / 512) * ((D.h + 31) / 32); });
     for (int l = 1; l < STAB_MAXL; ++l)
         mk(&pp.wl_pyr[l], [l](const StreamDev &D) { return l < D.L ? stab_pd_items(D.lw[l], D.lh[l]) : 0; });
+    // levels 2 .. L-1 in groups of pyr_tail_levels(); items are tiles of each
+    // stream's last level of the group
+    for (int l0 = 2; l0 < STAB_MAXL; l0 += pyr_tail_levels())
+        mk(&pp.wl_tail[l0], [l0](const StreamDev &D) {
+            if (D.L <= l0) return 0;
+            const int lt = std::min(l0 + pyr_tail_levels(), D.L) - 1;
+            return ((D.lw[lt] + pyr_tail_tile_w() - 1) / pyr_tail_tile_w()) *
+                   ((D.lh[lt] + pyr_tail_tile_h() - 1) / pyr_tail_tile_h());
+        });
     mk(&pp.wl_resp, [](const StreamDev &D) { return stab_resp_items(D.roi_x1 - D.roi_x0, D.roi_y1 - D.roi_y0); });
     mk(&pp.wl_filter, [](const StreamDev &D) { return (D.cand_cap + 2047) / 2048; });
     mk(&pp.wl_lk, [](const StreamDev &D) { return D.K; });
@@ -261,15 +270,33 @@ stab_status build(Pipeline &pp, int n, const int *w, const int *h, const int *C,
     // features of unequal cost (iterations, lost tracks) go to whichever group is free
     pp.wl_lk.ctr = reinterpret_cast<unsigned *>(pp.prefix + o);
     // kernel attributes and occupancy queries happen here, outside any capture
-    occ_level0_f(); occ_level0_h(); occ_pyr_f(); occ_pyr_h();
+    occ_level0_f(); occ_level0_h(); occ_pyr_f(); occ_pyr_h(); warm_pyr_tail();
     warm_detect(); warm_warp(); warm_lk();
     return cuda_check(pp.err, "create");
+}
+
+// Levels >= 1 of pyramid slot `slot` (-1: each stream's slot of its frame
+// index): level 1 by the strip kernel, the rest by the fused tile kernel in
+// groups of pyr_tail_levels() levels.  prof (optional) marks each launch.
+template <typename Mark>
+void reduce_levels(Pipeline &pp, const Launch &L, int slot, Mark mark)
+{
+    static const char *tail_names[STAB_MAXL] = {"", "", "pyr_tail_2", "pyr_tail_3", "pyr_tail_4",
+                                                 "pyr_tail_5", "pyr_tail_6", "pyr_tail_7"};
+    if (pp.Lmax > 1) {
+        launch_pyr_down(L, pp.prec, pp.ds, pp.wl_pyr[1], 1, slot);
+        mark("pyr_down_1");
+    }
+    for (int l0 = 2; l0 < pp.Lmax; l0 += pyr_tail_levels()) {
+        launch_pyr_tail(L, pp.prec, pp.ds, pp.wl_tail[l0], l0, std::min(l0 + pyr_tail_levels(), pp.Lmax), slot);
+        mark(tail_names[l0]);
+    }
 }
 
 void build_pyr(Pipeline &pp, const Launch &L, const uint8_t *frame, int pitch, int C, int slot)
 {
     launch_level0(L, pp.prec, pp.ds, pp.wl_l0, FrameSrc{frame, pitch, C, slot});
-    for (int l = 1; l < pp.Lmax; ++l) launch_pyr_down(L, pp.prec, pp.ds, pp.wl_pyr[l], l, slot);
+    reduce_levels(pp, L, slot, [](const char *) {});
 }
 
 void detect_chain(Pipeline &pp, const Launch &L, DetIO io)
@@ -297,8 +324,6 @@ struct Prof {
 void enqueue_step(Pipeline &pp, cudaStream_t s, Prof *pf = nullptr)
 {
     Launch L{s, pp.sms};
-    static const char *pyr_names[STAB_MAXL] = {"", "pyr_down_1", "pyr_down_2", "pyr_down_3", "pyr_down_4",
-                                                "pyr_down_5", "pyr_down_6", "pyr_down_7"};
     auto mark = [&](const char *n) { if (pf) pf->mark(n); };
     mark(nullptr);
     launch_begin(L, pp.ds, pp.n, -1, 0);
@@ -306,10 +331,7 @@ void enqueue_step(Pipeline &pp, cudaStream_t s, Prof *pf = nullptr)
     if (pf) {   // measured one kernel at a time
         launch_level0(L, pp.prec, pp.ds, pp.wl_l0, FrameSrc{nullptr, 0, 0, 0});
         mark("level0");
-        for (int l = 1; l < pp.Lmax; ++l) {
-            launch_pyr_down(L, pp.prec, pp.ds, pp.wl_pyr[l], l, -1);
-            mark(pyr_names[l]);
-        }
+        reduce_levels(pp, L, -1, mark);
         launch_response(L, pp.ds, pp.wl_resp, DetIO{});
         mark("response");
         launch_filter(L, pp.ds, pp.wl_filter);
@@ -343,7 +365,7 @@ void enqueue_step(Pipeline &pp, cudaStream_t s, Prof *pf = nullptr)
         launch_fit(Ls, pp.ds, pp.n, FitIO{}, 1, pp.hmax);
         cudaEventRecord(pp.ev_det, pp.side);
         launch_level0(L, pp.prec, pp.ds, pp.wl_l0, FrameSrc{nullptr, 0, 0, 0});
-        for (int l = 1; l < pp.Lmax; ++l) launch_pyr_down(L, pp.prec, pp.ds, pp.wl_pyr[l], l, -1);
+        reduce_levels(pp, L, -1, [](const char *) {});
         cudaStreamWaitEvent(s, pp.ev_det, 0);
         cudaStreamWaitEvent(s, pp.ev_warp, 0);
     }
