@@ -297,7 +297,8 @@ stab_status stab_batch_step_host(stab_batch *b, const uint8_t *const *frames_hos
  * added to it.  Needs at least three steps run (the tracker has features from
  * the third); synchronous on `stream`.
  * *variant (may be NULL) receives the choice; ms_out (may be NULL, one float
- * per variant) the measured mean ms per launch (-1 when taken from the cache). */
+ * per variant: stab_lk_variants() floats) the measured mean ms per launch (-1
+ * when taken from the cache). */
 stab_status stab_batch_autotune(stab_batch *b, const char *cache_path, int *variant, float *ms_out, void *stream);
 /* Bound the candidate list of corner detection (the NMS survivors kept
  * before the top-K selection, Sec. 3.1) of every stream of a context or batch
@@ -310,14 +311,18 @@ stab_status stab_batch_autotune(stab_batch *b, const char *cache_path, int *vari
  * latched-error path.  Synchronous: waits for the context's last stream. */
 stab_status stab_set_candidate_capacity(stab_ctx *ctx, int cap);
 stab_status stab_batch_set_candidate_capacity(stab_batch *b, int cap);
-/* Force a tracker variant (0..4) for a batch or a single-stream context:
+/* Force a tracker variant (0..6) for a batch or a single-stream context:
  * 0 / 1: one warp per feature, template in registers, register budgets of
  * 128 / 168; 2 / 3: two warps per feature, budgets of 80 / 128; 4: one warp
- * per feature, template in shared memory, budget of 96 (more resident warps).
- * The one-warp variants (0, 1, 4) give identical results; the two-warp ones
- * sum the window in another order (FP32 rounding differences only). */
+ * per feature, template in shared memory, budget of 96 (more resident warps);
+ * 5 / 6: two features per warp (a half-warp each), budgets of 255 / 168.
+ * Variants 0, 1 and 4 give identical results; the others sum the window in
+ * another order (FP32 rounding differences only).  Variants other than 0 serve
+ * the 21 x 21 window; other windows run variant 0. */
 stab_status stab_batch_set_lk_variant(stab_batch *b, int variant);
 stab_status stab_set_lk_variant(stab_ctx *ctx, int variant);
+/* Number of tracker variants (the size stab_batch_autotune's ms_out must have). */
+int stab_lk_variants(void);
 /* Copy the motions of the last step (n entries) to host memory (synchronous). */
 stab_status stab_batch_motions(stab_batch *b, stab_motion *out_host);
 /* Copy stream i's current feature set (2 * max_corners floats) and its count. */

@@ -456,6 +456,281 @@ __global__ void __launch_bounds__(128, MINB) k_lk(const StreamDev *__restrict__ 
     }
 }
 
+// ---------------------------------------------------------------------------
+// Two features per warp for the 21 x 21 window: each half-warp (16 lanes)
+// tracks its own feature with its own patches, 28 samples per lane (four
+// column segments of 7 rows, run as two pairs in packed f32x2 arithmetic).
+// The per-level and per-iteration control (staging, the 2 x 2 solve, the
+// convergence test, the loop bookkeeping) is one instruction stream for both
+// features, and each lane carries twice the independent arithmetic between
+// two reductions (four butterfly steps over the half-warp instead of five).
+// The two halves run the same loops with per-half flags: a half whose
+// feature is lost, converged or absent idles (its shared memory holds finite
+// values, its results are discarded) until the other finishes.
+
+// Sum over the 16 lanes of a half-warp (xor butterfly: the same bits in every lane).
+__device__ __forceinline__ float hsum16(float v)
+{
+#pragma unroll
+    for (int o = 8; o; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+template <typename PT>
+__device__ __noinline__ bool lk_track2(const StreamDev &D, int sa, int sb, bool act, float ux, float uy, float &vx,
+                                       float &vy, int &iters, int &tpl, PT *sI, typename Plane2<PT>::type *sG,
+                                       PT *sJ, int hl)
+{
+    typedef typename Plane2<PT>::type PT2;
+    constexpr int NT = 16, SEG = 7, Q = 4, ww = 21, pw = ww + 1, N = ww * ww, pj = pw + 2 * LK_MARGIN;
+    constexpr int swI = lk_sw(pw), swJ = lk_sw(pj);
+    // segments hl + 16 q (q = 0 .. 3): column (hl + 16 q) % 21, rows 7 ((hl + 16 q) / 21) .. + 6; the 64th
+    // (lane 15, q = 3) lies past the window and reads rows 0 .. 7 of column 0, dropped from every sum
+    int scol[Q], srow[Q];
+    bool sv[Q];
+#pragma unroll
+    for (int q = 0; q < Q; ++q) {
+        const int sgi = hl + NT * q;
+        sv[q] = sgi < ww * 3;
+        scol[q] = sv[q] ? sgi % ww : 0;
+        srow[q] = sv[q] ? (sgi / ww) * SEG : 0;
+    }
+    auto psum = [&](fx2 v, int pp) {
+        float u0, u1;
+        upk(v, u0, u1);
+        return (sv[2 * pp] ? u0 : 0.f) + (sv[2 * pp + 1] ? u1 : 0.f);
+    };
+    float gx = 0.f, gy = 0.f, dx = 0.f, dy = 0.f;
+    fx2 TT[2 * SEG], TTX[2 * SEG], TTY[2 * SEG];
+    bool ok = act;
+    const int L = act ? D.L : 0, Lw = max(L, __shfl_xor_sync(0xffffffffu, L, 16));
+    const int maxit = act ? D.max_iters : 0, maxw = max(maxit, __shfl_xor_sync(0xffffffffu, maxit, 16));
+    for (int l = Lw - 1; l >= 0; --l) {
+        const bool on = ok && l < L;   // this half works at level l
+        const int lc = on ? l : 0;
+        const PT *Ia = reinterpret_cast<const PT *>(D.pI[sa][lc]);
+        const PT2 *Ga = reinterpret_cast<const PT2 *>(D.pG[sa][lc]);
+        const PT *Jb = reinterpret_cast<const PT *>(D.pI[sb][lc]);
+        const int wl = D.lw[lc], hlv = D.lh[lc], p = D.lp[lc];
+        const float sc = __int_as_float((127 - lc) << 23);   // 2^-l
+        const float px = ux * sc, py = uy * sc;
+        const float bx = fminf(fmaxf(px, -64.f), (float)wl + 64.f);
+        const float by = fminf(fmaxf(py, -64.f), (float)hlv + 64.f);
+        const float fx = floorf(bx), fy = floorf(by);
+        const float ax = bx - fx, ay = by - fy;
+        const int ix = (int)fx - 10, iy = (int)fy - 10;
+        const bool inside = ix >= 0 && ix + ww <= wl - 1 && iy >= 0 && iy + ww <= hlv - 1;
+        int jx0 = (int)floorf(fminf(fmaxf(px + gx, -64.f), (float)wl + 64.f)) - 10 - LK_MARGIN;
+        int jy0 = (int)floorf(fminf(fmaxf(py + gy, -64.f), (float)hlv + 64.f)) - 10 - LK_MARGIN;
+        bool jin = jx0 >= 0 && jx0 + pj - 1 <= wl - 1 && jy0 >= 0 && jy0 + pj - 1 <= hlv - 1;
+        __syncwarp();
+        int offI = 0, offJ = 0;
+        if (on) {
+            offI = stage<PT, NT>(Ia, p, wl, hlv, ix, iy, pw, swI, inside, sI, hl);
+            stage<PT2, NT>(Ga, p, wl, hlv, ix, iy, pw, swI, inside, sG, hl);
+            offJ = stage<PT, NT>(Jb, p, wl, hlv, jx0, jy0, pj, swJ, jin, sJ, hl);
+        }
+        cpa_wait_all();
+        __syncwarp();
+        // ---- template T, Tx, Ty and G over the window
+        const fx2 AX = pk(ax, ax), AY = pk(ay, ay);
+        fx2 sxx[2], sxy[2], syy[2];
+#pragma unroll
+        for (int pp = 0; pp < 2; ++pp) {
+            const int qa = 2 * pp, qb = 2 * pp + 1;
+            sxx[pp] = pk(0.f, 0.f); sxy[pp] = sxx[pp]; syy[pp] = sxx[pp];
+            const PT *pIa = sI + offI + scol[qa] + srow[qa] * swI, *pIb = sI + offI + scol[qb] + srow[qb] * swI;
+            const PT2 *pGa = sG + offI + scol[qa] + srow[qa] * swI, *pGb = sG + offI + scol[qb] + srow[qb] * swI;
+            float2 ga0 = f2(pGa[0]), ga1 = f2(pGa[1]), gb0 = f2(pGb[0]), gb1 = f2(pGb[1]);
+            fx2 a0 = pk(f1(pIa[0]), f1(pIb[0])), a1 = pk(f1(pIa[1]), f1(pIb[1]));
+            fx2 hI = fma2(AX, sub2(a1, a0), a0);
+            a0 = pk(ga0.x, gb0.x); a1 = pk(ga1.x, gb1.x);
+            fx2 hX = fma2(AX, sub2(a1, a0), a0);
+            a0 = pk(ga0.y, gb0.y); a1 = pk(ga1.y, gb1.y);
+            fx2 hY = fma2(AX, sub2(a1, a0), a0);
+#pragma unroll
+            for (int e = 0; e < SEG; ++e) {
+                const int o = (e + 1) * swI;
+                ga0 = f2(pGa[o]); ga1 = f2(pGa[o + 1]); gb0 = f2(pGb[o]); gb1 = f2(pGb[o + 1]);
+                a0 = pk(f1(pIa[o]), f1(pIb[o])); a1 = pk(f1(pIa[o + 1]), f1(pIb[o + 1]));
+                const fx2 hI1 = fma2(AX, sub2(a1, a0), a0);
+                a0 = pk(ga0.x, gb0.x); a1 = pk(ga1.x, gb1.x);
+                const fx2 hX1 = fma2(AX, sub2(a1, a0), a0);
+                a0 = pk(ga0.y, gb0.y); a1 = pk(ga1.y, gb1.y);
+                const fx2 hY1 = fma2(AX, sub2(a1, a0), a0);
+                const int m = pp * SEG + e;
+                TT[m] = fma2(AY, sub2(hI1, hI), hI);
+                TTX[m] = fma2(AY, sub2(hX1, hX), hX);
+                TTY[m] = fma2(AY, sub2(hY1, hY), hY);
+                sxx[pp] = fma2(TTX[m], TTX[m], sxx[pp]);
+                sxy[pp] = fma2(TTX[m], TTY[m], sxy[pp]);
+                syy[pp] = fma2(TTY[m], TTY[m], syy[pp]);
+                hI = hI1; hX = hX1; hY = hY1;
+            }
+        }
+        const float gxx = hsum16(psum(sxx[0], 0) + psum(sxx[1], 1));
+        const float gxy = hsum16(psum(sxy[0], 0) + psum(sxy[1], 1));
+        const float gyy = hsum16(psum(syy[0], 0) + psum(syy[1], 1));
+        if (on) ++tpl;
+        const float lam = 0.5f * ((gxx + gyy) - sqrtf((gxx - gyy) * (gxx - gyy) + 4.f * gxy * gxy));
+        const float det = gxx * gyy - gxy * gxy;
+        if (on && (!(lam >= D.min_eig * (float)N) || !(det > 0.f))) ok = false;
+        const float idet = 1.f / det;
+        // ---- iterations
+        bool run = on && ok;
+        float nx = 0.f, ny = 0.f;
+        for (int it = 0; it < maxw; ++it) {
+            if (!__any_sync(0xffffffffu, run)) break;
+            const float qx = fminf(fmaxf(px + gx + nx, -64.f), (float)wl + 64.f);
+            const float qy = fminf(fmaxf(py + gy + ny, -64.f), (float)hlv + 64.f);
+            const float fqx = floorf(qx), fqy = floorf(qy);
+            const float cx = qx - fqx, cy = qy - fqy;
+            const int jx = (int)fqx - 10, jy = (int)fqy - 10;
+            int ox = jx - jx0, oy = jy - jy0;
+            const bool need = run && (ox < 0 || ox > 2 * LK_MARGIN || oy < 0 || oy > 2 * LK_MARGIN);
+            if (__any_sync(0xffffffffu, need)) {
+                __syncwarp();
+                if (need) {
+                    jx0 = jx - LK_MARGIN;
+                    jy0 = jy - LK_MARGIN;
+                    jin = jx0 >= 0 && jx0 + pj - 1 <= wl - 1 && jy0 >= 0 && jy0 + pj - 1 <= hlv - 1;
+                    offJ = stage<PT, NT>(Jb, p, wl, hlv, jx0, jy0, pj, swJ, jin, sJ, hl);
+                }
+                cpa_wait_all();
+                __syncwarp();
+                if (need) { ox = LK_MARGIN; oy = LK_MARGIN; }
+            }
+            // a half that is not running may hold any offsets: keep its reads inside its patch
+            if (!run) { ox = 0; oy = 0; }
+            const PT *sJo = sJ + oy * swJ + ox + offJ;
+            const fx2 CX = pk(cx, cx), CY = pk(cy, cy);
+            float bxs = 0.f, bys = 0.f;
+#pragma unroll
+            for (int pp = 0; pp < 2; ++pp) {
+                const int qa = 2 * pp, qb = 2 * pp + 1;
+                const PT *pJa = sJo + scol[qa] + srow[qa] * swJ, *pJb = sJo + scol[qb] + srow[qb] * swJ;
+                fx2 a0 = pk(f1(pJa[0]), f1(pJb[0])), a1 = pk(f1(pJa[1]), f1(pJb[1]));
+                fx2 h = fma2(CX, sub2(a1, a0), a0);
+                fx2 ax2 = pk(0.f, 0.f), ay2 = ax2;
+#pragma unroll
+                for (int e = 0; e < SEG; ++e) {
+                    const int o = (e + 1) * swJ;
+                    a0 = pk(f1(pJa[o]), f1(pJb[o])); a1 = pk(f1(pJa[o + 1]), f1(pJb[o + 1]));
+                    const fx2 h1 = fma2(CX, sub2(a1, a0), a0);
+                    const int m = pp * SEG + e;
+                    const fx2 err = sub2(TT[m], fma2(CY, sub2(h1, h), h));
+                    ax2 = fma2(err, TTX[m], ax2);
+                    ay2 = fma2(err, TTY[m], ay2);
+                    h = h1;
+                }
+                bxs += psum(ax2, pp);
+                bys += psum(ay2, pp);
+            }
+            bxs = hsum16(bxs);
+            bys = hsum16(bys);
+            if (run) {
+                const float ex = (gyy * bxs - gxy * bys) * idet;
+                const float ey = (gxx * bys - gxy * bxs) * idet;
+                nx += ex; ny += ey;
+                ++iters;
+                if (ex * ex + ey * ey < D.eps2 || it + 1 >= maxit) run = false;
+            }
+        }
+        if (on && ok) {
+            if (l > 0) { gx = 2.f * (gx + nx); gy = 2.f * (gy + ny); }
+            else { dx = gx + nx; dy = gy + ny; }
+        }
+    }
+    if (!ok) { vx = ux; vy = uy; return false; }
+    vx = ux + dx; vy = uy + dy;
+    return vx >= 0.f && vx <= (float)(D.w - 1) && vy >= 0.f && vy <= (float)(D.h - 1);
+}
+
+template <typename PT, int MINB>
+__global__ void __launch_bounds__(128, MINB) k_lk2(const StreamDev *__restrict__ S, WorkList wl, LkIO io)
+{
+    typedef typename Plane2<PT>::type PT2;
+    extern __shared__ __align__(16) unsigned char lk_smem[];
+    constexpr int ES = (int)sizeof(PT);
+    const int grp = threadIdx.x >> 4, hl = threadIdx.x & 15;
+    unsigned char *base = lk_smem + grp * lk_group_bytes(10, ES);
+    const int bI = lk_bytes_I(10, ES);
+    PT *sI = reinterpret_cast<PT *>(base);
+    PT2 *sG = reinterpret_cast<PT2 *>(base + bI);
+    PT *sJ = reinterpret_cast<PT *>(base + 3 * bI);
+    const int ngroups = (gridDim.x * blockDim.x) >> 4;
+    auto bcast = [](int v) { return __shfl_sync(0xffffffffu, v, 0, 16); };   // from lane 0 of each half
+    int item = (blockIdx.x * blockDim.x + threadIdx.x) >> 4, tk = 0;
+    if (wl.ctr) item = bcast(hl == 0 ? (int)atomicAdd(wl.ctr, 1u) : 0);
+    while (__any_sync(0xffffffffu, item < wl.total)) {
+        const bool have = item < wl.total;
+        if (wl.ctr && hl == 0 && have) tk = (int)atomicAdd(wl.ctr, 1u);   // drawn now, used after this item
+        const int s = have ? wl_stream(wl, item) : 0;
+        const StreamDev &D = S[s];
+        StreamState *st = D.st;
+        const int f = have ? item - __ldg(&wl.prefix[s]) : 0;
+        int n = 0, sp = 0, sn = 1;
+        const float2 *pts = D.feat;
+        if (io.pts) { n = io.n; pts = io.pts; sp = io.slot_prev; sn = io.slot_next; }
+        else if (have) {
+            const long long tb = st->t - D.lag;   // frames tb-1 -> tb
+            if (tb >= 1) { n = st->n_feat; sp = stab_pslot(tb - 1); sn = stab_pslot(tb); }
+        }
+        const bool valid = have && f < n;
+        const float2 u = valid ? pts[f] : make_float2(0.f, 0.f);
+        int iters = 0, tpl = 0;
+        float vx, vy, bx = u.x, by = u.y;
+        const bool ok1 = lk_track2<PT>(D, sp, sn, valid, u.x, u.y, vx, vy, iters, tpl, sI, sG, sJ, hl);
+        const bool ok2 = lk_track2<PT>(D, sn, sp, valid && ok1, vx, vy, bx, by, iters, tpl, sI, sG, sJ, hl) &&
+                         valid && ok1;
+        if (!ok1) { bx = u.x; by = u.y; }
+        const float ex = bx - u.x, ey = by - u.y;
+        const float e2 = ex * ex + ey * ey;
+        if (valid && hl == 0) {
+            float2 *fwd = io.fwd ? io.fwd : D.fwd;
+            float2 *back = io.back ? io.back : D.back;
+            float *fb = io.fb ? io.fb : D.fb;
+            uint8_t *stt = io.status ? io.status : D.status;
+            uint8_t *stf = io.status_fwd ? io.status_fwd : D.status_fwd;
+            fwd[f] = make_float2(vx, vy);
+            back[f] = make_float2(bx, by);
+            fb[f] = ok2 ? sqrtf(e2) : -1.f;
+            stt[f] = (uint8_t)(ok1 && ok2 && e2 <= D.fb2);
+            stf[f] = (uint8_t)ok1;
+            atomicAdd((unsigned long long *)&st->iters, (unsigned long long)iters);
+            atomicAdd((unsigned long long *)&st->tpl, (unsigned long long)tpl);
+        }
+        if (have) item = wl.ctr ? tk : item + ngroups;
+        item = wl.ctr ? bcast(item) : item;
+    }
+    // every half has drawn a ticket past the end; the last to finish resets the list
+    if (wl.ctr && hl == 0 && atomicAdd(wl.ctr + 1, 1u) == (unsigned)(ngroups - 1)) {
+        atomicExch(wl.ctr, 0u);
+        atomicExch(wl.ctr + 1, 0u);
+    }
+}
+
+template <typename PT, int MINB>
+struct Lk2Kernel {
+    static int smem() { return 8 * lk_group_bytes(10, (int)sizeof(PT)); }
+    static int occ()
+    {
+        static DevCache c;
+        return c.get([] {
+            int v = 0;
+            cudaFuncSetAttribute(k_lk2<PT, MINB>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem());
+            if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, k_lk2<PT, MINB>, 128, smem()) != cudaSuccess || v < 1)
+                v = 1;
+            return v;
+        });
+    }
+    static void run(const Launch &L, const StreamDev *S, WorkList wl, LkIO io)
+    {
+        const int blocks = (wl.total + 7) / 8;
+        k_lk2<PT, MINB><<<grid_for(L, blocks, occ()), 128, smem(), L.stream>>>(S, wl, io);
+    }
+};
+
 template <typename PT, int NS, int RC, int WPF, int MINB, bool TS = false>
 struct LkKernel {
     static int smem(int rmax)
@@ -492,6 +767,8 @@ struct LkKernel {
 //   3: two warps per feature, <= 128 registers (4 blocks / SM)
 //   4: one warp per feature, template in shared memory, <= 96 registers
 //      (5 blocks / SM with FP16 planes: 10.5 KB of shared memory per warp)
+//   5, 6: two features per warp (a half-warp each), <= 255 / 168 registers
+//      (2 / 3 blocks of 4 warps per SM)
 // Other radii use the runtime-radius build of variant 0.
 // rcode: the window radius shared by every stream, or minus the largest
 // radius when streams differ (then the runtime-radius build, sized for it).
@@ -504,6 +781,8 @@ void run_variant(int v, const Launch &L, const StreamDev *S, WorkList wl, LkIO i
         case 2: LkKernel<PT, 7, 10, 2, 6>::run(L, S, wl, io, 10); return;
         case 3: LkKernel<PT, 7, 10, 2, 4>::run(L, S, wl, io, 10); return;
         case 4: LkKernel<PT, 14, 10, 1, 5, true>::run(L, S, wl, io, 10); return;
+        case 5: Lk2Kernel<PT, 2>::run(L, S, wl, io); return;
+        case 6: Lk2Kernel<PT, 3>::run(L, S, wl, io); return;
         default: LkKernel<PT, 14, 10, 1, 4>::run(L, S, wl, io, 10); return;
         }
     }
@@ -520,6 +799,7 @@ void warm_all()
             LkKernel<PT, 14, 10, 1, 4>::occ(r); LkKernel<PT, 14, 10, 1, 3>::occ(r);
             LkKernel<PT, 7, 10, 2, 6>::occ(r); LkKernel<PT, 7, 10, 2, 4>::occ(r);
             LkKernel<PT, 14, 10, 1, 5, true>::occ(r);
+            Lk2Kernel<PT, 2>::occ(); Lk2Kernel<PT, 3>::occ();
             LkKernel<PT, 14, 0, 1, 4>::occ(r);
         } else if (r < 10) {
             LkKernel<PT, 14, 0, 1, 4>::occ(r);
@@ -531,7 +811,7 @@ void warm_all()
 
 }  // namespace
 
-int lk_variants() { return 5; }
+int lk_variants() { return 7; }
 
 void warm_lk()
 {

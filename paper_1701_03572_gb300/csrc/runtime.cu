@@ -752,6 +752,8 @@ stab_status stab_batch_set_candidate_capacity(stab_batch *b, int cap)
     return set_cand_cap(b->pp, cap);
 }
 
+int stab_lk_variants(void) { return lk_variants(); }
+
 stab_status stab_set_lk_variant(stab_ctx *c, int v)
 {
     if (!c || v < 0 || v >= lk_variants()) return STAB_ERR_INVALID_ARG;

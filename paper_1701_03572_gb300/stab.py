@@ -22,7 +22,7 @@ STAB_FLAG_SKIPPED, STAB_FLAG_DETECTED, STAB_FLAG_RIGID, STAB_FLAG_DECISION = 1, 
 MOTION_WORDS = 10          # 4-byte words of one stab_motion record
 BATCH_LAG = 1              # a batched step ingests frame t and tracks frames t-2 -> t-1
 BATCH_OUT_LAG = 2          # ... and composes frame t - BATCH_OUT_LAG - 1 - W/2
-LK_VARIANTS = 5            # tracker kernel variants (stab_set_lk_variant, the autotuner's candidates)
+LK_VARIANTS = 7            # tracker kernel variants (stab_set_lk_variant, the autotuner's candidates)
 
 
 class StabParams(C.Structure):
@@ -104,6 +104,7 @@ def lib():
             "stab_batch_autotune": ([_vp, C.c_char_p, C.POINTER(_i), _vp, _vp], _i),
             "stab_batch_set_lk_variant": ([_vp, _i], _i),
             "stab_set_lk_variant": ([_vp, _i], _i),
+            "stab_lk_variants": ([], _i),
             "stab_set_candidate_capacity": ([_vp, _i], _i),
             "stab_batch_set_candidate_capacity": ([_vp, _i], _i),
             "stab_batch_step_profiled": ([_vp, _vp, _vp, _i, C.POINTER(_i)], _i),
@@ -393,10 +394,11 @@ class Batch:
     def autotune(self, cache_path: str | None = None, stream=None):
         """Pick the fastest tracker variant; returns (variant, {variant: ms})."""
         v = C.c_int(-1)
-        ms = (C.c_float * 8)(*([-1.0] * 8))      # entries of variants that do not exist stay -1
+        nv = lib().stab_lk_variants()
+        ms = (C.c_float * nv)(*([-1.0] * nv))
         self._chk(lib().stab_batch_autotune(self._h, cache_path.encode() if cache_path else None, C.byref(v), ms,
                                             _s(stream)), "stab_batch_autotune")
-        return v.value, {k: ms[k] for k in range(LK_VARIANTS) if ms[k] >= 0}
+        return v.value, {k: ms[k] for k in range(nv) if ms[k] >= 0}
 
     def set_lk_variant(self, v: int):
         self._chk(lib().stab_batch_set_lk_variant(self._h, v), "stab_batch_set_lk_variant")

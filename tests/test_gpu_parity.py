@@ -185,8 +185,9 @@ PARITY_ITERS = 20
 
 
 @pytest.mark.parametrize("cfg,K,L,variant", [(0, 200, 3, 0), (0, 200, 3, 1), (0, 200, 3, 2), (0, 200, 3, 3),
-                                              (0, 200, 3, 4), (1, 500, 4, 1), (2, 1000, 5, 1), (2, 1000, 5, 3),
-                                              (2, 1000, 5, 4)])
+                                              (0, 200, 3, 4), (0, 200, 3, 5), (0, 200, 3, 6), (1, 500, 4, 1),
+                                              (1, 500, 4, 6), (2, 1000, 5, 1), (2, 1000, 5, 3), (2, 1000, 5, 4),
+                                              (2, 1000, 5, 5), (2, 1000, 5, 6)])
 def test_lk_parity(cfg, K, L, variant):
     f0, f1, pts, w, h = _lk_case(cfg, 20 + cfg, K, L)
     ref = O.track(O.pyramid(f0, L), O.pyramid(f1, L), pts, max_iters=PARITY_ITERS, eps=0.0)

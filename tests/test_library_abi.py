@@ -59,3 +59,7 @@ def test_default_params_and_argument_errors_without_a_device():
     assert L.stab_charb_forward(arr, arr, 640, 480, 1, arr, 300, 1e-3, None, None, None, None) == -1   # margin too big
     assert L.stab_charb_forward(arr, arr, 640, 480, 1, arr, 48, 0.0, None, None, None, None) == -1     # eps <= 0
     assert L.stab_version().startswith(b"gb300-stab")
+
+
+def test_variant_count_matches_the_library():
+    assert S.lib().stab_lk_variants() == S.LK_VARIANTS
