@@ -241,8 +241,8 @@ stab_status build(Pipeline &pp, int n, const int *w, const int *h, const int *C,
         wl->total = pre[n];
         lists.push_back({wl, pre});
     };
-    // level 0: strips of 512 columns x 32 rows (one thread per 4 columns)
-    mk(&pp.wl_l0, [](const StreamDev &D) { return ((D.w + 511) / 512) * ((D.h + 31) / 32); });
+    // level 0: strips of 512 columns x 16 rows (one thread per 4 columns)
+    mk(&pp.wl_l0, [](const StreamDev &D) { return ((D.w + 511) / 512) * ((D.h + 15) / 16); });
     for (int l = 1; l < STAB_MAXL; ++l)
         mk(&pp.wl_pyr[l], [l](const StreamDev &D) { return l < D.L ? stab_pd_items(D.lw[l], D.lh[l]) : 0; });
     // levels 2 .. L-1 in groups of pyr_tail_levels(); items are tiles of each
