@@ -96,14 +96,15 @@ __device__ __forceinline__ void rs_pixels(const uint8_t *__restrict__ g, int pit
     }
 }
 
-// Candidates of a strip are collected in shared memory and appended to the
-// stream's list with one global atomic per block (a full buffer appends the
-// warp's candidates directly).
-constexpr int RS_CAP = 1024;
+// Candidates of a strip are collected in the warp's shared-memory buffer and
+// appended to the stream's list with one global atomic per strip (a full
+// buffer appends the warp's candidates directly).
+constexpr int RS_CAP = 256;
 
 // Corner response (Eq. 2), NMS and candidate list as barrier-free vertical
-// strips: a thread owns ROI columns x .. x+3 of a 32-row strip and walks its
-// pixel rows once.  Per pixel row it forms the separable Sobel parts
+// strips, each warp on its own: a warp owns a strip of 120 ROI columns and 32
+// rows (drawn from an atomic ticket when the work list has one), a thread
+// columns x .. x+3 of it, and walks its pixel rows once.  Per pixel row it forms the separable Sobel parts
 // (horizontal difference and [1 2 1] smoothing) of its 4 columns and keeps two
 // rows of them; three rows give gx, gy of the previous row, whose products are
 // summed over 3 columns (the products of columns x-1 and x+4 come from the
@@ -112,14 +113,16 @@ constexpr int RS_CAP = 1024;
 // neighbours' outer scores again by shuffle) give the NMS of the row before.
 // Lanes 0 and 31 of a warp compute their columns only for lanes 1 and 30 and
 // emit nothing.  Integer sums are exact; the score is lambda32 of them.
-__global__ void __launch_bounds__(STAB_RS_THREADS) k_response(const StreamDev *__restrict__ S, WorkList wl, DetIO io)
+__global__ void __launch_bounds__(STAB_RS_THREADS, 4) k_response(const StreamDev *__restrict__ S, WorkList wl, DetIO io)
 {
-    __shared__ unsigned smax;
-    __shared__ int s_last, s_n, s_valid, s_base;
-    __shared__ unsigned s_cnt[256];
-    __shared__ unsigned long long s_keys[RS_CAP];
-    const int tid = threadIdx.x, lane = tid & 31;
-    for (int item = blockIdx.x; item < wl.total; item += gridDim.x) {
+    __shared__ unsigned long long s_keys[STAB_RS_THREADS / 32][RS_CAP];
+    const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
+    unsigned long long *wkeys = s_keys[wp];
+    const int nwarps = gridDim.x * (STAB_RS_THREADS / 32);
+    int item = blockIdx.x * (STAB_RS_THREADS / 32) + wp, tk = 0;
+    if (wl.ctr) item = __shfl_sync(0xffffffffu, lane == 0 ? (int)atomicAdd(wl.ctr, 1u) : 0, 0);
+    for (; item < wl.total; item = wl.ctr ? __shfl_sync(0xffffffffu, tk, 0) : item + nwarps) {
+        if (wl.ctr && lane == 0) tk = (int)atomicAdd(wl.ctr, 1u);   // drawn now, used after this strip
         const int s = wl_stream(wl, item);
         const StreamDev &D = S[s];
         StreamState *st = D.st;
@@ -133,13 +136,12 @@ __global__ void __launch_bounds__(STAB_RS_THREADS) k_response(const StreamDev *_
         const int w = D.w, h = D.h;
         const int rx1 = D.roi_x1, ry1 = D.roi_y1;
         const int ngx = (rx1 - D.roi_x0 + STAB_RS_COLS - 1) / STAB_RS_COLS;
-        const int x = D.roi_x0 + (local % ngx) * STAB_RS_COLS + (tid >> 5) * 120 + 4 * (lane - 1);
+        const int x = D.roi_x0 + (local % ngx) * STAB_RS_COLS + 4 * (lane - 1);
         const bool owner = lane >= 1 && lane <= 30;   // lanes 0 and 31 only supply neighbours
         const int y0 = D.roi_y0 + (local / ngx) * STAB_RS_ROWS;
         const int nrows = min(STAB_RS_ROWS, ry1 - y0);
         const bool fast = x >= 4 && x + 8 <= w && ((x | pitch) & 3) == 0 && (reinterpret_cast<uintptr_t>(g) & 3) == 0;
-        if (tid == 0) { smax = 0; s_n = 0; s_valid = RS_CAP; }
-        __syncthreads();
+        int wn = 0;   // candidates in the warp's buffer (the same in every lane)
         // own columns x .. x+3; the scores also hold columns x-1 (index 0) and x+4 (5)
         int d1[4] = {0}, d2[4] = {0}, s1[4] = {0}, s2[4] = {0};      // Sobel parts of pixel rows py-1, py-2
         int ha1[4] = {0}, hb1[4] = {0}, hc1[4] = {0};                // tensor row sums of row py-2
@@ -205,7 +207,7 @@ __global__ void __launch_bounds__(STAB_RS_THREADS) k_response(const StreamDev *_
                     }
                 }
             }
-            // warp-aggregated append of this row's candidates to the block's buffer
+            // warp-aggregated append of this row's candidates to the warp's buffer
             if (__any_sync(0xffffffffu, nk > 0)) {
                 int incl = nk;
                 for (int o = 1; o < 32; o <<= 1) {
@@ -213,20 +215,17 @@ __global__ void __launch_bounds__(STAB_RS_THREADS) k_response(const StreamDev *_
                     if (lane >= o) incl += v;
                 }
                 const int tot = __shfl_sync(0xffffffffu, incl, 31);
-                int base = 0;
-                if (lane == 31) base = atomicAdd(&s_n, tot);
-                base = __shfl_sync(0xffffffffu, base, 31);
-                // reservations only grow, so the buffered entries are those below the
-                // first reservation that did not fit
-                const bool full = base + tot > RS_CAP;
-                if (full && lane == 31) {
-                    atomicMin(&s_valid, base);
-                    base = atomicAdd(&st->n_cand, tot);   // this warp's candidates go straight out
+                int base = wn;
+                const bool full = wn + tot > RS_CAP;
+                if (full) {   // this row's candidates go straight out
+                    if (lane == 31) base = atomicAdd(&st->n_cand, tot);
+                    base = __shfl_sync(0xffffffffu, base, 31);
+                } else {
+                    wn += tot;
                 }
-                if (full) base = __shfl_sync(0xffffffffu, base, 31);
                 const int pos = base + incl - nk;
                 for (int q = 0; q < nk; ++q) {
-                    if (!full) s_keys[pos + q] = keys[q];
+                    if (!full) wkeys[pos + q] = keys[q];
                     else {
                         if (pos + q < D.cand_cap) D.cand[pos + q] = keys[q];
                         else set_err(st, STAB_ERR_CAPACITY);
@@ -244,62 +243,68 @@ __global__ void __launch_bounds__(STAB_RS_THREADS) k_response(const StreamDev *_
 #pragma unroll
             for (int i = 0; i < 6; ++i) { l2[i] = l1[i]; l1[i] = l0[i]; }
         }
-        // block max of the score; the buffered candidates go out with one atomic
+        // the strip's max score and its buffered candidates go out with one atomic each
         for (int o = 16; o; o >>= 1) lmax = max(lmax, __shfl_xor_sync(0xffffffffu, lmax, o));
-        if (lane == 0) atomicMax(&smax, lmax);
-        __syncthreads();
-        const int nb = min(s_n, s_valid);
-        if (tid == 0) s_base = nb ? atomicAdd(&st->n_cand, nb) : 0;
-        __syncthreads();
-        for (int i = tid; i < nb; i += blockDim.x) {
-            const unsigned long long key = s_keys[i];
-            if (s_base + i < D.cand_cap) D.cand[s_base + i] = key;
+        __syncwarp();   // the buffer's entries are visible to the whole warp
+        int base = 0;
+        if (lane == 0 && wn) base = atomicAdd(&st->n_cand, wn);
+        base = __shfl_sync(0xffffffffu, base, 0);
+        for (int i = lane; i < wn; i += 32) {
+            const unsigned long long key = wkeys[i];
+            if (base + i < D.cand_cap) D.cand[base + i] = key;
             else set_err(st, STAB_ERR_CAPACITY);
             atomicAdd(&D.hist[(unsigned)(key >> (32 + STAB_HSHIFT))], 1u);
         }
-        __syncthreads();
-        if (tid == 0) {
-            atomicMax(&st->lam_max, smax);
+        __syncwarp();   // the buffer is refilled by the next strip
+        int last = 0;
+        if (lane == 0) {
+            atomicMax(&st->lam_max, lmax);
             __threadfence();
-            int done = atomicAdd(&st->blocks_done, 1);
-            s_last = (done == ntiles - 1);
+            last = atomicAdd(&st->blocks_done, 1) == ntiles - 1;
         }
-        __syncthreads();
-        if (s_last) {
+        if (__shfl_sync(0xffffffffu, last, 0)) {
             // This is the stream's last strip: every append and histogram count is
             // visible (they were made before each strip's fence and ticket).
             __threadfence();
-            unsigned lm = __ldcg(&st->lam_max);
-            float thr = __fmul_rn(D.quality, __uint_as_float(lm));
-            unsigned thr_bits = __float_as_uint(thr);
-            unsigned tbin = thr_bits >> STAB_HSHIFT;
-            // thread i owns bins [4095 - 32 i - 31, 4095 - 32 i], highest first
+            const unsigned lm = __ldcg(&st->lam_max);
+            const float thr = __fmul_rn(D.quality, __uint_as_float(lm));
+            const unsigned thr_bits = __float_as_uint(thr), tbin = thr_bits >> STAB_HSHIFT;
+            // lane i owns bins [4095 - 128 i - 127, 4095 - 128 i], highest first; the
+            // K-th key lies in the first bin (from the top) where the count reaches K
+            constexpr int BPL = STAB_HBINS / 32;
             unsigned cnt = 0;
-            for (int j = 0; j < 32; ++j) {
-                unsigned b = STAB_HBINS - 1 - 32 * tid - j;
+            for (int j = 0; j < BPL; ++j) {
+                const unsigned b = STAB_HBINS - 1 - BPL * lane - j;
                 if (b >= tbin) cnt += __ldcg(&D.hist[b]);
             }
-            s_cnt[tid] = cnt;
-            __syncthreads();
-            if (tid == 0) {
-                unsigned K = (unsigned)D.K, cum = 0, bin = tbin;
-                for (int i = 0; i < STAB_RS_THREADS; ++i) {
-                    if (cum + s_cnt[i] >= K) {
-                        for (int j = 0; j < 32; ++j) {
-                            unsigned b = STAB_HBINS - 1 - 32 * i - j;
-                            if (b < tbin) break;
-                            cum += __ldcg(&D.hist[b]);
-                            if (cum >= K) { bin = b; break; }
-                        }
-                        break;
-                    }
-                    cum += s_cnt[i];
+            unsigned incl = cnt;
+            for (int o = 1; o < 32; o <<= 1) {
+                const unsigned v = __shfl_up_sync(0xffffffffu, incl, o);
+                if (lane >= o) incl += v;
+            }
+            const unsigned K = (unsigned)D.K, excl = incl - cnt;
+            unsigned bin = tbin;
+            if (excl < K && K <= incl) {   // at most one lane
+                unsigned cum = excl;
+                for (int j = 0; j < BPL; ++j) {
+                    const unsigned b = STAB_HBINS - 1 - BPL * lane - j;
+                    if (b < tbin) break;
+                    cum += __ldcg(&D.hist[b]);
+                    if (cum >= K) { bin = b; break; }
                 }
+            }
+            const unsigned who = __ballot_sync(0xffffffffu, excl < K && K <= incl);
+            if (who) bin = __shfl_sync(0xffffffffu, bin, __ffs(who) - 1);
+            if (lane == 0) {
                 st->bin_lo = bin > tbin ? bin : tbin;
                 st->thr_bits = thr_bits;
             }
         }
-        __syncthreads();
+    }
+    // every warp has drawn a ticket past the end; the last to finish resets the list
+    if (wl.ctr && lane == 0 && atomicAdd(wl.ctr + 1, 1u) == (unsigned)(nwarps - 1)) {
+        atomicExch(wl.ctr, 0u);
+        atomicExch(wl.ctr + 1, 0u);
     }
 }
 
@@ -476,7 +481,8 @@ void warm_detect()
 
 void launch_response(const Launch &L, const StreamDev *S, WorkList wl, DetIO io)
 {
-    k_response<<<grid_for(L, wl.total, occ_response()), STAB_RS_THREADS, 0, L.stream>>>(S, wl, io);
+    const int blocks = (wl.total + STAB_RS_THREADS / 32 - 1) / (STAB_RS_THREADS / 32);   // a warp per strip
+    k_response<<<grid_for(L, blocks, occ_response()), STAB_RS_THREADS, 0, L.stream>>>(S, wl, io);
 }
 
 void launch_filter(const Launch &L, const StreamDev *S, WorkList wl)

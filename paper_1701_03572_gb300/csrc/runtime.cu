@@ -260,6 +260,7 @@ stab_status build(Pipeline &pp, int n, const int *w, const int *h, const int *C,
     mk(&pp.wl_warp, [](const StreamDev &D) { return ((D.w + STAB_TW - 1) / STAB_TW) * ((D.h + STAB_WTH - 1) / STAB_WTH); });
     for (auto &e : lists) all.insert(all.end(), e.second.begin(), e.second.end());
     all.push_back(0); all.push_back(0);   // the tracker's ticket and finished-group counters
+    all.push_back(0); all.push_back(0);   // the corner response's ticket and finished-warp counters
     if (cudaMalloc(&pp.prefix, all.size() * sizeof(int)) != cudaSuccess) return fail(pp.err, STAB_ERR_OOM, "cudaMalloc");
     cudaMemcpy(pp.prefix, all.data(), all.size() * sizeof(int), cudaMemcpyHostToDevice);
     size_t o = 0;
@@ -269,6 +270,7 @@ stab_status build(Pipeline &pp, int n, const int *w, const int *h, const int *C,
     }
     // features of unequal cost (iterations, lost tracks) go to whichever group is free
     pp.wl_lk.ctr = reinterpret_cast<unsigned *>(pp.prefix + o);
+    pp.wl_resp.ctr = reinterpret_cast<unsigned *>(pp.prefix + o + 2);
     // kernel attributes and occupancy queries happen here, outside any capture
     occ_level0_f(); occ_level0_h(); occ_pyr_f(); occ_pyr_h(); warm_pyr_tail();
     warm_detect(); warm_warp(); warm_lk();
