@@ -51,7 +51,7 @@ LK_FLOP_SURVEY = (15, 7)
 # DRAM traffic per launch of the dominant kernel from one ncu capture
 # (dram__bytes_read.sum + dram__bytes_write.sum of one launch on this workload,
 # 16 streams); used only while the kernel source is unchanged.
-TRAFFIC = {"lk": {"file": "k_lk.cu", "sha": "ff90049d60006f6b", "bytes_per_launch": 190591744 + 3222784}}
+TRAFFIC = {"lk": {"file": "k_lk.cu", "sha": "81fdb5a9da7c1d73", "bytes_per_launch": 190807808 + 5619712}}
 
 
 def config_dict(streams):
@@ -288,7 +288,10 @@ def run_ours(args):
     for _ in range(A + 2 + S.BATCH_OUT_LAG):
         batch.step(True)
     tuned = None
-    if not args.no_autotune:
+    if args.lk_variant >= 0:
+        batch.set_lk_variant(args.lk_variant)
+        tuned = {"lk_variant": args.lk_variant, "lk_variant_ms": None}
+    elif not args.no_autotune:
         v, ms = batch.autotune(None)
         tuned = {"lk_variant": v, "lk_variant_ms": {str(k): round(x, 4) for k, x in ms.items()}}
     for _ in range(args.warmup):
@@ -365,7 +368,7 @@ def run_ours(args):
            "autotune": tuned, "streams_per_rank": len(mine),
            "mixed_64_streams": mixed, "photometric_gn": gn, "fits": fits}
     if ws == 1 and rank == 0 and not args.no_cpu_baseline:
-        out["cpu_baseline"] = cpu_baseline(clips[0].cpu().numpy(), args.cpu_frames)
+        out["cpu_baseline"] = cpu_baseline(clips[0].cpu().numpy(), args.cpu_frames, args.cpu_frames_single)
     if rank == 0:
         print(json.dumps(out))
     if ws > 1:
@@ -804,13 +807,13 @@ def oracle_all_cores():
     return prev, threads
 
 
-def cpu_baseline(frames, n):
+def cpu_baseline(frames, n, n1):
     """The oracle timed on one 1080p RGB stream: single-threaded (the build the
     tests use) and on all usable host cores (its OpenMP build over rows and
     features).  `value` / `cores` are the all-core run's."""
     from oracle import oracle as O
     info = cpu_info()
-    cnt1, sec1 = oracle_stream(frames, n)
+    cnt1, sec1 = oracle_stream(frames, n1)
     single = {"value": round(cnt1 / sec1, 4), "unit": "frames/s", "cores": 1, "frames": cnt1,
               "seconds": round(sec1, 2)}
     prev, threads = oracle_all_cores()
@@ -870,7 +873,10 @@ def main():
     ap.add_argument("--prof-steps", type=int, default=10)
     ap.add_argument("--plain-steps", type=int, default=60)
     ap.add_argument("--e2e-steps", type=int, default=20)
-    ap.add_argument("--cpu-frames", type=int, default=16)
+    ap.add_argument("--cpu-frames", type=int, default=640,
+                    help="frames of the oracle's all-core timing (about 10 s on 16 cores)")
+    ap.add_argument("--cpu-frames-single", type=int, default=40,
+                    help="frames of the oracle's single-thread timing (about 10 s)")
     ap.add_argument("--lat-steps", type=int, default=300, help="steps of the latency loop (0 = skip)")
     ap.add_argument("--lat-warmup", type=int, default=20)
     ap.add_argument("--clock-sampler", default=None, help=argparse.SUPPRESS)
@@ -883,6 +889,7 @@ def main():
     ap.add_argument("--clips", type=int, default=4, help="distinct seeded clips shared round-robin by the streams")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-autotune", action="store_true")
+    ap.add_argument("--lk-variant", type=int, default=-1, help="force a tracker variant instead of autotuning")
     args = ap.parse_args()
     if args.clock_sampler:
         clock_sampler_main(args.clock_sampler, args.clock_index, args.clock_uuid, args.clock_period_ms)

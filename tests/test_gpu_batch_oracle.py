@@ -113,3 +113,56 @@ def test_batch_mixed_resolutions_vs_oracle():
     motions, outs = _run_batch(clips, params)
     for i, f in enumerate(clips):
         _check_stream(f, motions[i], outs[i], ops[i], f"{MIXED[i][0]}x{MIXED[i][1]}")
+
+
+def test_batch_16_streams_in_the_benchmark_configuration():
+    """The benchmark's launch configuration: 16 streams of 1920x1080 RGB, 1000
+    corners, 5 levels, 100 hypotheses, a 30-frame window, FP16 storage, the
+    autotuned tracker.  Two of the streams (the first and the last of the
+    work lists) are checked against the oracle motion by motion and frame by
+    frame; every stream's motions are checked against the generator's exact
+    camera motion (a property that holds at any size)."""
+    T16, W30 = 22, 30          # composed frames from step 3 + 15 = 18 on
+    spec = dataclasses.replace(CONFIG_SPECS[2], frames=T16)
+    clips = [make_clip(spec, 4300 + s, device=DEV) for s in range(16)]
+    frames = [c["frames"].cpu().numpy() for c in clips]
+    p = S.default_params(max_corners=1000, levels=5, hypotheses=100, smooth_window=W30, model=S.STAB_SIMILARITY,
+                         precision=S.STAB_FP16_STORAGE)
+    b = S.Batch([(1920, 1080, 3, p)] * 16)
+    motions = [[None] * T16 for _ in range(16)]
+    outs = [{} for _ in range(16)]
+    for t in range(T16):
+        for i, f in enumerate(frames):
+            b.input_slot(i, t % b.ring).copy_(_cuda(f[t]))
+        if t == 3:
+            b.autotune(None)
+        b.step(use_graph=True)
+        torch.cuda.synchronize()
+        mot = b.motions()
+        for i in range(16):
+            motions[i][t] = mot[i]
+            k = t - S.BATCH_OUT_LAG - 1 - W30 // 2
+            if k >= 0 and i in (0, 15):
+                outs[i][k] = b.output(i).cpu().numpy().copy()
+    assert b.sync() == 0
+    op = O.Params(max_corners=1000, levels=5, hypotheses=100, smooth_window=W30, rigid=False)
+    for i in (0, 15):
+        ref = O.run_clip(frames[i], op)
+        for t in range(1 + S.BATCH_LAG, T16):
+            tt = t - S.BATCH_LAG
+            m = np.array(motions[i][t]["m"], np.float64)
+            assert np.abs(m[2:] - ref["incs"][tt, 2:]).max() < 2e-4, (i, tt)
+            assert np.abs(m[:2] - ref["incs"][tt, :2]).max() < 0.05, (i, tt)
+        assert len(outs[i]) == T16 - S.BATCH_OUT_LAG - 1 - W30 // 2
+        for k, frame in outs[i].items():
+            d = np.abs(frame.astype(int) - ref["out"][k].astype(int))
+            assert (d > 1).mean() < 0.02 and d.mean() < 0.3, (i, k)
+    for i in range(16):
+        gt = clips[i]["incs"]
+        for t in range(1 + S.BATCH_LAG, T16):
+            tt = t - S.BATCH_LAG
+            g = motions[i][t]
+            m = np.array(g["m"], np.float64)
+            assert not g["flags"] & S.STAB_FLAG_SKIPPED and g["n_tracks"] > 300, (i, tt, g)
+            assert abs(m[2] - gt[tt, 2]) < 1e-3 and abs(m[3] - gt[tt, 3]) < 1e-3, (i, tt)
+            assert np.abs(m[:2] - gt[tt, :2]).max() < 0.1, (i, tt)
