@@ -101,6 +101,10 @@ __device__ __forceinline__ void rs_pixels(const uint8_t *__restrict__ g, int pit
 // buffer appends the warp's candidates directly).
 constexpr int RS_CAP = 256;
 
+// A compile-time slot index passed to the row step of k_response.
+template <int I>
+struct Slot { static constexpr int value = I; };
+
 // Corner response (Eq. 2), NMS and candidate list as barrier-free vertical
 // strips, each warp on its own: a warp owns a strip of 120 ROI columns and 32
 // rows (drawn from an atomic ticket when the work list has one), a thread
@@ -142,74 +146,84 @@ __global__ void __launch_bounds__(STAB_RS_THREADS, 4) k_response(const StreamDev
         const int nrows = min(STAB_RS_ROWS, ry1 - y0);
         const bool fast = x >= 4 && x + 8 <= w && ((x | pitch) & 3) == 0 && (reinterpret_cast<uintptr_t>(g) & 3) == 0;
         int wn = 0;   // candidates in the warp's buffer (the same in every lane)
-        // own columns x .. x+3; the scores also hold columns x-1 (index 0) and x+4 (5)
-        int d1[4] = {0}, d2[4] = {0}, s1[4] = {0}, s2[4] = {0};      // Sobel parts of pixel rows py-1, py-2
-        int ha1[4] = {0}, hb1[4] = {0}, hc1[4] = {0};                // tensor row sums of row py-2
-        int ha2[4] = {0}, hb2[4] = {0}, hc2[4] = {0};                // ... of row py-3
-        float l1[6] = {0.f}, l2[6] = {0.f};                          // scores of rows py-3, py-4
+        // Row windows of period 3, in slots rotated by the unrolled loop (no
+        // register moves): Sobel parts d, sm of pixel rows, tensor row sums ha, hb,
+        // hc, scores l (own columns x .. x+3; the scores also hold columns x-1
+        // (index 0) and x+4 (index 5)).
+        int d[3][4] = {}, sm[3][4] = {}, ha[3][4] = {}, hb[3][4] = {}, hc[3][4] = {};
+        float l[3][6] = {};
         unsigned lmax = 0;
+        const int nk = nrows + 6, nk3 = ((nk + 2) / 3) * 3;   // rows past nk emit nothing
         RsWords nxt = fast ? rs_words(g, pitch, h, x, y0 - 3) : RsWords{0u, 0u, 0u};
-        for (int k = 0; k < nrows + 6; ++k) {
+        // Row k: pixel row py = y0 - 3 + k enters in slot N (the rows before it are
+        // in slots P, then O).
+        auto row = [&](auto cn, auto cp, auto co, int k) {
+            constexpr int N = decltype(cn)::value, P = decltype(cp)::value, O = decltype(co)::value;
             const int py = y0 - 3 + k;
             const RsWords cur = nxt;
-            if (fast && k + 1 < nrows + 6) nxt = rs_words(g, pitch, h, x, py + 1);   // next row in flight
+            if (fast && k + 1 < nk3) nxt = rs_words(g, pitch, h, x, py + 1);   // next row in flight
             int p[6];
             rs_pixels(g, pitch, w, h, x, py, fast, cur, p);
-            int d0[4], s0[4];
 #pragma unroll
             for (int j = 0; j < 4; ++j) {
-                d0[j] = p[j + 2] - p[j];
-                s0[j] = p[j] + 2 * p[j + 1] + p[j + 2];
+                d[N][j] = p[j + 2] - p[j];
+                sm[N][j] = p[j] + 2 * p[j + 1] + p[j + 2];
             }
             // gx, gy of row py-1 at columns x .. x+3 (index 1 .. 4); the products of
-            // columns x-1 and x+4 come from the neighbouring lanes
-            int A[6], B[6], C[6];
+            // columns x-1 and x+4 come from the neighbouring lanes.  Only rows whose
+            // tensor sums reach a score that an NMS reads (k >= 2) are formed, and only
+            // scores that an NMS reads (rows k = 4 .. nk-1) are computed (k is the same
+            // in every lane).
+            if (k >= 2 && k < nk) {
+                int A[6], B[6], C[6];
 #pragma unroll
-            for (int j = 0; j < 4; ++j) {
-                const int gx = d2[j] + 2 * d1[j] + d0[j], gy = s0[j] - s2[j];
-                A[j + 1] = gx * gx; B[j + 1] = gx * gy; C[j + 1] = gy * gy;
-            }
-            A[0] = __shfl_up_sync(0xffffffffu, A[4], 1); A[5] = __shfl_down_sync(0xffffffffu, A[1], 1);
-            B[0] = __shfl_up_sync(0xffffffffu, B[4], 1); B[5] = __shfl_down_sync(0xffffffffu, B[1], 1);
-            C[0] = __shfl_up_sync(0xffffffffu, C[4], 1); C[5] = __shfl_down_sync(0xffffffffu, C[1], 1);
-            int ha0[4], hb0[4], hc0[4];
+                for (int j = 0; j < 4; ++j) {
+                    const int gx = d[O][j] + 2 * d[P][j] + d[N][j], gy = sm[N][j] - sm[O][j];
+                    A[j + 1] = gx * gx; B[j + 1] = gx * gy; C[j + 1] = gy * gy;
+                }
+                A[0] = __shfl_up_sync(0xffffffffu, A[4], 1); A[5] = __shfl_down_sync(0xffffffffu, A[1], 1);
+                B[0] = __shfl_up_sync(0xffffffffu, B[4], 1); B[5] = __shfl_down_sync(0xffffffffu, B[1], 1);
+                C[0] = __shfl_up_sync(0xffffffffu, C[4], 1); C[5] = __shfl_down_sync(0xffffffffu, C[1], 1);
 #pragma unroll
-            for (int i = 0; i < 4; ++i) {
-                ha0[i] = A[i] + A[i + 1] + A[i + 2];
-                hb0[i] = B[i] + B[i + 1] + B[i + 2];
-                hc0[i] = C[i] + C[i + 1] + C[i + 2];
+                for (int i = 0; i < 4; ++i) {
+                    ha[N][i] = A[i] + A[i + 1] + A[i + 2];
+                    hb[N][i] = B[i] + B[i + 1] + B[i + 2];
+                    hc[N][i] = C[i] + C[i + 1] + C[i + 2];
+                }
             }
             // score of row py-2 at columns x .. x+3, and of x-1, x+4 from the neighbours
-            float l0[6];
+            if (k >= 4 && k < nk) {
 #pragma unroll
-            for (int i = 0; i < 4; ++i)
-                l0[i + 1] = lambda32(ha2[i] + ha1[i] + ha0[i], hb2[i] + hb1[i] + hb0[i], hc2[i] + hc1[i] + hc0[i]);
-            l0[0] = __shfl_up_sync(0xffffffffu, l0[4], 1);
-            l0[5] = __shfl_down_sync(0xffffffffu, l0[1], 1);
-            // NMS of row py-3 (scores l2 = row py-4, l1 = py-3, l0 = py-2)
+                for (int i = 0; i < 4; ++i)
+                    l[N][i + 1] = lambda32(ha[O][i] + ha[P][i] + ha[N][i], hb[O][i] + hb[P][i] + hb[N][i],
+                                           hc[O][i] + hc[P][i] + hc[N][i]);
+                l[N][0] = __shfl_up_sync(0xffffffffu, l[N][4], 1);
+                l[N][5] = __shfl_down_sync(0xffffffffu, l[N][1], 1);
+            }
+            // NMS of row py-3 (scores l[O] = row py-4, l[P] = py-3, l[N] = py-2)
             unsigned long long keys[2];
-            int nk = 0;
+            int nk_ = 0;
             const int y = py - 3;
-            if (k >= 6) {
+            if (k >= 6 && k < nk) {
 #pragma unroll
                 for (int c = 0; c < 4; ++c) {
                     if (owner && x + c < rx1) {
-                        const float v = l1[c + 1];
+                        const float v = l[P][c + 1];
                         lmax = max(lmax, __float_as_uint(v));
                         // strict maximum over the 3x3 neighbourhood; a tie goes to the lower raster index
-                        bool keep = v > 0.0f && v > l2[c] && v > l2[c + 1] && v > l2[c + 2] && v > l1[c];
-                        keep = keep && v >= l1[c + 2] && v >= l0[c] && v >= l0[c + 1] && v >= l0[c + 2];
-                        if (keep && nk < 2) {
+                        bool keep = v > 0.0f && v > l[O][c] && v > l[O][c + 1] && v > l[O][c + 2] && v > l[P][c];
+                        keep = keep && v >= l[P][c + 2] && v >= l[N][c] && v >= l[N][c + 1] && v >= l[N][c + 2];
+                        if (keep && nk_ < 2) {
                             const unsigned idx = (unsigned)(y * w + x + c);
-                            keys[nk++] = ((unsigned long long)__float_as_uint(v) << 32) |
-                                         (unsigned long long)(0xFFFFFFFFu - idx);
+                            keys[nk_++] = ((unsigned long long)__float_as_uint(v) << 32) |
+                                          (unsigned long long)(0xFFFFFFFFu - idx);
                         }
                     }
                 }
             }
             // warp-aggregated append of this row's candidates to the warp's buffer
-            if (__any_sync(0xffffffffu, nk > 0)) {
-                int incl = nk;
+            if (__any_sync(0xffffffffu, nk_ > 0)) {
+                int incl = nk_;
                 for (int o = 1; o < 32; o <<= 1) {
                     const int v = __shfl_up_sync(0xffffffffu, incl, o);
                     if (lane >= o) incl += v;
@@ -223,8 +237,8 @@ __global__ void __launch_bounds__(STAB_RS_THREADS, 4) k_response(const StreamDev
                 } else {
                     wn += tot;
                 }
-                const int pos = base + incl - nk;
-                for (int q = 0; q < nk; ++q) {
+                const int pos = base + incl - nk_;
+                for (int q = 0; q < nk_; ++q) {
                     if (!full) wkeys[pos + q] = keys[q];
                     else {
                         if (pos + q < D.cand_cap) D.cand[pos + q] = keys[q];
@@ -233,15 +247,12 @@ __global__ void __launch_bounds__(STAB_RS_THREADS, 4) k_response(const StreamDev
                     }
                 }
             }
-            // shift the row windows
-#pragma unroll
-            for (int j = 0; j < 4; ++j) { d2[j] = d1[j]; d1[j] = d0[j]; s2[j] = s1[j]; s1[j] = s0[j]; }
-#pragma unroll
-            for (int i = 0; i < 4; ++i) {
-                ha2[i] = ha1[i]; ha1[i] = ha0[i]; hb2[i] = hb1[i]; hb1[i] = hb0[i]; hc2[i] = hc1[i]; hc1[i] = hc0[i];
-            }
-#pragma unroll
-            for (int i = 0; i < 6; ++i) { l2[i] = l1[i]; l1[i] = l0[i]; }
+        };
+#pragma unroll 1
+        for (int k = 0; k < nk3; k += 3) {
+            row(Slot<0>{}, Slot<2>{}, Slot<1>{}, k);
+            row(Slot<1>{}, Slot<0>{}, Slot<2>{}, k + 1);
+            row(Slot<2>{}, Slot<1>{}, Slot<0>{}, k + 2);
         }
         // the strip's max score and its buffered candidates go out with one atomic each
         for (int o = 16; o; o >>= 1) lmax = max(lmax, __shfl_xor_sync(0xffffffffu, lmax, o));
@@ -270,12 +281,24 @@ __global__ void __launch_bounds__(STAB_RS_THREADS, 4) k_response(const StreamDev
             const float thr = __fmul_rn(D.quality, __uint_as_float(lm));
             const unsigned thr_bits = __float_as_uint(thr), tbin = thr_bits >> STAB_HSHIFT;
             // lane i owns bins [4095 - 128 i - 127, 4095 - 128 i], highest first; the
-            // K-th key lies in the first bin (from the top) where the count reaches K
-            constexpr int BPL = STAB_HBINS / 32;
+            // K-th key lies in the first bin (from the top) where the count reaches K.
+            // A lane reads its bins as 16-byte vectors, eight vectors in flight at a
+            // time, so the cut costs a few L2 round trips rather than one per bin.
+            constexpr int BPL = STAB_HBINS / 32, VPL = BPL / 4, VB = 8;
+            const int lo = STAB_HBINS - BPL * (lane + 1);   // lowest bin of the lane, 16-byte aligned
+            const uint4 *hv = reinterpret_cast<const uint4 *>(D.hist + lo);
+            const int tb = (int)tbin;
             unsigned cnt = 0;
-            for (int j = 0; j < BPL; ++j) {
-                const unsigned b = STAB_HBINS - 1 - BPL * lane - j;
-                if (b >= tbin) cnt += __ldcg(&D.hist[b]);
+            for (int v0 = 0; v0 < VPL; v0 += VB) {
+                uint4 q[VB];
+#pragma unroll
+                for (int v = 0; v < VB; ++v) q[v] = __ldcg(hv + v0 + v);
+#pragma unroll
+                for (int v = 0; v < VB; ++v) {
+                    const int b = lo + 4 * (v0 + v);   // bins b .. b+3
+                    cnt += (b >= tb ? q[v].x : 0u) + (b + 1 >= tb ? q[v].y : 0u) + (b + 2 >= tb ? q[v].z : 0u) +
+                           (b + 3 >= tb ? q[v].w : 0u);
+                }
             }
             unsigned incl = cnt;
             for (int o = 1; o < 32; o <<= 1) {
@@ -284,13 +307,25 @@ __global__ void __launch_bounds__(STAB_RS_THREADS, 4) k_response(const StreamDev
             }
             const unsigned K = (unsigned)D.K, excl = incl - cnt;
             unsigned bin = tbin;
-            if (excl < K && K <= incl) {   // at most one lane
+            if (excl < K && K <= incl) {   // at most one lane: walk its bins from the top
                 unsigned cum = excl;
-                for (int j = 0; j < BPL; ++j) {
-                    const unsigned b = STAB_HBINS - 1 - BPL * lane - j;
-                    if (b < tbin) break;
-                    cum += __ldcg(&D.hist[b]);
-                    if (cum >= K) { bin = b; break; }
+                bool found = false;
+                for (int v0 = VPL - VB; v0 >= 0 && !found; v0 -= VB) {
+                    uint4 q[VB];
+#pragma unroll
+                    for (int v = 0; v < VB; ++v) q[v] = __ldcg(hv + v0 + v);
+#pragma unroll
+                    for (int v = VB - 1; v >= 0; --v) {
+                        const int b = lo + 4 * (v0 + v);
+                        const unsigned c4[4] = {q[v].x, q[v].y, q[v].z, q[v].w};
+#pragma unroll
+                        for (int e = 3; e >= 0; --e) {
+                            if (!found && b + e >= tb) {
+                                cum += c4[e];
+                                if (cum >= K) { bin = (unsigned)(b + e); found = true; }
+                            }
+                        }
+                    }
                 }
             }
             const unsigned who = __ballot_sync(0xffffffffu, excl < K && K <= incl);

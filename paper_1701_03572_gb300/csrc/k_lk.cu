@@ -109,6 +109,49 @@ __device__ __forceinline__ int stage(const E *__restrict__ P, int pitch, int wl,
     return 0;
 }
 
+// The same staging for a PW x PW patch of compile-time size (the fixed-radius
+// trackers), cheaper to issue: when the patch's columns lie inside the row,
+// every row is copied as NV = (PW + 6) / 4 aligned vectors (covering any
+// start offset; the extra vector lies inside the row pitch and is not read),
+// lane tig owns vector tig % NV of rows tig / NV, + NT / NV, ... (all index
+// arithmetic by constants), and a row outside the plane is replaced by the
+// nearest border row (the replicated border).  Otherwise every tap is clamped
+// and copied singly, offset 0.
+template <typename E, int NT, int PW, int SW>
+__device__ __forceinline__ int stage_k(const E *__restrict__ P, int pitch, int wl, int hl, int x0, int y0, E *dst,
+                                       int tig)
+{
+    constexpr int NV = (PW + 6) / 4, RPP = NT / NV, NPASS = (PW + RPP - 1) / RPP;
+    static_assert(4 * NV <= SW && RPP >= 1, "a staged row fits the stride");
+    const int x0a = x0 & ~3;
+    if (x0 >= 0 && x0 + PW <= wl && x0a + 4 * NV <= pitch) {
+        const int v = tig % NV, r0 = tig / NV;
+        if (r0 < RPP) {
+            const E *src = P + x0a + 4 * v;
+            E *d = dst + 4 * v;
+            const bool rows_in = y0 >= 0 && y0 + PW <= hl;
+#pragma unroll
+            for (int i = 0; i < NPASS; ++i) {
+                const int r = r0 + RPP * i;
+                if (r < PW) {
+                    const int yy = rows_in ? y0 + r : clampi(y0 + r, 0, hl - 1);
+                    cpa_vec4(d + r * SW, src + (size_t)yy * pitch);
+                }
+            }
+        }
+        return x0 - x0a;
+    }
+    constexpr int n = PW * PW, q = NT / PW, rr = NT - q * PW;
+    int row = tig / PW, col = tig - row * PW;
+    for (int e = tig; e < n; e += NT) {
+        const int xx = clampi(x0 + col, 0, wl - 1), yy = clampi(y0 + row, 0, hl - 1);
+        dst[row * SW + col] = P[(size_t)yy * pitch + xx];
+        col += rr; row += q;
+        if (col >= PW) { col -= PW; ++row; }
+    }
+    return 0;
+}
+
 // Margin (px) of the next frame's staged patch: iterations whose window stays
 // within it sample shared memory only; a larger move re-stages the patch.
 constexpr int LK_MARGIN = 2;
@@ -202,9 +245,17 @@ __device__ __noinline__ bool lk_track(const StreamDev &D, int sa, int sb, float 
         int jy0 = (int)floorf(fminf(fmaxf(py + gy, -64.f), (float)hl + 64.f)) - r - LK_MARGIN;
         bool jin = jx0 >= 0 && jx0 + pj - 1 <= wl - 1 && jy0 >= 0 && jy0 + pj - 1 <= hl - 1;
         group_sync<WPF>(grp);
-        const int offI = stage<PT, NT>(Ia, p, wl, hl, ix, iy, pw, swI, inside, sI, tig);
-        stage<PT2, NT>(Ga, p, wl, hl, ix, iy, pw, swI, inside, sG, tig);
-        int offJ = stage<PT, NT>(Jb, p, wl, hl, jx0, jy0, pj, swJ, jin, sJ, tig);
+        int offI, offJ;
+        if constexpr (RC > 0) {
+            constexpr int PWc = 2 * RC + 2, PJc = PWc + 2 * LK_MARGIN, SWI = lk_sw(PWc), SWJ = lk_sw(PJc);
+            offI = stage_k<PT, NT, PWc, SWI>(Ia, p, wl, hl, ix, iy, sI, tig);
+            stage_k<PT2, NT, PWc, SWI>(Ga, p, wl, hl, ix, iy, sG, tig);
+            offJ = stage_k<PT, NT, PJc, SWJ>(Jb, p, wl, hl, jx0, jy0, sJ, tig);
+        } else {
+            offI = stage<PT, NT>(Ia, p, wl, hl, ix, iy, pw, swI, inside, sI, tig);
+            stage<PT2, NT>(Ga, p, wl, hl, ix, iy, pw, swI, inside, sG, tig);
+            offJ = stage<PT, NT>(Jb, p, wl, hl, jx0, jy0, pj, swJ, jin, sJ, tig);
+        }
         cpa_wait_all();
         group_sync<WPF>(grp);
         float gxx = 0.f, gxy = 0.f, gyy = 0.f;
@@ -296,7 +347,12 @@ __device__ __noinline__ bool lk_track(const StreamDev &D, int sa, int sb, float 
                 jy0 = jy - LK_MARGIN;
                 jin = jx0 >= 0 && jx0 + pj - 1 <= wl - 1 && jy0 >= 0 && jy0 + pj - 1 <= hl - 1;
                 group_sync<WPF>(grp);
-                offJ = stage<PT, NT>(Jb, p, wl, hl, jx0, jy0, pj, swJ, jin, sJ, tig);
+                if constexpr (RC > 0) {
+                    constexpr int PJc = 2 * RC + 2 + 2 * LK_MARGIN, SWJ = lk_sw(PJc);
+                    offJ = stage_k<PT, NT, PJc, SWJ>(Jb, p, wl, hl, jx0, jy0, sJ, tig);
+                } else {
+                    offJ = stage<PT, NT>(Jb, p, wl, hl, jx0, jy0, pj, swJ, jin, sJ, tig);
+                }
                 cpa_wait_all();
                 group_sync<WPF>(grp);
                 ox = LK_MARGIN;
@@ -519,16 +575,14 @@ __device__ __noinline__ bool lk_track2(const StreamDev &D, int sa, int sb, bool 
         const float fx = floorf(bx), fy = floorf(by);
         const float ax = bx - fx, ay = by - fy;
         const int ix = (int)fx - 10, iy = (int)fy - 10;
-        const bool inside = ix >= 0 && ix + ww <= wl - 1 && iy >= 0 && iy + ww <= hlv - 1;
         int jx0 = (int)floorf(fminf(fmaxf(px + gx, -64.f), (float)wl + 64.f)) - 10 - LK_MARGIN;
         int jy0 = (int)floorf(fminf(fmaxf(py + gy, -64.f), (float)hlv + 64.f)) - 10 - LK_MARGIN;
-        bool jin = jx0 >= 0 && jx0 + pj - 1 <= wl - 1 && jy0 >= 0 && jy0 + pj - 1 <= hlv - 1;
         __syncwarp();
         int offI = 0, offJ = 0;
         if (on) {
-            offI = stage<PT, NT>(Ia, p, wl, hlv, ix, iy, pw, swI, inside, sI, hl);
-            stage<PT2, NT>(Ga, p, wl, hlv, ix, iy, pw, swI, inside, sG, hl);
-            offJ = stage<PT, NT>(Jb, p, wl, hlv, jx0, jy0, pj, swJ, jin, sJ, hl);
+            offI = stage_k<PT, NT, pw, swI>(Ia, p, wl, hlv, ix, iy, sI, hl);
+            stage_k<PT2, NT, pw, swI>(Ga, p, wl, hlv, ix, iy, sG, hl);
+            offJ = stage_k<PT, NT, pj, swJ>(Jb, p, wl, hlv, jx0, jy0, sJ, hl);
         }
         cpa_wait_all();
         __syncwarp();
@@ -593,8 +647,7 @@ __device__ __noinline__ bool lk_track2(const StreamDev &D, int sa, int sb, bool 
                 if (need) {
                     jx0 = jx - LK_MARGIN;
                     jy0 = jy - LK_MARGIN;
-                    jin = jx0 >= 0 && jx0 + pj - 1 <= wl - 1 && jy0 >= 0 && jy0 + pj - 1 <= hlv - 1;
-                    offJ = stage<PT, NT>(Jb, p, wl, hlv, jx0, jy0, pj, swJ, jin, sJ, hl);
+                    offJ = stage_k<PT, NT, pj, swJ>(Jb, p, wl, hlv, jx0, jy0, sJ, hl);
                 }
                 cpa_wait_all();
                 __syncwarp();
