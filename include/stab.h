@@ -311,14 +311,16 @@ stab_status stab_batch_autotune(stab_batch *b, const char *cache_path, int *vari
  * latched-error path.  Synchronous: waits for the context's last stream. */
 stab_status stab_set_candidate_capacity(stab_ctx *ctx, int cap);
 stab_status stab_batch_set_candidate_capacity(stab_batch *b, int cap);
-/* Force a tracker variant (0..6) for a batch or a single-stream context:
+/* Force a tracker variant (0..8) for a batch or a single-stream context:
  * 0 / 1: one warp per feature, template in registers, register budgets of
  * 128 / 168; 2 / 3: two warps per feature, budgets of 80 / 128; 4: one warp
  * per feature, template in shared memory, budget of 96 (more resident warps);
- * 5 / 6: two features per warp (a half-warp each), budgets of 255 / 168.
- * Variants 0, 1 and 4 give identical results; the others sum the window in
- * another order (FP32 rounding differences only).  Variants other than 0 serve
- * the 21 x 21 window; other windows run variant 0. */
+ * 5 / 6: two features per warp (a half-warp each), budgets of 255 / 168;
+ * 7 / 8: as 0 / 1, with patches inside their pyramid level copied by tensor
+ * (TMA) copies.  Variants 0, 1, 4, 7 and 8 give identical results; the others
+ * sum the window in another order (FP32 rounding differences only).
+ * Variants other than 0 serve the 21 x 21 window; other windows run
+ * variant 0. */
 stab_status stab_batch_set_lk_variant(stab_batch *b, int variant);
 stab_status stab_set_lk_variant(stab_ctx *ctx, int variant);
 /* Number of tracker variants (the size stab_batch_autotune's ms_out must have). */

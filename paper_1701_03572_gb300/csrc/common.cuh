@@ -84,6 +84,10 @@ struct StreamDev {
     uint8_t *u8[STAB_PSLOTS][STAB_MAXL];
     void *pI[STAB_PSLOTS][STAB_MAXL];   // float or __half
     void *pG[STAB_PSLOTS][STAB_MAXL];   // float2 or __half2
+    // tracker tensor maps (device memory, 128 bytes each): [slot][level][k],
+    // k = 0 template I box, 1 template (Ix, Iy) box, 2 next-frame I box; null
+    // when the stream's window radius has no map geometry
+    const void *tmap;
     // features and tracks
     float2 *feat;
     float2 *fwd, *back;

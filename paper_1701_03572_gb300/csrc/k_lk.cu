@@ -15,6 +15,11 @@
 // accumulates b = sum e [Tx, Ty] and solves the 2x2 system.  Sums are reduced with xor-butterfly shuffles (same
 // bits in every lane) and, for two warps, combined through shared memory in a
 // fixed order, so every thread of the group takes the same branch.
+#include <cuda.h>   // CUtensorMap and the types of its encoding call (no driver library is linked)
+
+#include <cstring>
+#include <vector>
+
 #include "kernels.cuh"
 
 namespace {
@@ -62,6 +67,59 @@ __device__ __forceinline__ void cpa(void *sdst, const void *gsrc)
     else asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(d), "l"(gsrc) : "memory");
 }
 __device__ __forceinline__ void cpa_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
+
+// Tensor-memory-access (TMA) staging of the fixed 21 x 21 window's patches.
+// A patch lying inside its level is copied by three 2-D tensor copies (the
+// template's I and (Ix, Iy) boxes, the next frame's I box) that one lane
+// issues, completing on the group's mbarrier; shared rows are the boxes' rows.
+// Box columns start at the patch's first column rounded down to 16 bytes
+// (the copy's coordinate rule), so a box is A - 1 columns wider than the patch.
+template <typename PT>
+struct LkTma {
+    static constexpr int ES = (int)sizeof(PT), A = 16 / ES;   // column alignment of a box start, elements
+    static constexpr int PW = 22, PJ = 26;                     // template and next-frame patch sides
+    static constexpr int BWI = (PW + 2 * A - 2) / A * A, BWJ = (PJ + 2 * A - 2) / A * A;
+    static constexpr unsigned TX_I = PW * BWI * ES, TX_G = PW * BWI * 2 * ES, TX_J = PJ * BWJ * ES;
+    static constexpr int al128(unsigned b) { return (int)((b + 127) / 128 * 128); }
+    static constexpr int OFF_G = al128(TX_I), OFF_J = OFF_G + al128(TX_G), OFF_RED = OFF_J + al128(TX_J);
+    static constexpr int GROUP = OFF_RED + 128;   // 32 reduction bytes, the mbarrier at +64
+    static_assert(BWI * ES % 16 == 0 && BWJ * ES % 16 == 0 && BWI >= PW + A - 1 && BWJ >= PJ + A - 1, "box geometry");
+};
+
+__device__ __forceinline__ unsigned smem_u32(const void *p) { return (unsigned)__cvta_generic_to_shared(p); }
+__device__ __forceinline__ void mbar_init(unsigned long long *mb)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(smem_u32(mb)) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(unsigned long long *mb, unsigned bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(smem_u32(mb)), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ void tma_load_2d(void *dst, const void *map, int x, int y, unsigned long long *mb)
+{
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];\n" ::"r"(
+            smem_u32(dst)),
+        "l"(map), "r"(x), "r"(y), "r"(smem_u32(mb))
+        : "memory");
+}
+// Generic-proxy reads of a buffer are ordered before the tensor copies that refill it.
+__device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory"); }
+// Wait for the mbarrier phase `ph` to complete, giving up after about a second
+// of polling (each try_wait suspends briefly); false if it gave up.
+__device__ __forceinline__ bool mbar_wait(unsigned long long *mb, unsigned ph)
+{
+    for (int i = 0; i < (1 << 20); ++i) {
+        unsigned ok;
+        asm volatile(
+            "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+            : "=r"(ok)
+            : "r"(smem_u32(mb)), "r"(ph)
+            : "memory");
+        if (ok) return true;
+    }
+    return false;
+}
 
 // 4 consecutive plane elements (one staged vector) by asynchronous copy.
 __device__ __forceinline__ void cpa_vec4(float *d, const float *g) { cpa<16>(d, g); }
@@ -176,16 +234,22 @@ __device__ __forceinline__ float lerpf(float a, float b, float f) { return fmaf(
 // lets more warps reside; otherwise sT is unused.
 // Not inlined: the kernel calls it for the forward and the backward track, and
 // one copy of its unrolled body keeps the instruction working set small.
-template <typename PT, int NS, int RC, int WPF, bool TS>
+// TM: patches lying inside their level are copied by tensor copies (LkTma),
+// the rest by stage_k into the same layout; mb / ph: the group's mbarrier and
+// its phase.
+template <typename PT, int NS, int RC, int WPF, bool TS, bool TM>
 __device__ __noinline__ bool lk_track(const StreamDev &D, int sa, int sb, float ux, float uy, float &vx, float &vy, int &iters,
-                         int &tpl, PT *sI, typename Plane2<PT>::type *sG, PT *sJ, float *red, fx2 *sT, int tig, int grp)
+                         int &tpl, PT *sI, typename Plane2<PT>::type *sG, PT *sJ, float *red, fx2 *sT,
+                         unsigned long long *mb, unsigned &ph, int tig, int grp)
 {
+    static_assert(!TM || (RC == 10 && WPF == 1 && !TS), "tensor-copy staging serves the 21 x 21 window, one warp");
+    typedef LkTma<PT> TG;
     typedef typename Plane2<PT>::type PT2;
     constexpr int NT = 32 * WPF;
     const int wig = tig >> 5;
     const int r = RC ? RC : D.r, ww = 2 * r + 1, pw = ww + 1, N = ww * ww;
     const int pj = pw + 2 * LK_MARGIN;
-    const int swI = lk_sw(pw), swJ = lk_sw(pj);
+    const int swI = TM ? TG::BWI : lk_sw(pw), swJ = TM ? TG::BWJ : lk_sw(pj);
     constexpr int SEG = lk_seg(NS), Q = NS / SEG;
     // EXACT: segments tile the window's rows exactly, so every row a segment
     // reads (its SEG + 1 rows) lies in the patch and needs no clamp; a thread
@@ -246,7 +310,31 @@ __device__ __noinline__ bool lk_track(const StreamDev &D, int sa, int sb, float 
         bool jin = jx0 >= 0 && jx0 + pj - 1 <= wl - 1 && jy0 >= 0 && jy0 + pj - 1 <= hl - 1;
         group_sync<WPF>(grp);
         int offI, offJ;
-        if constexpr (RC > 0) {
+        if constexpr (TM) {
+            const unsigned char *maps = static_cast<const unsigned char *>(D.tmap);
+            const bool tin = maps && ix >= 0 && ix + TG::PW <= wl && iy >= 0 && iy + TG::PW <= hl && jx0 >= 0 &&
+                             jx0 + TG::PJ <= wl && jy0 >= 0 && jy0 + TG::PJ <= hl;
+            if (tin) {
+                const int xa = ix & ~(TG::A - 1), jxa = jx0 & ~(TG::A - 1);
+                offI = ix - xa;
+                offJ = jx0 - jxa;
+                if (tig == 0) {
+                    const unsigned char *mt = maps + (size_t)((sa * STAB_MAXL + l) * 3) * 128;
+                    const unsigned char *mj = maps + (size_t)((sb * STAB_MAXL + l) * 3 + 2) * 128;
+                    fence_proxy_async();
+                    mbar_expect_tx(mb, TG::TX_I + TG::TX_G + TG::TX_J);
+                    tma_load_2d(sI, mt, xa, iy, mb);
+                    tma_load_2d(sG, mt + 128, xa, iy, mb);
+                    tma_load_2d(sJ, mj, jxa, jy0, mb);
+                }
+                if (!mbar_wait(mb, ph)) set_err(D.st, STAB_ERR_TIMEOUT);
+                ph ^= 1u;
+            } else {
+                offI = stage_k<PT, NT, TG::PW, TG::BWI>(Ia, p, wl, hl, ix, iy, sI, tig);
+                stage_k<PT2, NT, TG::PW, TG::BWI>(Ga, p, wl, hl, ix, iy, sG, tig);
+                offJ = stage_k<PT, NT, TG::PJ, TG::BWJ>(Jb, p, wl, hl, jx0, jy0, sJ, tig);
+            }
+        } else if constexpr (RC > 0) {
             constexpr int PWc = 2 * RC + 2, PJc = PWc + 2 * LK_MARGIN, SWI = lk_sw(PWc), SWJ = lk_sw(PJc);
             offI = stage_k<PT, NT, PWc, SWI>(Ia, p, wl, hl, ix, iy, sI, tig);
             stage_k<PT2, NT, PWc, SWI>(Ga, p, wl, hl, ix, iy, sG, tig);
@@ -347,7 +435,22 @@ __device__ __noinline__ bool lk_track(const StreamDev &D, int sa, int sb, float 
                 jy0 = jy - LK_MARGIN;
                 jin = jx0 >= 0 && jx0 + pj - 1 <= wl - 1 && jy0 >= 0 && jy0 + pj - 1 <= hl - 1;
                 group_sync<WPF>(grp);
-                if constexpr (RC > 0) {
+                if constexpr (TM) {
+                    const unsigned char *maps = static_cast<const unsigned char *>(D.tmap);
+                    if (maps && jx0 >= 0 && jx0 + TG::PJ <= wl && jy0 >= 0 && jy0 + TG::PJ <= hl) {
+                        const int jxa = jx0 & ~(TG::A - 1);
+                        offJ = jx0 - jxa;
+                        if (tig == 0) {
+                            fence_proxy_async();
+                            mbar_expect_tx(mb, TG::TX_J);
+                            tma_load_2d(sJ, maps + (size_t)((sb * STAB_MAXL + l) * 3 + 2) * 128, jxa, jy0, mb);
+                        }
+                        if (!mbar_wait(mb, ph)) set_err(D.st, STAB_ERR_TIMEOUT);
+                        ph ^= 1u;
+                    } else {
+                        offJ = stage_k<PT, NT, TG::PJ, TG::BWJ>(Jb, p, wl, hl, jx0, jy0, sJ, tig);
+                    }
+                } else if constexpr (RC > 0) {
                     constexpr int PJc = 2 * RC + 2 + 2 * LK_MARGIN, SWJ = lk_sw(PJc);
                     offJ = stage_k<PT, NT, PJc, SWJ>(Jb, p, wl, hl, jx0, jy0, sJ, tig);
                 } else {
@@ -434,21 +537,41 @@ __host__ __device__ constexpr int lk_group_bytes(int r, int es, int tbytes = 0)
     return 3 * lk_bytes_I(r, es) + lk_bytes_J(r, es) + 32 + tbytes;
 }
 
-template <typename PT, int NS, int RC, int WPF, int MINB, bool TS>
+template <typename PT, int NS, int RC, int WPF, int MINB, bool TS, bool TM>
 __global__ void __launch_bounds__(128, MINB) k_lk(const StreamDev *__restrict__ S, WorkList wl, LkIO io, int rmax)
 {
     typedef typename Plane2<PT>::type PT2;
-    extern __shared__ __align__(16) unsigned char lk_smem[];
+    extern __shared__ __align__(128) unsigned char lk_smem[];
     constexpr int NT = 32 * WPF, ES = (int)sizeof(PT), TB = TS ? lk_bytes_T(NS) : 0;
     const int grp = threadIdx.x / NT, tig = threadIdx.x - grp * NT;
-    unsigned char *base = lk_smem + grp * lk_group_bytes(rmax, ES, TB);
-    // regions sized for rmax; a stream with a smaller radius uses a prefix
-    const int bI = lk_bytes_I(rmax, ES);
-    PT *sI = reinterpret_cast<PT *>(base);
-    PT2 *sG = reinterpret_cast<PT2 *>(base + bI);
-    PT *sJ = reinterpret_cast<PT *>(base + 3 * bI);
-    float *red = reinterpret_cast<float *>(base + 3 * bI + lk_bytes_J(rmax, ES));
-    fx2 *sT = reinterpret_cast<fx2 *>(base + 3 * bI + lk_bytes_J(rmax, ES) + 32);
+    PT *sI;
+    PT2 *sG;
+    PT *sJ;
+    float *red;
+    fx2 *sT = nullptr;
+    unsigned long long *mb = nullptr;
+    unsigned ph = 0;
+    if constexpr (TM) {   // 128-byte aligned boxes (LkTma)
+        unsigned char *base = lk_smem + grp * LkTma<PT>::GROUP;
+        sI = reinterpret_cast<PT *>(base);
+        sG = reinterpret_cast<PT2 *>(base + LkTma<PT>::OFF_G);
+        sJ = reinterpret_cast<PT *>(base + LkTma<PT>::OFF_J);
+        red = reinterpret_cast<float *>(base + LkTma<PT>::OFF_RED);
+        mb = reinterpret_cast<unsigned long long *>(base + LkTma<PT>::OFF_RED + 64);
+        if (tig == 0) mbar_init(mb);
+        asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+        fence_proxy_async();
+        group_sync<WPF>(grp);
+    } else {
+        unsigned char *base = lk_smem + grp * lk_group_bytes(rmax, ES, TB);
+        // regions sized for rmax; a stream with a smaller radius uses a prefix
+        const int bI = lk_bytes_I(rmax, ES);
+        sI = reinterpret_cast<PT *>(base);
+        sG = reinterpret_cast<PT2 *>(base + bI);
+        sJ = reinterpret_cast<PT *>(base + 3 * bI);
+        red = reinterpret_cast<float *>(base + 3 * bI + lk_bytes_J(rmax, ES));
+        sT = reinterpret_cast<fx2 *>(base + 3 * bI + lk_bytes_J(rmax, ES) + 32);
+    }
     const int ngroups = (gridDim.x * blockDim.x) / NT;
     // The group's next item: a fixed stride, or with a ticket list the ticket
     // thread 0 of the group drew (tk), broadcast to the group.
@@ -482,11 +605,11 @@ __global__ void __launch_bounds__(128, MINB) k_lk(const StreamDev *__restrict__ 
         const float2 u = pts[f];
         int iters = 0, tpl = 0;
         float vx, vy, bx = u.x, by = u.y;
-        const bool ok1 = lk_track<PT, NS, RC, WPF, TS>(D, sp, sn, u.x, u.y, vx, vy, iters, tpl, sI, sG, sJ, red,
-                                                       sT, tig, grp);
+        const bool ok1 = lk_track<PT, NS, RC, WPF, TS, TM>(D, sp, sn, u.x, u.y, vx, vy, iters, tpl, sI, sG, sJ,
+                                                           red, sT, mb, ph, tig, grp);
         bool ok2 = false;
-        if (ok1) ok2 = lk_track<PT, NS, RC, WPF, TS>(D, sn, sp, vx, vy, bx, by, iters, tpl, sI, sG, sJ, red, sT,
-                                                     tig, grp);
+        if (ok1) ok2 = lk_track<PT, NS, RC, WPF, TS, TM>(D, sn, sp, vx, vy, bx, by, iters, tpl, sI, sG, sJ, red, sT,
+                                                         mb, ph, tig, grp);
         if (!ok1) { bx = u.x; by = u.y; }
         const float ex = bx - u.x, ey = by - u.y;
         const float e2 = ex * ex + ey * ey;
@@ -703,7 +826,7 @@ template <typename PT, int MINB>
 __global__ void __launch_bounds__(128, MINB) k_lk2(const StreamDev *__restrict__ S, WorkList wl, LkIO io)
 {
     typedef typename Plane2<PT>::type PT2;
-    extern __shared__ __align__(16) unsigned char lk_smem[];
+    extern __shared__ __align__(128) unsigned char lk_smem[];
     constexpr int ES = (int)sizeof(PT);
     const int grp = threadIdx.x >> 4, hl = threadIdx.x & 15;
     unsigned char *base = lk_smem + grp * lk_group_bytes(10, ES);
@@ -784,10 +907,11 @@ struct Lk2Kernel {
     }
 };
 
-template <typename PT, int NS, int RC, int WPF, int MINB, bool TS = false>
+template <typename PT, int NS, int RC, int WPF, int MINB, bool TS = false, bool TM = false>
 struct LkKernel {
     static int smem(int rmax)
     {
+        if (TM) return (128 / (32 * WPF)) * LkTma<PT>::GROUP;
         return (128 / (32 * WPF)) * lk_group_bytes(rmax, (int)sizeof(PT), TS ? lk_bytes_T(NS) : 0);
     }
     // sets the kernel's shared-memory attribute and queries its occupancy, once
@@ -797,8 +921,9 @@ struct LkKernel {
         static DevCache c[STAB_MAXR + 1];
         return c[rmax].get([rmax] {
             int v = 0;
-            cudaFuncSetAttribute(k_lk<PT, NS, RC, WPF, MINB, TS>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem(rmax));
-            if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, k_lk<PT, NS, RC, WPF, MINB, TS>, 128, smem(rmax)) !=
+            cudaFuncSetAttribute(k_lk<PT, NS, RC, WPF, MINB, TS, TM>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 smem(rmax));
+            if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, k_lk<PT, NS, RC, WPF, MINB, TS, TM>, 128, smem(rmax)) !=
                     cudaSuccess ||
                 v < 1)
                 v = 1;
@@ -809,7 +934,8 @@ struct LkKernel {
     {
         const int groups_per_block = 128 / (32 * WPF);
         const int blocks = (wl.total + groups_per_block - 1) / groups_per_block;
-        k_lk<PT, NS, RC, WPF, MINB, TS><<<grid_for(L, blocks, occ(rmax)), 128, smem(rmax), L.stream>>>(S, wl, io, rmax);
+        k_lk<PT, NS, RC, WPF, MINB, TS, TM><<<grid_for(L, blocks, occ(rmax)), 128, smem(rmax), L.stream>>>(S, wl, io,
+                                                                                                      rmax);
     }
 };
 
@@ -822,6 +948,7 @@ struct LkKernel {
 //      (5 blocks / SM with FP16 planes: 10.5 KB of shared memory per warp)
 //   5, 6: two features per warp (a half-warp each), <= 255 / 168 registers
 //      (2 / 3 blocks of 4 warps per SM)
+//   7, 8: as 0 / 1, patches inside their level staged by tensor copies
 // Other radii use the runtime-radius build of variant 0.
 // rcode: the window radius shared by every stream, or minus the largest
 // radius when streams differ (then the runtime-radius build, sized for it).
@@ -836,6 +963,8 @@ void run_variant(int v, const Launch &L, const StreamDev *S, WorkList wl, LkIO i
         case 4: LkKernel<PT, 14, 10, 1, 5, true>::run(L, S, wl, io, 10); return;
         case 5: Lk2Kernel<PT, 2>::run(L, S, wl, io); return;
         case 6: Lk2Kernel<PT, 3>::run(L, S, wl, io); return;
+        case 7: LkKernel<PT, 14, 10, 1, 4, false, true>::run(L, S, wl, io, 10); return;
+        case 8: LkKernel<PT, 14, 10, 1, 3, false, true>::run(L, S, wl, io, 10); return;
         default: LkKernel<PT, 14, 10, 1, 4>::run(L, S, wl, io, 10); return;
         }
     }
@@ -853,6 +982,7 @@ void warm_all()
             LkKernel<PT, 7, 10, 2, 6>::occ(r); LkKernel<PT, 7, 10, 2, 4>::occ(r);
             LkKernel<PT, 14, 10, 1, 5, true>::occ(r);
             Lk2Kernel<PT, 2>::occ(); Lk2Kernel<PT, 3>::occ();
+            LkKernel<PT, 14, 10, 1, 4, false, true>::occ(r); LkKernel<PT, 14, 10, 1, 3, false, true>::occ(r);
             LkKernel<PT, 14, 0, 1, 4>::occ(r);
         } else if (r < 10) {
             LkKernel<PT, 14, 0, 1, 4>::occ(r);
@@ -864,7 +994,53 @@ void warm_all()
 
 }  // namespace
 
-int lk_variants() { return 7; }
+int lk_variants() { return 9; }
+
+// Tensor maps of one stream's tracker planes: for every pyramid slot and
+// level, the template's I box (BWI x 22), its (Ix, Iy) box (BWI x 22) and the
+// next frame's I box (BWJ x 26), each over the level's w x h plane with its
+// pitch; columns past w read zero (never sampled).
+int lk_tensor_maps(const StreamDev &D, int prec, void *host_out)
+{
+    typedef CUresult (*EncodeFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
+                                 const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
+                                 CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+    static EncodeFn encode = [] {
+        void *f = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000, cudaEnableDefault, &q) != cudaSuccess ||
+            q != cudaDriverEntryPointSuccess)
+            f = nullptr;
+        return reinterpret_cast<EncodeFn>(f);
+    }();
+    if (!encode) return -1;
+    const int es = prec ? 2 : 4;
+    const int bwi = prec ? LkTma<__half>::BWI : LkTma<float>::BWI, bwj = prec ? LkTma<__half>::BWJ : LkTma<float>::BWJ;
+    const CUtensorMapDataType ti = prec ? CU_TENSOR_MAP_DATA_TYPE_UINT16 : CU_TENSOR_MAP_DATA_TYPE_UINT32;
+    const CUtensorMapDataType tg = prec ? CU_TENSOR_MAP_DATA_TYPE_UINT32 : CU_TENSOR_MAP_DATA_TYPE_UINT64;
+    std::vector<CUtensorMap> maps(STAB_PSLOTS * STAB_MAXL * 3);
+    std::memset(maps.data(), 0, maps.size() * sizeof(CUtensorMap));
+    static_assert(sizeof(CUtensorMap) == 128, "tensor map size");
+    const cuuint32_t one[2] = {1, 1};
+    for (int s = 0; s < STAB_PSLOTS; ++s)
+        for (int l = 0; l < D.L; ++l) {
+            const cuuint64_t dim[2] = {(cuuint64_t)D.lw[l], (cuuint64_t)D.lh[l]};
+            const cuuint64_t si[1] = {(cuuint64_t)D.lp[l] * es}, sg[1] = {(cuuint64_t)D.lp[l] * 2 * es};
+            const cuuint32_t bi[2] = {(cuuint32_t)bwi, 22}, bj[2] = {(cuuint32_t)bwj, 26};
+            CUtensorMap *m = &maps[(s * STAB_MAXL + l) * 3];
+            if (encode(m, ti, 2, D.pI[s][l], dim, si, bi, one, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                       CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS ||
+                encode(m + 1, tg, 2, D.pG[s][l], dim, sg, bi, one, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                       CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                       CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS ||
+                encode(m + 2, ti, 2, D.pI[s][l], dim, si, bj, one, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                       CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                       CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+                return -1;
+        }
+    std::memcpy(host_out, maps.data(), maps.size() * sizeof(CUtensorMap));
+    return 0;
+}
 
 void warm_lk()
 {

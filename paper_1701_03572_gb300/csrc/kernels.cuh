@@ -129,6 +129,11 @@ void launch_select(const Launch &L, const StreamDev *S, int n, DetIO io);
 
 // Tracker variants (warps per feature, register budget); see k_lk.cu.
 int lk_variants();
+// Bytes of a stream's tracker tensor maps, and their encoding on the host
+// (kLkMapBytes bytes at host_out); returns 0, or -1 if the driver cannot
+// encode them.  Only streams with the 21 x 21 window have maps.
+constexpr int kLkMapBytes = STAB_PSLOTS * STAB_MAXL * 3 * 128;
+int lk_tensor_maps(const StreamDev &D, int prec, void *host_out);
 // rcode: the window radius of every stream, or minus the largest when they differ.
 void launch_lk(const Launch &L, int prec, int rcode, int variant, const StreamDev *S, WorkList wl, LkIO io);
 

@@ -180,6 +180,7 @@ stab_status build(Pipeline &pp, int n, const int *w, const int *h, const int *C,
             int my = p.roi_margin_y < 0 ? std::max(h[i] / 10, p.win_radius + 2) : p.roi_margin_y;
             D.roi_x0 = mx; D.roi_y0 = my; D.roi_x1 = w[i] - mx; D.roi_y1 = h[i] - my;
             D.lag = lag;
+            D.tmap = p.win_radius == 10 ? take(kLkMapBytes) : nullptr;
             for (int s = 0; s < STAB_PSLOTS; ++s)
                 for (int l = 0; l < D.L; ++l) {
                     size_t px = (size_t)D.lp[l] * D.lh[l];
@@ -226,6 +227,16 @@ stab_status build(Pipeline &pp, int n, const int *w, const int *h, const int *C,
             }
             if (cudaMemset(pp.arena, 0, off) != cudaSuccess) return cuda_check(pp.err, "cudaMemset");
         }
+    }
+    // the tracker's tensor maps address the planes just carved
+    for (int i = 0; i < n; ++i) {
+        StreamDev &D = pp.hs[i];
+        if (!D.tmap) continue;
+        std::vector<unsigned char> maps(kLkMapBytes);
+        if (lk_tensor_maps(D, pp.prec, maps.data()) != 0)
+            return fail(pp.err, STAB_ERR_CUDA, "the driver could not encode the tracker's tensor maps");
+        if (cudaMemcpy(const_cast<void *>(D.tmap), maps.data(), kLkMapBytes, cudaMemcpyHostToDevice) != cudaSuccess)
+            return cuda_check(pp.err, "cudaMemcpy");
     }
     for (int i = 0; i < n; ++i) pp.cand_cap0.push_back(pp.hs[i].cand_cap);
     if (cudaMalloc(&pp.ds, sizeof(StreamDev) * n) != cudaSuccess) return fail(pp.err, STAB_ERR_OOM, "cudaMalloc");

@@ -22,7 +22,7 @@ STAB_FLAG_SKIPPED, STAB_FLAG_DETECTED, STAB_FLAG_RIGID, STAB_FLAG_DECISION = 1, 
 MOTION_WORDS = 10          # 4-byte words of one stab_motion record
 BATCH_LAG = 1              # a batched step ingests frame t and tracks frames t-2 -> t-1
 BATCH_OUT_LAG = 2          # ... and composes frame t - BATCH_OUT_LAG - 1 - W/2
-LK_VARIANTS = 7            # tracker kernel variants (stab_set_lk_variant, the autotuner's candidates)
+LK_VARIANTS = 9            # tracker kernel variants (stab_set_lk_variant, the autotuner's candidates)
 
 
 class StabParams(C.Structure):

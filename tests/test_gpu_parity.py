@@ -187,7 +187,8 @@ PARITY_ITERS = 20
 @pytest.mark.parametrize("cfg,K,L,variant", [(0, 200, 3, 0), (0, 200, 3, 1), (0, 200, 3, 2), (0, 200, 3, 3),
                                               (0, 200, 3, 4), (0, 200, 3, 5), (0, 200, 3, 6), (1, 500, 4, 1),
                                               (1, 500, 4, 6), (2, 1000, 5, 1), (2, 1000, 5, 3), (2, 1000, 5, 4),
-                                              (2, 1000, 5, 5), (2, 1000, 5, 6)])
+                                              (2, 1000, 5, 5), (2, 1000, 5, 6), (0, 200, 3, 7), (1, 500, 4, 8),
+                                              (2, 1000, 5, 7), (2, 1000, 5, 8)])
 def test_lk_parity(cfg, K, L, variant):
     f0, f1, pts, w, h = _lk_case(cfg, 20 + cfg, K, L)
     ref = O.track(O.pyramid(f0, L), O.pyramid(f1, L), pts, max_iters=PARITY_ITERS, eps=0.0)
@@ -206,6 +207,23 @@ def test_lk_parity(cfg, K, L, variant):
     assert d.max() < 0.01, d.max()
     db = np.hypot(*(g["back"][both] - ref["back"][both]).T)
     assert db.max() < 0.02
+
+
+@pytest.mark.parametrize("base,tm", [(0, 7), (1, 8)])
+def test_lk_tensor_copy_variants_compute_what_their_base_computes(base, tm):
+    """Variants 7 and 8 stage the patches that lie inside their level by tensor
+    copies into wider rows (the copy's column alignment); the values and the
+    arithmetic are those of variants 0 and 1, so every output is the same bit
+    for bit -- features near the border, whose patches are copied by the
+    threads with clamped rows and columns, included -- in both storages and
+    with the production stopping rule."""
+    f0, f1, pts, w, h = _lk_case(2, 33, 1000, 5)
+    pts = np.concatenate([pts, np.array([[3.0, 4.0], [w - 2.5, 7.25], [11.5, h - 1.0], [w / 2, 2.0]], np.float32)])
+    for prec in (0, 1):
+        a = _lk_gpu(f0, f1, pts, w, h, len(pts), 5, base, prec)
+        b = _lk_gpu(f0, f1, pts, w, h, len(pts), 5, tm, prec)
+        for k in a:
+            assert np.array_equal(a[k], b[k]), (prec, k)
 
 
 @pytest.mark.parametrize("cfg,K,L", [(0, 200, 3), (2, 1000, 5)])
