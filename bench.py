@@ -38,6 +38,7 @@ METRIC = "1080p stabilized frames/s on 1 GB300 (batched vs plain); p99 frame lat
 W, H, CH = 1920, 1080, 3
 STREAMS = 16
 PARAMS = dict(max_corners=1000, levels=5, hypotheses=100, smooth_window=30, model=1)
+PERIOD = 5      # re-detection period (Sec. 3.2: detect on one frame, track through the next five)
 RING = 2 * (PARAMS["smooth_window"] // 2 + 2)   # >= W/2 + 5 frames, even for the retracing clip
 FP32_PEAK_NOTE = "152 SMs x 128 FP32 lanes x 2 flop x 2.07 GHz max SM clock"
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
@@ -54,11 +55,21 @@ LK_FLOP_SURVEY = (15, 7)
 TRAFFIC = {"lk": {"file": "k_lk.cu", "sha": "81fdb5a9da7c1d73", "bytes_per_launch": 190807808 + 5619712}}
 
 
-def config_dict(streams):
+def phase_of(g: int, staggered: bool) -> int:
+    """Place of video g in its detection cycle: staggered videos enter the cycle
+    at g mod period, so that a fifth of the streams detect at each step, as
+    independently started videos would; lockstep videos all detect together."""
+    return g % PERIOD if staggered else 0
+
+
+def config_dict(streams, staggered=False):
     return {"workload": f"{streams} streams x 1920x1080 RGB, config-2 shape (K=1000 corners, 5 levels, "
                         "similarity, 100 hypotheses, 30-frame window), batched CUDA-graph step, FP16 plane storage",
             "streams": streams, "resolution": "1920x1080", "channels": 3, "corners": 1000, "levels": 5,
             "hypotheses": 100, "smooth_window": 30,
+            "detection": (f"every {PERIOD}th frame; streams staggered (video g detects on frames t with "
+                          f"(t + g) % {PERIOD} == 0)" if staggered else
+                          f"every {PERIOD}th frame, all streams on the same steps"),
             "l2": "inputs larger than L2: each step reads new frames from a device ring of "
                   f"{streams} x {RING} RGB 1080p frames ({streams * RING * W * H * CH / 1e9:.1f} GB)"}
 
@@ -273,13 +284,19 @@ def run_ours(args):
     mine = partition_streams(ws * B, ws, rank)
     n_clips = min(args.clips, B)
     clips = make_frames(n_clips, ring, dev)
-    p16 = S.default_params(**PARAMS, precision=S.STAB_FP16_STORAGE)
-    batch = S.Batch([(W, H, CH, p16) for _ in mine], ring=ring)
+    staggered = args.detect_phases == "staggered"
     src_clip = [g % n_clips for g in mine]
     offs = [(g // n_clips) * 3 % ring for g in mine]
-    for i in range(len(mine)):
-        for s in range(ring):
-            batch.input_slot(i, s).copy_(clips[src_clip[i]][(s + offs[i]) % ring])
+
+    def make_batch(stag):
+        b = S.Batch([(W, H, CH, S.default_params(**PARAMS, precision=S.STAB_FP16_STORAGE,
+                                                 redetect_phase=phase_of(g, stag))) for g in mine], ring=ring)
+        for i in range(len(mine)):
+            for s in range(ring):
+                b.input_slot(i, s).copy_(clips[src_clip[i]][(s + offs[i]) % ring])
+        return b
+
+    batch = make_batch(staggered)
     stream = torch.cuda.current_stream()
     # prime the smoother's lookahead (no composed frame before step A + 3: the
     # step tracks one frame behind the frame it ingests and composes one step
@@ -329,6 +346,28 @@ def run_ours(args):
     # ---- per-step latency: each step launched alone on an idle GPU, events
     # around it, over a fixed count of steps independent of --steps
     lat = latency_loop(batch, stream, args.lat_steps, args.lat_warmup) if args.lat_steps > 0 else None
+    lat_other = None
+    if lat:
+        # the same videos with the other detection schedule: latency and mean
+        # step time (a trade: staggered detection runs the latency-bound
+        # detection kernels on a fifth of the streams at every step)
+        lb = make_batch(not staggered)
+        for _ in range(A + 2 + S.BATCH_OUT_LAG):
+            lb.step(True)
+        if tuned:
+            lb.set_lk_variant(tuned["lk_variant"])
+        lat_other = latency_loop(lb, stream, args.lat_steps, args.lat_warmup)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(args.steps):
+            lb.step(True)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        lat_other["ms_per_step"] = round(e0.elapsed_time(e1) / args.steps, 4)
+        lat_other["detection"] = config_dict(B, not staggered)["detection"]
+        assert lb.sync() == 0
+        del lb
+        torch.cuda.synchronize()
     gaps = sorted(step_ms)
 
     # ---- per-kernel times (event-bracketed steps without a graph)
@@ -355,11 +394,12 @@ def run_ours(args):
     out = {"metric": METRIC, "value": round(value, 1), "unit": "frames/s", "n_gpus": ws, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": round(total_ms / args.steps, 4), "higher_is_better": True,
            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "storage": "u8 frames, f16 I/Ix/Iy planes",
-           "data": "synthetic", "config": config_dict(B),
+           "data": "synthetic", "config": config_dict(B, staggered),
            "latency_ms": dict(lat or {}, per="batch step (16 frames)",
                               # not in the step latency: the step that ingests frame t emits frame
                               # t - (BATCH_OUT_LAG + 1 + W/2), of which W/2 is the smoother's lookahead
                               output_delay_frames=S.BATCH_OUT_LAG + 1 + A, smoothing_lookahead_frames=A),
+           ("latency_lockstep_ms" if staggered else "latency_staggered_ms"): lat_other,
            "step_interval_ms": {"p50": round(gaps[len(gaps) // 2], 4), "max": round(gaps[-1], 4),
                                 "of": f"event gaps between the {args.steps} back-to-back timed steps"},
            "plain": plain, "e2e": e2e, "roofline": roof,
@@ -379,8 +419,10 @@ def run_ours(args):
 def latency_loop(batch, stream, steps: int, warm: int) -> dict:
     """p50 / p99 / max of the device time of one batched step launched with the
     GPU idle (CUDA events around the graph launch, a synchronisation after
-    each), over `steps` steps after `warm` untimed ones; one step in five
-    detects corners, so the p99 is a detection step."""
+    each), over `steps` steps after `warm` untimed ones.  A stream detects
+    corners on one step in five: with the streams' detection steps staggered
+    every step detects on a fifth of them, in lockstep one step in five detects
+    on all (its p99 is that step)."""
     import torch
     a = torch.cuda.Event(enable_timing=True)
     b = torch.cuda.Event(enable_timing=True)
@@ -890,6 +932,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-autotune", action="store_true")
     ap.add_argument("--lk-variant", type=int, default=-1, help="force a tracker variant instead of autotuning")
+    ap.add_argument("--detect-phases", default="lockstep", choices=["staggered", "lockstep"],
+                    help="spread the streams' detection steps over the cycle, or detect on all streams together")
     args = ap.parse_args()
     if args.clock_sampler:
         clock_sampler_main(args.clock_sampler, args.clock_index, args.clock_uuid, args.clock_period_ms)

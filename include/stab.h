@@ -71,7 +71,8 @@ typedef struct {
     float quality;        /* corner threshold: q * max response (0.01) */
     int roi_margin_x;     /* reduced ROI (Sec. 3.1); -1 = max(w/10, r+2) */
     int roi_margin_y;     /* -1 = max(h/10, r+2) */
-    int redetect_period;  /* detect on frame t-1 when (t-1) % period == 0 (Sec. 3.2: 5) */
+    int redetect_period;  /* detect on frame t-1 when (t-1 + redetect_phase) % period == 0
+                             (Sec. 3.2: 5) */
     int min_tracks;       /* also re-detect when fewer live tracks */
     float fb_thresh;      /* forward-backward round-trip limit (px) */
     float inlier_thresh;  /* robust fit inlier radius (px) */
@@ -85,6 +86,10 @@ typedef struct {
     float crop_zoom;      /* composition crop (Sec. 5.1): output = centre region of the warped
                              frame magnified by crop_zoom about the image centre; 1 = no crop,
                              range [1, 4] */
+    int redetect_phase;   /* place of the stream in its detection cycle, 0 .. period-1: besides
+                             the first transition, detect on frame t-1 when
+                             (t-1 + phase) % period == 0.  Streams of a batch with different
+                             phases spread their detection frames over the cycle (default 0) */
 } stab_params;
 
 typedef struct {

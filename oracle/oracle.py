@@ -333,6 +333,7 @@ class Params:
     min_eig: float = 1e-2
     quality: float = 0.01
     redetect_period: int = 5     # Sec. 3.2: detect on one frame, track through the next five
+    redetect_phase: int = 0      # where the clip enters that cycle (0: detect on frames 0, 5, 10, ...)
     min_tracks: int = 10
     fb_thresh: float = 1.0
     inlier_thresh: float = 1.0
@@ -406,7 +407,7 @@ def run_clip(frames: np.ndarray, p: Params) -> dict:
     cur_rigid = p.rigid and not p.hybrid     # hybrid: similarity until the first decision
     feats = None
     for t in range(1, T):
-        if feats is None or (t - 1) % p.redetect_period == 0 or len(feats) < p.min_tracks:
+        if feats is None or (t - 1 + p.redetect_phase) % p.redetect_period == 0 or len(feats) < p.min_tracks:
             feats, _, _ = detect(gray[t - 1], roi, p.max_corners, p.quality)
             detected[t - 1] = True
         tr = track(pyrs[t - 1], pyrs[t], feats, p.win_r, p.max_iters, p.eps, p.min_eig, p.fb_thresh)

@@ -75,7 +75,7 @@ struct StreamDev {
     int w, h, C, L, K;
     int lw[STAB_MAXL], lh[STAB_MAXL], lp[STAB_MAXL];   // level sizes, pitch (elements)
     // parameters
-    int r, max_iters, period, min_tracks, min_fit, H, model, dwell, W, prec;
+    int r, max_iters, period, phase, min_tracks, min_fit, H, model, dwell, W, prec;
     int lag;   // tracking runs this many frames behind the frame being ingested (batches: 1)
     float eps2, min_eig, quality, fb2, tau2, zoom;
     unsigned long long seed;

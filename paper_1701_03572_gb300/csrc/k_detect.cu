@@ -60,7 +60,7 @@ __global__ void k_begin(const StreamDev *__restrict__ S, int n, long long t_ov, 
     const long long tb = t - D.lag;   // transition tracked by this step: frames tb-1 -> tb
     int due;
     if (force_due) due = 1;
-    else due = (tb >= 1) && (st->n_feat == 0 || ((tb - 1) % D.period) == 0 || st->n_feat < D.min_tracks);
+    else due = (tb >= 1) && (st->n_feat == 0 || ((tb - 1 + D.phase) % D.period) == 0 || st->n_feat < D.min_tracks);
     st->due = due;
     st->n_cand = 0;
     st->n_sel = 0;

@@ -110,6 +110,8 @@ stab_status check_params(const stab_params &p, int w, int h, std::string &err)
         !(p.inlier_thresh > 0.f))
         return fail(err, STAB_ERR_INVALID_ARG, "negative threshold");
     if (p.redetect_period < 1) return fail(err, STAB_ERR_INVALID_ARG, "redetect_period < 1");
+    if (p.redetect_phase < 0 || p.redetect_phase >= p.redetect_period)
+        return fail(err, STAB_ERR_INVALID_ARG, "redetect_phase out of [0, redetect_period)");
     if (p.hypotheses < 1 || p.hypotheses > 1 << 20) return fail(err, STAB_ERR_INVALID_ARG, "hypotheses out of range");
     if (p.smooth_window < 1 || p.smooth_window >= STAB_CRING) return fail(err, STAB_ERR_INVALID_ARG, "smooth_window out of [1, 63]");
     if (p.model != STAB_RIGID && p.model != STAB_SIMILARITY && p.model != STAB_HYBRID)
@@ -164,7 +166,7 @@ stab_status build(Pipeline &pp, int n, const int *w, const int *h, const int *C,
             D.lw[0] = w[i]; D.lh[0] = h[i];
             for (int l = 1; l < D.L; ++l) { D.lw[l] = (D.lw[l - 1] + 1) / 2; D.lh[l] = (D.lh[l - 1] + 1) / 2; }
             for (int l = 0; l < D.L; ++l) D.lp[l] = up(D.lw[l], 64);
-            D.r = p.win_radius; D.max_iters = p.max_iters; D.period = p.redetect_period;
+            D.r = p.win_radius; D.max_iters = p.max_iters; D.period = p.redetect_period; D.phase = p.redetect_phase;
             D.min_tracks = p.min_tracks; D.min_fit = p.min_fit; D.H = p.hypotheses;
             D.model = p.model; D.dwell = p.dwell; D.zoom = p.crop_zoom;
             D.W = p.smooth_window; D.prec = p.precision;

@@ -31,7 +31,7 @@ class StabParams(C.Structure):
                 ("roi_margin_y", C.c_int), ("redetect_period", C.c_int), ("min_tracks", C.c_int),
                 ("fb_thresh", C.c_float), ("inlier_thresh", C.c_float), ("hypotheses", C.c_int),
                 ("seed", C.c_uint64), ("min_fit", C.c_int), ("smooth_window", C.c_int), ("model", C.c_int),
-                ("precision", C.c_int), ("dwell", C.c_int), ("crop_zoom", C.c_float)]
+                ("precision", C.c_int), ("dwell", C.c_int), ("crop_zoom", C.c_float), ("redetect_phase", C.c_int)]
 
 
 class StabMotion(C.Structure):

@@ -103,13 +103,15 @@ MIXED = [(320, 240, 200, 3), (640, 480, 292, 4), (1280, 720, 538, 5), (1920, 108
 def test_batch_mixed_resolutions_vs_oracle():
     """One stream of each resolution of the 64-stream mixed workload in one
     batch: uneven work lists (strips, features, tiles) across streams, five
-    levels next to three, one graph launch per step."""
+    levels next to three, one graph launch per step; the streams sit at
+    detection phases 1 .. 4, so different streams detect on different steps."""
     clips, params, ops = [], [], []
     for k, (w, h, K, L) in enumerate(MIXED):
         clips.append(make_clip(ClipSpec(w, h, T), 4200 + k, device=DEV)["frames"].cpu().numpy())
         params.append(S.default_params(max_corners=K, levels=L, hypotheses=100, smooth_window=W,
-                                       precision=S.STAB_FP16_STORAGE))
-        ops.append(O.Params(max_corners=K, levels=L, hypotheses=100, smooth_window=W, rigid=False))
+                                       precision=S.STAB_FP16_STORAGE, redetect_phase=k + 1))
+        ops.append(O.Params(max_corners=K, levels=L, hypotheses=100, smooth_window=W, rigid=False,
+                            redetect_phase=k + 1))
     motions, outs = _run_batch(clips, params)
     for i, f in enumerate(clips):
         _check_stream(f, motions[i], outs[i], ops[i], f"{MIXED[i][0]}x{MIXED[i][1]}")
@@ -118,17 +120,19 @@ def test_batch_mixed_resolutions_vs_oracle():
 def test_batch_16_streams_in_the_benchmark_configuration():
     """The benchmark's launch configuration: 16 streams of 1920x1080 RGB, 1000
     corners, 5 levels, 100 hypotheses, a 30-frame window, FP16 storage, the
-    autotuned tracker.  Two of the streams (the first and the last of the
-    work lists) are checked against the oracle motion by motion and frame by
-    frame; every stream's motions are checked against the generator's exact
-    camera motion (a property that holds at any size)."""
+    autotuned tracker -- with the streams' detection steps staggered (stream s
+    at phase s mod 5, the benchmark's alternate schedule; the lockstep one is
+    phase 0 everywhere, as in the tests above).  Three of the streams (the first and the last of the work
+    lists, and one at phase 2) are checked against the oracle motion by motion
+    and frame by frame; every stream's motions are checked against the
+    generator's exact camera motion (a property that holds at any size)."""
     T16, W30 = 22, 30          # composed frames from step 3 + 15 = 18 on
     spec = dataclasses.replace(CONFIG_SPECS[2], frames=T16)
     clips = [make_clip(spec, 4300 + s, device=DEV) for s in range(16)]
     frames = [c["frames"].cpu().numpy() for c in clips]
-    p = S.default_params(max_corners=1000, levels=5, hypotheses=100, smooth_window=W30, model=S.STAB_SIMILARITY,
-                         precision=S.STAB_FP16_STORAGE)
-    b = S.Batch([(1920, 1080, 3, p)] * 16)
+    b = S.Batch([(1920, 1080, 3, S.default_params(max_corners=1000, levels=5, hypotheses=100, smooth_window=W30,
+                                                  model=S.STAB_SIMILARITY, precision=S.STAB_FP16_STORAGE,
+                                                  redetect_phase=s % 5)) for s in range(16)])
     motions = [[None] * T16 for _ in range(16)]
     outs = [{} for _ in range(16)]
     for t in range(T16):
@@ -142,15 +146,17 @@ def test_batch_16_streams_in_the_benchmark_configuration():
         for i in range(16):
             motions[i][t] = mot[i]
             k = t - S.BATCH_OUT_LAG - 1 - W30 // 2
-            if k >= 0 and i in (0, 15):
+            if k >= 0 and i in (0, 7, 15):
                 outs[i][k] = b.output(i).cpu().numpy().copy()
     assert b.sync() == 0
-    op = O.Params(max_corners=1000, levels=5, hypotheses=100, smooth_window=W30, rigid=False)
-    for i in (0, 15):
+    for i in (0, 7, 15):
+        op = O.Params(max_corners=1000, levels=5, hypotheses=100, smooth_window=W30, rigid=False,
+                      redetect_phase=i % 5)
         ref = O.run_clip(frames[i], op)
         for t in range(1 + S.BATCH_LAG, T16):
             tt = t - S.BATCH_LAG
             m = np.array(motions[i][t]["m"], np.float64)
+            assert bool(motions[i][t]["flags"] & S.STAB_FLAG_DETECTED) == bool(ref["detected"][tt - 1]), (i, tt)
             assert np.abs(m[2:] - ref["incs"][tt, 2:]).max() < 2e-4, (i, tt)
             assert np.abs(m[:2] - ref["incs"][tt, :2]).max() < 0.05, (i, tt)
         assert len(outs[i]) == T16 - S.BATCH_OUT_LAG - 1 - W30 // 2

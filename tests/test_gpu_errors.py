@@ -67,3 +67,9 @@ def test_candidate_capacity_argument_errors():
         ctx.set_candidate_capacity(-1)
     assert S.lib().stab_set_candidate_capacity(None, 10) == -1
     assert S.lib().stab_batch_set_candidate_capacity(None, 10) == -1
+
+
+@pytest.mark.parametrize("phase", [-1, 5])
+def test_detection_phase_outside_the_cycle_is_rejected(phase):
+    with pytest.raises(S.StabError):
+        S.Context(320, 240, S.default_params(redetect_phase=phase))

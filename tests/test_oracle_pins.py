@@ -580,6 +580,23 @@ def test_pipeline_recovers_generator_motion():
     assert np.abs(r["incs"][1:, :2] - gt[1:, :2]).max() < 0.1
 
 
+@pytest.mark.parametrize("phase", [0, 2, 4])
+def test_detection_cycle_and_its_phase(phase):
+    """Sec. 3.2: corners are detected on one frame and tracked through the next
+    five, then detected again; a clip entering that cycle at `phase` detects on
+    frame 0 (nothing to track yet) and then on the frames t with
+    (t + phase) % 5 == 0.  Every transition still recovers the camera motion."""
+    import dataclasses
+    from paper_1701_03572_gb300.synth import make_clip, CONFIG_SPECS
+    clip = make_clip(dataclasses.replace(CONFIG_SPECS[0], frames=13), 6)
+    r = O.run_clip(clip["frames"].numpy(), O.Params(redetect_phase=phase))
+    want = sorted({0} | {t for t in range(12) if (t + phase) % 5 == 0})
+    assert list(np.flatnonzero(r["detected"])) == want
+    gt = clip["incs"]
+    assert np.abs(r["incs"][1:, 2:] - gt[1:, 2:]).max() < 1e-3
+    assert np.abs(r["incs"][1:, :2] - gt[1:, :2]).max() < 0.1
+
+
 # ------------------------------------------- hybrid mechanism (Sec. 4.1) --
 def test_hybrid_choice_rule():
     # rigid iff both fits exist and rigid's RMS is strictly lower; a failed
