@@ -25,11 +25,11 @@ __host__ __device__ inline int stab_pslot(long long f) { return (int)(((f % STAB
 #define STAB_HSHIFT 19
 #define STAB_SEL_SMEM 12288  // selection keys held in shared memory
 #define STAB_TW 64           // warp output tile width (pixels)
-// Corner response work: strips of 32 rows and 120 columns of the ROI, one warp
+// Corner response work: strips of 20 rows and 120 columns of the ROI, one warp
 // each (lanes 1..30 own 4 columns each; lanes 0 and 31 supply the neighbouring
 // columns to lanes 1 and 30), four warps per block.
 #define STAB_RS_THREADS 128
-#define STAB_RS_ROWS 32
+#define STAB_RS_ROWS 20
 #define STAB_RS_COLS 120
 __host__ __device__ inline int stab_resp_items(int rw, int rh)
 {

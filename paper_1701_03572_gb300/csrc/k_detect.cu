@@ -2,7 +2,7 @@
 // (Sec. 3.1, Eq. 2) and exact top-K selection.
 //
 //  k_begin     per stream: frame index, whether detection is due, counters.
-//  k_response  vertical strips of the ROI (a thread walks 4 columns down 32
+//  k_response  vertical strips of the ROI (a thread walks 4 columns down 20
 //              rows): Sobel 3x3 -> integer tensor over a 3x3 box -> FP32 min
 //              eigenvalue -> 3x3 non-maximum suppression.  Survivors are
 //              appended as 64-bit keys (score bits << 32 | ~raster index), so
@@ -106,7 +106,7 @@ template <int I>
 struct Slot { static constexpr int value = I; };
 
 // Corner response (Eq. 2), NMS and candidate list as barrier-free vertical
-// strips, each warp on its own: a warp owns a strip of 120 ROI columns and 32
+// strips, each warp on its own: a warp owns a strip of 120 ROI columns and 20
 // rows (drawn from an atomic ticket when the work list has one), a thread
 // columns x .. x+3 of it, and walks its pixel rows once.  Per pixel row it forms the separable Sobel parts
 // (horizontal difference and [1 2 1] smoothing) of its 4 columns and keeps two
