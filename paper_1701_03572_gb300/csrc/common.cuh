@@ -69,6 +69,7 @@ struct StreamState {
     int n_det;            // corners of the last detection
     int n_above;          // candidates above the quality threshold (before the top-K cut)
     int hyb_rigid;        // hybrid mechanism: the model held since the last decision (1 rigid)
+    int n_due[2];         // stream 0 only: streams due for detection at steps of frame parity 0 / 1
 };
 
 struct StreamDev {

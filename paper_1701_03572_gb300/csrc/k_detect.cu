@@ -62,6 +62,11 @@ __global__ void k_begin(const StreamDev *__restrict__ S, int n, long long t_ov, 
     if (force_due) due = 1;
     else due = (tb >= 1) && (st->n_feat == 0 || ((tb - 1 + D.phase) % D.period) == 0 || st->n_feat < D.min_tracks);
     st->due = due;
+    // detection-due count of this step (read by the detection kernels, which
+    // return at once when it is 0); the other parity's count is cleared for
+    // the next step
+    if (due) atomicAdd(&S[0].st->n_due[t & 1], 1);
+    if (s == 0) S[0].st->n_due[(t + 1) & 1] = 0;
     st->n_cand = 0;
     st->n_sel = 0;
     st->n_above = 0;
@@ -96,6 +101,13 @@ __device__ __forceinline__ void rs_pixels(const uint8_t *__restrict__ g, int pit
     }
 }
 
+// True when k_begin found no stream due for detection at this step.
+__device__ __forceinline__ bool no_detection_due(const StreamDev *__restrict__ S)
+{
+    const StreamState *s0 = S[0].st;
+    return __ldcg(&s0->n_due[s0->t & 1]) == 0;
+}
+
 // Candidates of a strip are collected in the warp's shared-memory buffer and
 // appended to the stream's list with one global atomic per strip (a full
 // buffer appends the warp's candidates directly).
@@ -120,6 +132,7 @@ struct Slot { static constexpr int value = I; };
 __global__ void __launch_bounds__(STAB_RS_THREADS, 4) k_response(const StreamDev *__restrict__ S, WorkList wl, DetIO io)
 {
     __shared__ unsigned long long s_keys[STAB_RS_THREADS / 32][RS_CAP];
+    if (no_detection_due(S)) return;
     const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
     unsigned long long *wkeys = s_keys[wp];
     const int nwarps = gridDim.x * (STAB_RS_THREADS / 32);
@@ -345,6 +358,7 @@ __global__ void __launch_bounds__(STAB_RS_THREADS, 4) k_response(const StreamDev
 
 __global__ void __launch_bounds__(256) k_filter(const StreamDev *__restrict__ S, WorkList wl)
 {
+    if (no_detection_due(S)) return;
     const int tid = threadIdx.x, lane = tid & 31;
     for (int item = blockIdx.x; item < wl.total; item += gridDim.x) {
         const int s = wl_stream(wl, item);
