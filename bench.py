@@ -46,9 +46,10 @@ FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
 # (3 x 7 flop) + G accumulation (3 FMA = 6 flop) = 27; iteration = bilinear J
 # (7) + residual (1) + b accumulation (2 FMA = 4) = 12.
 LK_FLOP_TEMPLATE, LK_FLOP_ITER = 27, 12
-# The hot-path survey's rough estimate of the same counts (6.6 k and 3.1 k per
-# 441-sample window, i.e. about 15 and 7 per sample), reported beside ours.
-LK_FLOP_SURVEY = (15, 7)
+# A coarser count of the same work (6.6 k and 3.1 k flop per 441-sample window,
+# about 15 and 7 per sample: one sampled plane in the template pass), reported
+# beside ours.
+LK_FLOP_COARSE = (15, 7)
 # DRAM traffic per launch of the dominant kernel from one ncu capture
 # (dram__bytes_read.sum + dram__bytes_write.sum of one launch on this workload,
 # 16 streams); used only while the kernel source is unchanged.
@@ -486,12 +487,12 @@ def roofline(kavg: dict, lkw: list, B: int) -> dict:
     lk_flop = tp * n_win * LK_FLOP_TEMPLATE + it * n_win * LK_FLOP_ITER
     if kavg.get("lk", 0) > 0:
         tf = lk_flop / (kavg["lk"] / 1e3) / 1e12
-        tf_s = (tp * n_win * LK_FLOP_SURVEY[0] + it * n_win * LK_FLOP_SURVEY[1]) / (kavg["lk"] / 1e3) / 1e12
+        tf_s = (tp * n_win * LK_FLOP_COARSE[0] + it * n_win * LK_FLOP_COARSE[1]) / (kavg["lk"] / 1e3) / 1e12
         kernels["lk"] = {"bound": "alu", "achieved": round(tf, 3), "unit": "TFLOP/s",
                          "frac": round(tf / FP32_PEAK_TFLOPS, 4), "ms": round(kavg["lk"], 4),
                          "iterations": int(it), "template_passes": int(tp),
                          "flop_per_sample": {"template": LK_FLOP_TEMPLATE, "iteration": LK_FLOP_ITER},
-                         "frac_at_survey_estimate": {"flop_per_sample": list(LK_FLOP_SURVEY),
+                         "frac_at_coarse_count": {"flop_per_sample": list(LK_FLOP_COARSE),
                                                      "frac": round(tf_s / FP32_PEAK_TFLOPS, 4)}}
     if dom in kernels:
         d = kernels[dom]
