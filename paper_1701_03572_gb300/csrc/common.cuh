@@ -29,6 +29,8 @@ __host__ __device__ inline int stab_pslot(long long f) { return (int)(((f % STAB
 // each (lanes 1..30 own 4 columns each; lanes 0 and 31 supply the neighbouring
 // columns to lanes 1 and 30), four warps per block.
 #define STAB_RS_THREADS 128
+// Level-0 work: strips of STAB_L0_ROWS rows and 512 columns (128 threads x 4 columns).
+#define STAB_L0_ROWS 24
 #define STAB_RS_ROWS 20
 #define STAB_RS_COLS 120
 __host__ __device__ inline int stab_resp_items(int rw, int rh)

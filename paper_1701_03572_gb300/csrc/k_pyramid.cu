@@ -37,12 +37,12 @@ __device__ __forceinline__ void store_G(float2 *p, const float gx[4], const floa
 
 // Level 0: frame (gray, or RGB converted to luma) -> u8 level 0 + planes.
 // Vertical strips, no shared memory and no barriers: a thread owns 4
-// consecutive columns x .. x+3 of a 16-row strip and walks down it with the
+// consecutive columns x .. x+3 of a STAB_L0_ROWS-row strip and walks down it with the
 // luma of rows y-1, y, y+1 (columns x-1 .. x+4) in registers; each new row
 // costs five aligned 32-bit loads of RGB (three of gray), each emitted row
 // three vector stores.  Columns and rows outside the image are clamped
 // (replicated border), so the planes match the clamped central differences.
-constexpr int L0_STRIP = 16;   // rows per strip
+constexpr int L0_STRIP = STAB_L0_ROWS;   // rows per strip
 constexpr int L0_GROUPS = 128; // 4-column groups per work item (one per thread)
 
 __device__ __forceinline__ unsigned luma4(unsigned a, unsigned b, unsigned c)

@@ -255,7 +255,7 @@ stab_status build(Pipeline &pp, int n, const int *w, const int *h, const int *C,
         lists.push_back({wl, pre});
     };
     // level 0: strips of 512 columns x 16 rows (one thread per 4 columns)
-    mk(&pp.wl_l0, [](const StreamDev &D) { return ((D.w + 511) / 512) * ((D.h + 15) / 16); });
+    mk(&pp.wl_l0, [](const StreamDev &D) { return ((D.w + 511) / 512) * ((D.h + STAB_L0_ROWS - 1) / STAB_L0_ROWS); });
     for (int l = 1; l < STAB_MAXL; ++l)
         mk(&pp.wl_pyr[l], [l](const StreamDev &D) { return l < D.L ? stab_pd_items(D.lw[l], D.lh[l]) : 0; });
     // levels 2 .. L-1 in groups of pyr_tail_levels(); items are tiles of each
