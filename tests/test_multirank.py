@@ -74,3 +74,17 @@ def test_single_process_helpers():
         areas.append(sum(MIXED_SIZES[i][0] * MIXED_SIZES[i][1] for i in xs))
     assert max(areas) - min(areas) <= 1920 * 1080
     assert bench.max_over_ranks(3.5) == 3.5
+
+
+def test_detection_phases_of_the_two_schedules():
+    """Staggered videos enter the detection cycle at g mod 5, so every step detects on a fifth
+    of a rank's streams (16 videos: 3 or 4 per phase, each phase present); lockstep videos
+    all sit at phase 0.  The bench line names the schedule it ran."""
+    g = list(range(bench.STREAMS))
+    stag = [bench.phase_of(v, True) for v in g]
+    assert all(0 <= p < bench.PERIOD for p in stag)
+    counts = [stag.count(p) for p in range(bench.PERIOD)]
+    assert min(counts) >= bench.STREAMS // bench.PERIOD and max(counts) <= bench.STREAMS // bench.PERIOD + 1
+    assert [bench.phase_of(v, False) for v in g] == [0] * bench.STREAMS
+    assert "staggered" in bench.config_dict(bench.STREAMS, True)["detection"]
+    assert "same steps" in bench.config_dict(bench.STREAMS, False)["detection"]
