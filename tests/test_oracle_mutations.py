@@ -67,6 +67,9 @@ PY_MUTATIONS = [
     ("hybrid schedule off by one", "if p.hybrid and (t - 1) % p.dwell == 0:", "if p.hybrid and t % p.dwell == 0:"),
     ("hybrid motion from the other model", "f = fr if rigid else fs", "f = fs if rigid else fr"),
     ("hybrid choice not held", "rigid = cur_rigid if p.hybrid else p.rigid", "rigid = False if p.hybrid else p.rigid"),
+    ("detection phase ignored", "(t - 1 + p.redetect_phase) % p.redetect_period == 0", "(t - 1) % p.redetect_period == 0"),
+    ("detection phase sign", "(t - 1 + p.redetect_phase) % p.redetect_period == 0",
+     "(t - 1 - p.redetect_phase) % p.redetect_period == 0"),
 ]
 
 PINS = [
@@ -98,6 +101,7 @@ PINS = [
     (P.test_affine_refit_is_least_squares_on_inliers, {}), (P.test_affine_of_a_similarity_is_the_similarity, {}),
     (P.test_affine_collinear_points_are_skipped, {}),
     (P.test_hybrid_transitions_on_scripted_pairs, {}), (P.test_hybrid_dwell_schedule_and_bookkeeping, {}),
+    (P.test_detection_cycle_and_its_phase, dict(phase=2)),
 ]
 
 
